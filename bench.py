@@ -1,0 +1,350 @@
+"""Benchmark of the Mindlin-operator apply on the 512 x 512 x 64 operator workload.
+
+One step = one apply of the discretised Mindlin operator (plastic strain -> stress,
+all six components on every voxel: eigenstress, forward in-plane FFT, per-mode depth
+operator, inverse FFT with the stress epilogue) on a seeded random plastic-strain
+field (i.i.d. N(0, 1e-3^2) per voxel and component times exp(-z/0.1)), FP32, inputs
+resident in HBM (402.7 MB in, 402.7 MB out: larger than the 129 MB L2, so no flush
+is needed between steps).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead
+(a bounded sample of the same workload, extrapolated to a full apply).
+Multi-GPU (torchrun): one independent replica per rank ("replicas only"), value is
+the sum of voxels over ranks divided by the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N1 = N2 = 512
+NZ = 64
+DEPTH = 0.4
+E, NU = 1.0, 0.3
+SEED = 1812
+METRIC = "Mindlin-apply voxels/s"
+UNIT = "voxel/s"
+WORKLOAD = "mindlin_apply_512x512x64_fp32"
+# algorithmic bytes per voxel of one kernel pass: read 6 FP32 values, write 6 FP32 values
+# (each kernel of the apply reads and writes the whole field once; the apply as a whole
+# needs the same 48 B/voxel)
+ALG_BYTES_PER_VOXEL = 48.0
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.idx)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], r[5:9]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_1811_11558_gb300 import Context, fvim, inputs
+
+    ws, rank, local = _dist()
+    if not os.path.exists(fvim.LIB_PATH):
+        import __graft_entry__
+
+        __graft_entry__.build()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        pg = dist
+    z = inputs.uniform_depth(NZ, DEPTH)
+    ep = inputs.plastic_strain_field(N1, N2, z, seed=SEED + rank, dtype=np.float32)
+    vox = N1 * N2 * NZ
+    ctx = Context(N1, N2, z, 1.0, 1.0, precision="fp32", E=E, nu=NU)
+    d_in = torch.from_numpy(ep).cuda()
+    d_out = torch.empty_like(d_in)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    # --- device-resident timing (per-kernel events recorded live by the library) ---
+    for _ in range(args.warmup):
+        ctx.apply_mindlin(d_in, d_out)
+    kernels_per_step = ctx.last_kernel_count()
+    ctx.profile_read()
+    ctx.profile(True)
+    ctx.profile_read()
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        ctx.apply_mindlin(d_in, d_out)
+    t1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ms = t0.elapsed_time(t1)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if pg is not None:
+        pg.all_reduce(ms_t, op=pg.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = ws * vox * args.steps / (ms_max / 1e3)
+
+    # --- end to end through the same C-ABI call with host buffers -------------------
+    h_in = torch.from_numpy(ep).pin_memory()
+    h_out = torch.empty(h_in.shape, dtype=torch.float32).pin_memory()
+    for _ in range(max(1, args.warmup // 2)):
+        d_in.copy_(h_in, non_blocking=True)
+        ctx.apply_mindlin(d_in, d_out)
+        h_out.copy_(d_out, non_blocking=True)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        d_in.copy_(h_in, non_blocking=True)
+        ctx.apply_mindlin(d_in, d_out)
+        h_out.copy_(d_out, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    ems = e0.elapsed_time(e1)
+    ems_t = torch.tensor([ems], dtype=torch.float64, device="cuda")
+    if pg is not None:
+        pg.all_reduce(ems_t, op=pg.ReduceOp.MAX)
+    e2e_value = ws * vox * args.steps / (float(ems_t.item()) / 1e3)
+    assert np.isfinite(h_out[0, 0, :4, :4].numpy()).all()
+
+    # --- roofline of the dominant kernel ---------------------------------------------
+    peak, peak_kind = _peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n) = dom
+    avg_ms = dom_ms / dom_n
+    alg_bytes = ALG_BYTES_PER_VOXEL * vox
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+    roofline = {
+        "bound": "hbm",
+        "kernel": dom_name,
+        "achieved": round(achieved, 1),
+        "peak": peak,
+        "peak_kind": peak_kind,
+        "unit": "GB/s",
+        "frac": round(achieved / peak, 4),
+        "traffic": TRAFFIC_BYTES.get(dom_name),
+        "alg_bytes": alg_bytes,
+        "avg_launch_ms": round(avg_ms, 5),
+    }
+    kernel_ms = {k: round(v[0] / v[1], 5) for k, v in prof.items()}
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n1": N1, "n2": N2, "nz": NZ, "depth": DEPTH, "output": "stress",
+                   "voxels": vox, "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs (402.7 MB) larger than L2, no flush"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h_in.numel() * 4),
+                "d2h_bytes_per_step": int(h_out.numel() * 4)},
+        "gpu_launches": kernels_per_step * args.steps,
+        "kernel_ms": kernel_ms,
+        "roofline": roofline,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sample_modes=256, sample_planes=None)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each kernel on this
+# workload; None until a capture of the current kernel exists (profiles/ summaries).
+TRAFFIC_BYTES = {}
+
+
+def cpu_baseline(sample_modes=256, sample_planes=None, seed=SEED):
+    """Time the FP64 oracle on a bounded sample of the operator workload.
+
+    Sample: the oracle's forward and inverse DFT of ``sample_planes`` of the 384
+    (layer, component) planes (all of them when None) plus its per-mode depth
+    operator on ``sample_modes`` random modes; both are scaled to one full apply
+    (384 planes each way, 131 072 resolved modes).
+    """
+    from oracle import operators as op
+    from oracle import tensors as T
+    from paper_1811_11558_gb300 import inputs
+
+    z = inputs.uniform_depth(NZ, DEPTH)
+    ep = inputs.plastic_strain_field(N1, N2, z, seed=seed)
+    lam, mu = T.lame(E, NU)
+    planes = NZ * 6
+    npl = planes if sample_planes is None else int(sample_planes)
+    t0 = time.perf_counter()
+    w = T.hooke6(ep, lam, mu, axis=1).reshape(planes, N2, N1)[:npl]
+    wh = np.fft.fft2(w, axes=(-2, -1))
+    back = np.fft.ifft2(wh, axes=(-2, -1)).real
+    t_fft = (time.perf_counter() - t0) * planes / npl
+    assert back.shape == w.shape
+    rng = np.random.default_rng(seed)
+    k2 = rng.integers(0, N2, sample_modes)
+    k1 = rng.integers(0, N1, sample_modes)
+    Q1, Q2, nyq, zero = op.mode_grid(N1, N2, 1.0, 1.0)
+    keep = ~(nyq[k2, k1] | zero[k2, k1])
+    k1, k2 = k1[keep], k2[keep]
+    W = (rng.standard_normal((k1.size, NZ, 3, 3)) + 1j * rng.standard_normal((k1.size, NZ, 3, 3))) * 1e-3
+    W = 0.5 * (W + np.swapaxes(W, -1, -2))
+    Q = np.stack([Q1[k2, k1], Q2[k2, k1]], axis=1)
+    t1 = time.perf_counter()
+    op.mindlin_modes(W, Q, z, E, NU)
+    t_modes = (time.perf_counter() - t1) * (N1 * (N2 // 2)) / k1.size
+    total = t_fft + t_modes
+    return {
+        "value": N1 * N2 * NZ / total,
+        "unit": UNIT,
+        "cores": 1,
+        "kind": "oracle",
+        "sample": "FP64 oracle: DFT of %d of 384 planes each way + per-mode depth quadrature on %d random "
+                  "modes, scaled to one 512x512x64 apply (%.1f s extrapolated)" % (npl, k1.size, total),
+    }
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    t = []
+    for i in range(args.warmup + args.steps):
+        s = time.perf_counter()
+        cb = cpu_baseline(sample_modes=16, sample_planes=4, seed=SEED + i)
+        dt = time.perf_counter() - s
+        if i >= args.warmup:
+            t.append(cb["value"])
+    value = float(np.median(t))
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "impl": "reference",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * N1 * N2 * NZ / value,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n1": N1, "n2": N2, "nz": NZ, "depth": DEPTH, "output": "stress",
+                   "voxels": N1 * N2 * NZ},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "per step: FP64 oracle DFT of 4 of 384 planes each way + depth quadrature "
+                                   "on <=16 random modes, scaled to one full apply"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="fvim", choices=["fvim", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,150 @@
+/*
+ * fvim.h -- C ABI of the GB300 (sm_103a) implementation of the Fourier-accelerated
+ * volume integral method for elastoplastic contact (Frerot, Bonnet, Molinari &
+ * Anciaux, arXiv:1811.11558).
+ *
+ * Problem (Sec. 1): a horizontally periodic half-space y3 >= 0 (e3 points into the
+ * body), periodic cell ]-L1/2, L1/2[ x ]-L2/2, L2/2[ (Eq. periodic_cell), discretised
+ * on N1 x N2 in-plane points and Nz depth nodes X3 = {z_0 = 0 < z_1 < ... < z_{Nz-1}}
+ * (Sec. 3.1).  Isotropic elasticity (E, nu), J2 plasticity with linear isotropic
+ * hardening (sigma_y, E_h) (Sec. 4.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Symmetric tensors are stored as six TENSOR components in the order
+ *   (11, 22, 33, 23, 13, 12); shears are eps_ij, not engineering shears.
+ * - Volume fields are contiguous [Nz][6][N2][N1] arrays (x1 fastest); surface fields
+ *   are contiguous [N2][N1]; scalar volume fields are [Nz][N2][N1].
+ * - Element type is float for FVIM_FP32 contexts and double for FVIM_FP64 contexts.
+ * - Pointers marked "device" are CUDA device pointers owned by the caller; the library
+ *   never frees them.  The context owns its scratch buffers and its plastic state.
+ * - Every call is enqueued on the context's CUDA stream and returns before the GPU has
+ *   finished (stream ordered), unless stated otherwise.  Arguments are checked on the
+ *   host before anything is launched.  Functions never throw across the ABI; they
+ *   return FVIM_OK or a negative status.
+ * - Pressure p >= 0 pushes into the body (a force p e3 per unit area, Sec. 1.1),
+ *   so sigma_33 = -p on the surface; u3 > 0 is a displacement into the body.
+ */
+#ifndef FVIM_H
+#define FVIM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FVIM_FP32 0
+#define FVIM_FP64 1
+
+#define FVIM_STRESS 0 /* output sigma = C:grad^sym N[w] - w (or C:grad^sym M[p]) */
+#define FVIM_STRAIN 1 /* output grad^sym N[w] (or grad^sym M[p])                 */
+
+enum {
+  FVIM_OK = 0,
+  FVIM_ERR_ARG = -1,           /* invalid argument (size, pointer, kind)          */
+  FVIM_ERR_OOM = -2,           /* device allocation failed                         */
+  FVIM_ERR_CUDA = -3,          /* a CUDA runtime call or launch failed             */
+  FVIM_ERR_NONFINITE = -4,     /* non-finite value detected                        */
+  FVIM_ERR_NOT_CONVERGED = -5, /* iteration cap reached before the tolerance       */
+  FVIM_ERR_TIMEOUT = -6,       /* bounded device wait expired                      */
+  FVIM_ERR_UNSUPPORTED = -7    /* valid request this build does not support       */
+};
+
+typedef struct fvim_ctx fvim_ctx;
+
+/*
+ * fvim_create -- grid, depth nodes, periodic cell and precision (Sec. 3.1, Eq.
+ * periodic_cell).
+ *   out        receives the new context (host pointer to an opaque handle).
+ *   n1, n2     in-plane points; powers of two, 4 <= n1 <= 4096, 2 <= n2 <= 4096.
+ *   nz         depth nodes, 2 <= nz <= 512.
+ *   z_nodes    HOST array of nz depths, z_nodes[0] == 0, strictly increasing.
+ *   L1, L2     cell lengths (> 0).
+ *   precision  FVIM_FP32 or FVIM_FP64: element type of every array argument.
+ *   stream     cudaStream_t to enqueue on (NULL = legacy default stream).
+ * The context allocates its scratch on the current CUDA device (FVIM_ERR_OOM if
+ * that fails).  Material defaults: E = 1, nu = 0.3, sigma_y = inf, E_h = 0.
+ */
+int fvim_create(fvim_ctx** out, int n1, int n2, int nz, const double* z_nodes,
+                double L1, double L2, int precision, void* stream);
+
+/* fvim_set_material -- isotropic C(E, nu) and linear hardening f_h = sigma_y + E_h e_p
+ * (Sec. 4.1).  E > 0, -1 < nu < 0.5, sigma_y > 0, E_h >= 0. */
+int fvim_set_material(fvim_ctx* ctx, double E, double nu, double sigma_y, double E_h);
+
+/* fvim_set_stream -- change the stream later calls are enqueued on. */
+int fvim_set_stream(fvim_ctx* ctx, void* stream);
+
+/*
+ * fvim_apply_mindlin -- the Mindlin operator (Eq. N:conv, Thm 1, Eq. 2gradient,
+ * Eq. jump, Eq. mindlin_B_U) applied to the eigenstress w = C:eps_p.
+ *   eps_p       device, [Nz][6][N2][N1], plastic strain (input, not modified).
+ *   out         device, [Nz][6][N2][N1]: sigma = C:grad^sym N[w] - w (FVIM_STRESS,
+ *               Sec. 6.1) or grad^sym N[w] (FVIM_STRAIN).  May not alias eps_p.
+ *   out_kind    FVIM_STRESS or FVIM_STRAIN.
+ *   u3_surface  device [N2][N1] or NULL: surface normal displacement N[w].e3 at z = 0
+ *               (mode k = 0 set to zero, Rem. fundamental_mode).
+ * Modes k1 = N1/2 or k2 = N2/2 (not in Z^2_N, Sec. 3.1) carry no operator term.
+ */
+int fvim_apply_mindlin(fvim_ctx* ctx, const void* eps_p, void* out, int out_kind, void* u3_surface);
+
+/*
+ * fvim_apply_boussinesq -- the Boussinesq operator M[p] for a normal surface pressure
+ * (Eq. M:conv, Eq. B:fourier).
+ *   p           device [N2][N1] pressure (input).
+ *   u3_surface  device [N2][N1] or NULL: u3 = M[p].e3 at z = 0, u3_hat = 2 p_hat/(E* q),
+ *               mode 0 set to zero.
+ *   vol_out     device [Nz][6][N2][N1] or NULL: C:grad^sym M[p] (FVIM_STRESS) or
+ *               grad^sym M[p] (FVIM_STRAIN) at every node.
+ */
+int fvim_apply_boussinesq(fvim_ctx* ctx, const void* p, void* u3_surface, void* vol_out, int out_kind);
+
+/*
+ * fvim_return_map -- J2 radial return with linear isotropic hardening (Sec. 4.1) for
+ * a strain increment, from the context's plastic state (sigma_n, e_p).  The state is
+ * read, not updated (fvim_commit_state updates it).
+ *   d_eps    device [Nz][6][N2][N1] total strain increment (input).
+ *   d_eps_p  device [Nz][6][N2][N1] plastic strain increment (output).
+ *   d_ep     device [Nz][N2][N1] increment of cumulated plastic strain (output) or NULL.
+ */
+int fvim_return_map(fvim_ctx* ctx, const void* d_eps, void* d_eps_p, void* d_ep);
+
+/* fvim_commit_state -- S_{n+1} = S_n + increment: sigma_n += C:(d_eps - d_eps_p),
+ * e_p += d_ep (Sec. 4.2 update(S)).  d_eps, d_eps_p: [Nz][6][N2][N1]; d_ep: [Nz][N2][N1]. */
+int fvim_commit_state(fvim_ctx* ctx, const void* d_eps, const void* d_eps_p, const void* d_ep);
+
+/* fvim_get_state / fvim_set_state -- device-to-device copies of the plastic state:
+ * eps_p [Nz][6][N2][N1] (accumulated plastic strain), e_p [Nz][N2][N1],
+ * sigma [Nz][6][N2][N1].  Any pointer may be NULL to skip that field. */
+int fvim_get_state(fvim_ctx* ctx, void* eps_p, void* e_p, void* sigma);
+int fvim_set_state(fvim_ctx* ctx, const void* eps_p, const void* e_p, const void* sigma);
+
+/* fvim_sync -- wait for the context's stream; returns FVIM_ERR_CUDA on a device error. */
+int fvim_sync(fvim_ctx* ctx);
+
+/* fvim_destroy -- free the context and its scratch (synchronises its stream). */
+int fvim_destroy(fvim_ctx* ctx);
+
+/* fvim_strerror -- static description of a status code. */
+const char* fvim_strerror(int status);
+
+/* fvim_last_kernel_count -- number of kernels the last entry point launched. */
+int fvim_last_kernel_count(const fvim_ctx* ctx);
+
+/*
+ * Kernel timing.  While enabled, every kernel the context launches is bracketed by
+ * two CUDA events recorded on the context's stream.  fvim_profile_read synchronises
+ * the stream, adds up the elapsed times per kernel kind and clears the records:
+ *   total_ms[s], launches[s] for s < nslots (host arrays), slot names from
+ *   fvim_profile_name(s) (NULL past the last slot).
+ */
+int fvim_profile_enable(fvim_ctx* ctx, int on);
+int fvim_profile_read(fvim_ctx* ctx, double* total_ms, int* launches, int nslots);
+const char* fvim_profile_name(int slot);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FVIM_H */

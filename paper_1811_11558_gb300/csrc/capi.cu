@@ -1,0 +1,396 @@
+// C ABI of libfvim (declarations and argument contracts in include/fvim.h).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "fvim_internal.cuh"
+
+namespace {
+
+// J2 radial return with linear isotropic hardening (Sec. 4.1), one thread per voxel.
+template <typename T>
+__global__ void k_return_map(const T* __restrict__ d_eps, const T* __restrict__ sig_n, const T* __restrict__ ep,
+                             T* __restrict__ d_eps_p, T* __restrict__ d_ep, size_t nxy, size_t nvox, T lam, T mu,
+                             T sy, T Eh) {
+  const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nvox) return;
+  const size_t z = v / nxy, xy = v - z * nxy;
+  const size_t base = z * 6 * nxy + xy;
+  T de[6], st[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    de[c] = d_eps[base + c * nxy];
+    st[c] = sig_n[base + c * nxy];
+  }
+  const T tr = de[0] + de[1] + de[2];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) st[c] += 2 * mu * de[c];
+  st[0] += lam * tr;
+  st[1] += lam * tr;
+  st[2] += lam * tr;
+  const T m = (st[0] + st[1] + st[2]) / (T)3;
+  T s[6] = {st[0] - m, st[1] - m, st[2] - m, st[3], st[4], st[5]};
+  const T nrm2 = s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + 2 * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
+  const T fy = sqrt((T)1.5 * nrm2);
+  const T f = fy - (sy + Eh * ep[v]);
+  T dEp = 0, k = 0;
+  if (f > 0) {
+    dEp = f / ((T)3 * mu + Eh);
+    k = (T)1.5 * dEp / fy;
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) d_eps_p[base + c * nxy] = k * s[c];
+  if (d_ep) d_ep[v] = dEp;
+}
+
+// S_{n+1} = S_n + increment (Sec. 4.2, update(S)).
+template <typename T>
+__global__ void k_commit(const T* __restrict__ d_eps, const T* __restrict__ d_eps_p, const T* __restrict__ d_ep,
+                         T* __restrict__ sig, T* __restrict__ eps_p, T* __restrict__ ep, size_t nxy, size_t nvox,
+                         T lam, T mu) {
+  const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nvox) return;
+  const size_t z = v / nxy, xy = v - z * nxy;
+  const size_t base = z * 6 * nxy + xy;
+  T ee[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const T dp = d_eps_p[base + c * nxy];
+    ee[c] = d_eps[base + c * nxy] - dp;
+    eps_p[base + c * nxy] += dp;
+  }
+  const T tr = ee[0] + ee[1] + ee[2];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) sig[base + c * nxy] += 2 * mu * ee[c] + (c < 3 ? lam * tr : (T)0);
+  if (d_ep) ep[v] += d_ep[v];
+}
+
+struct ProfState {
+  bool on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[PROF_NSLOTS];
+};
+
+const char* kProfNames[PROF_NSLOTS] = {"rows_fwd6", "cols_fwd", "mindlin_depth", "cols_inv", "rows_inv6",
+                                       "rows_fwd1", "rows_inv1", "boussinesq", "return_map", "commit"};
+
+// run one launcher, bracketed by events when profiling is on
+template <typename F> int timed(fvim_ctx* c, int slot, int& nk, F&& launch) {
+  ProfState* ps = (ProfState*)c->prof;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (ps && ps->on) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, c->stream);
+  }
+  const int rc = launch();
+  if (a) {
+    cudaEventRecord(b, c->stream);
+    ps->ev[slot].push_back({a, b});
+  }
+  if (rc == FVIM_OK) ++nk;
+  return rc;
+}
+
+size_t elem_size(const fvim_ctx* c) { return c->prec == FVIM_FP64 ? 8 : 4; }
+size_t nvox(const fvim_ctx* c) { return (size_t)c->nz * c->n2 * c->n1; }
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+void free_all(fvim_ctx* c) {
+  void* bufs[] = {c->z_dev, c->tw1, c->tw2, c->spec, c->nq, c->surf, c->surf_nq, c->st_eps_p, c->st_ep, c->st_sig};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  free(c->z_host);
+  ProfState* ps = (ProfState*)c->prof;
+  if (ps) {
+    for (auto& v : ps->ev)
+      for (auto& e : v) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    delete ps;
+    c->prof = nullptr;
+  }
+}
+
+template <typename T> int upload_twiddles(void** dst, int n) {
+  typedef typename Cx<T>::t V;
+  std::vector<V> h(n);
+  for (int k = 0; k < n; ++k) {
+    const double a = -6.283185307179586476925 * (double)k / (double)n;
+    h[k] = mk<V>((T)cos(a), (T)sin(a));
+  }
+  if (cudaMalloc(dst, n * sizeof(V)) != cudaSuccess) return FVIM_ERR_OOM;
+  if (cudaMemcpy(*dst, h.data(), n * sizeof(V), cudaMemcpyHostToDevice) != cudaSuccess) return FVIM_ERR_CUDA;
+  return FVIM_OK;
+}
+
+template <typename T> int upload_nodes(fvim_ctx* c) {
+  std::vector<T> h(c->nz);
+  for (int i = 0; i < c->nz; ++i) h[i] = (T)c->z_host[i];
+  if (cudaMalloc(&c->z_dev, c->nz * sizeof(T)) != cudaSuccess) return FVIM_ERR_OOM;
+  if (cudaMemcpy(c->z_dev, h.data(), c->nz * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return FVIM_ERR_CUDA;
+  return FVIM_OK;
+}
+
+template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, int kind, T* u3) {
+  int rc;
+  int nk = 0;
+  if ((rc = timed(c, PROF_ROWS_FWD6, nk, [&] { return launch_rows_fwd6<T>(c, eps_p, 0, c->nz); }))) return rc;
+  if ((rc = timed(c, PROF_COLS_FWD, nk, [&] { return launch_cols<T>(c, false, c->spec, c->nz * 6); }))) return rc;
+  if ((rc = timed(c, PROF_MINDLIN_DEPTH, nk, [&] { return launch_mindlin_depth<T>(c, kind, u3 != nullptr); })))
+    return rc;
+  if ((rc = timed(c, PROF_COLS_INV, nk, [&] { return launch_cols<T>(c, true, c->spec, c->nz * 6); }))) return rc;
+  if ((rc = timed(c, PROF_ROWS_INV6, nk, [&] {
+         return launch_rows_inv6<T>(c, out, kind == FVIM_STRESS ? (T)-1 : (T)0, 0, c->nz);
+       })))
+    return rc;
+  if (u3) {
+    if ((rc = timed(c, PROF_COLS_INV, nk, [&] { return launch_cols<T>(c, true, c->surf, 1); }))) return rc;
+    if ((rc = timed(c, PROF_ROWS_INV1, nk, [&] { return launch_rows_inv1<T>(c, u3); }))) return rc;
+  }
+  c->last_kernels = nk;
+  return FVIM_OK;
+}
+
+template <typename T> int apply_boussinesq_t(fvim_ctx* c, const T* p, T* u3, T* vol, int kind) {
+  int rc;
+  int nk = 0;
+  if ((rc = timed(c, PROF_ROWS_FWD1, nk, [&] { return launch_rows_fwd1<T>(c, p); }))) return rc;
+  if ((rc = timed(c, PROF_COLS_FWD, nk, [&] { return launch_cols<T>(c, false, c->surf, 1); }))) return rc;
+  if ((rc = timed(c, PROF_BOUSSINESQ, nk,
+                  [&] { return launch_boussinesq<T>(c, kind, vol != nullptr, u3 != nullptr); })))
+    return rc;
+  if (vol) {
+    if ((rc = timed(c, PROF_COLS_INV, nk, [&] { return launch_cols<T>(c, true, c->spec, c->nz * 6); }))) return rc;
+    if ((rc = timed(c, PROF_ROWS_INV6, nk, [&] { return launch_rows_inv6<T>(c, vol, (T)0, 0, c->nz); }))) return rc;
+  }
+  if (u3) {
+    if ((rc = timed(c, PROF_COLS_INV, nk, [&] { return launch_cols<T>(c, true, c->surf, 1); }))) return rc;
+    if ((rc = timed(c, PROF_ROWS_INV1, nk, [&] { return launch_rows_inv1<T>(c, u3); }))) return rc;
+  }
+  c->last_kernels = nk;
+  return FVIM_OK;
+}
+
+template <typename T> int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep) {
+  const size_t nv = nvox(c);
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((nv + threads - 1) / threads);
+  int nk = 0;
+  const int rc = timed(c, PROF_RETURN_MAP, nk, [&] {
+    k_return_map<T><<<blocks, threads, 0, c->stream>>>(d_eps, (const T*)c->st_sig, (const T*)c->st_ep, d_eps_p, d_ep,
+                                                       (size_t)c->n1 * c->n2, nv, (T)c->lam, (T)c->mu,
+                                                       (T)c->sigma_y, (T)c->E_h);
+    FVIM_CUDA_CHECK_LAUNCH();
+    return FVIM_OK;
+  });
+  c->last_kernels = nk;
+  return rc;
+}
+
+template <typename T> int commit_t(fvim_ctx* c, const T* d_eps, const T* d_eps_p, const T* d_ep) {
+  const size_t nv = nvox(c);
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((nv + threads - 1) / threads);
+  int nk = 0;
+  const int rc = timed(c, PROF_COMMIT, nk, [&] {
+    k_commit<T><<<blocks, threads, 0, c->stream>>>(d_eps, d_eps_p, d_ep, (T*)c->st_sig, (T*)c->st_eps_p,
+                                                   (T*)c->st_ep, (size_t)c->n1 * c->n2, nv, (T)c->lam, (T)c->mu);
+    FVIM_CUDA_CHECK_LAUNCH();
+    return FVIM_OK;
+  });
+  c->last_kernels = nk;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fvim_strerror(int s) {
+  switch (s) {
+    case FVIM_OK: return "ok";
+    case FVIM_ERR_ARG: return "invalid argument";
+    case FVIM_ERR_OOM: return "device allocation failed";
+    case FVIM_ERR_CUDA: return "CUDA error";
+    case FVIM_ERR_NONFINITE: return "non-finite value";
+    case FVIM_ERR_NOT_CONVERGED: return "not converged";
+    case FVIM_ERR_TIMEOUT: return "bounded wait expired";
+    case FVIM_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+int fvim_create(fvim_ctx** out, int n1, int n2, int nz, const double* z_nodes, double L1, double L2, int precision,
+                void* stream) {
+  if (!out) return FVIM_ERR_ARG;
+  *out = nullptr;
+  if (!is_pow2(n1) || !is_pow2(n2) || n1 < 4 || n2 < 2 || n1 > 1024 || n2 > 1024) return FVIM_ERR_ARG;
+  if (nz < 2 || nz > 512 || !z_nodes) return FVIM_ERR_ARG;
+  if (!(L1 > 0) || !(L2 > 0)) return FVIM_ERR_ARG;
+  if (precision != FVIM_FP32 && precision != FVIM_FP64) return FVIM_ERR_ARG;
+  if (z_nodes[0] != 0.0) return FVIM_ERR_ARG;
+  for (int i = 1; i < nz; ++i)
+    if (!(z_nodes[i] > z_nodes[i - 1]) || !isfinite(z_nodes[i])) return FVIM_ERR_ARG;
+  fvim_ctx* c = new (std::nothrow) fvim_ctx();
+  if (!c) return FVIM_ERR_OOM;
+  memset(c, 0, sizeof(*c));
+  c->n1 = n1;
+  c->n2 = n2;
+  c->nz = nz;
+  c->h1 = n1 / 2;
+  c->prec = precision;
+  c->L1 = L1;
+  c->L2 = L2;
+  c->stream = (cudaStream_t)stream;
+  cudaGetDevice(&c->device);
+  c->z_host = (double*)malloc(nz * sizeof(double));
+  if (!c->z_host) { delete c; return FVIM_ERR_OOM; }
+  memcpy(c->z_host, z_nodes, nz * sizeof(double));
+  const double h = z_nodes[1] - z_nodes[0];
+  c->uniform = 1;
+  for (int i = 1; i < nz; ++i)
+    if (fabs((z_nodes[i] - z_nodes[i - 1]) - h) > 1e-12 * fabs(z_nodes[nz - 1])) c->uniform = 0;
+  c->hz = h;
+  fvim_set_material(c, 1.0, 0.3, INFINITY, 0.0);
+  int rc;
+  const size_t es = precision == FVIM_FP64 ? 8 : 4;
+  const size_t cs = 2 * es;
+  if (precision == FVIM_FP64) {
+    if ((rc = upload_twiddles<double>(&c->tw1, n1)) || (rc = upload_twiddles<double>(&c->tw2, n2)) ||
+        (rc = upload_nodes<double>(c))) { free_all(c); delete c; return rc; }
+  } else {
+    if ((rc = upload_twiddles<float>(&c->tw1, n1)) || (rc = upload_twiddles<float>(&c->tw2, n2)) ||
+        (rc = upload_nodes<float>(c))) { free_all(c); delete c; return rc; }
+  }
+  const size_t nv = nvox(c);
+  struct { void** p; size_t bytes; } al[] = {
+      {&c->spec, (size_t)nz * 6 * n2 * c->h1 * cs}, {&c->nq, (size_t)nz * 6 * n2 * es},
+      {&c->surf, (size_t)n2 * c->h1 * cs},          {&c->surf_nq, (size_t)n2 * es},
+      {&c->st_eps_p, nv * 6 * es},                   {&c->st_ep, nv * es},
+      {&c->st_sig, nv * 6 * es}};
+  for (auto& a : al) {
+    if (cudaMalloc(a.p, a.bytes) != cudaSuccess) { cudaGetLastError(); free_all(c); delete c; return FVIM_ERR_OOM; }
+    if (cudaMemset(*a.p, 0, a.bytes) != cudaSuccess) { free_all(c); delete c; return FVIM_ERR_CUDA; }
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) { free_all(c); delete c; return FVIM_ERR_CUDA; }
+  *out = c;
+  return FVIM_OK;
+}
+
+int fvim_set_material(fvim_ctx* c, double E, double nu, double sigma_y, double E_h) {
+  if (!c) return FVIM_ERR_ARG;
+  if (!(E > 0) || !(nu > -1.0 && nu < 0.5) || !(sigma_y > 0) || !(E_h >= 0)) return FVIM_ERR_ARG;
+  c->E = E;
+  c->nu = nu;
+  c->sigma_y = sigma_y;
+  c->E_h = E_h;
+  c->mu = E / (2.0 * (1.0 + nu));
+  c->lam = 2.0 * c->mu * nu / (1.0 - 2.0 * nu);
+  return FVIM_OK;
+}
+
+int fvim_set_stream(fvim_ctx* c, void* stream) {
+  if (!c) return FVIM_ERR_ARG;
+  c->stream = (cudaStream_t)stream;
+  return FVIM_OK;
+}
+
+int fvim_apply_mindlin(fvim_ctx* c, const void* eps_p, void* out, int out_kind, void* u3) {
+  if (!c || !eps_p || !out || eps_p == out) return FVIM_ERR_ARG;
+  if (out_kind != FVIM_STRESS && out_kind != FVIM_STRAIN) return FVIM_ERR_ARG;
+  c->last_kernels = 0;
+  if (c->prec == FVIM_FP64) return apply_mindlin_t<double>(c, (const double*)eps_p, (double*)out, out_kind, (double*)u3);
+  return apply_mindlin_t<float>(c, (const float*)eps_p, (float*)out, out_kind, (float*)u3);
+}
+
+int fvim_apply_boussinesq(fvim_ctx* c, const void* p, void* u3, void* vol, int out_kind) {
+  if (!c || !p || (!u3 && !vol)) return FVIM_ERR_ARG;
+  if (out_kind != FVIM_STRESS && out_kind != FVIM_STRAIN) return FVIM_ERR_ARG;
+  c->last_kernels = 0;
+  if (c->prec == FVIM_FP64)
+    return apply_boussinesq_t<double>(c, (const double*)p, (double*)u3, (double*)vol, out_kind);
+  return apply_boussinesq_t<float>(c, (const float*)p, (float*)u3, (float*)vol, out_kind);
+}
+
+int fvim_return_map(fvim_ctx* c, const void* d_eps, void* d_eps_p, void* d_ep) {
+  if (!c || !d_eps || !d_eps_p || d_eps == d_eps_p) return FVIM_ERR_ARG;
+  if (!isfinite(c->sigma_y)) return FVIM_ERR_ARG;
+  if (c->prec == FVIM_FP64) return return_map_t<double>(c, (const double*)d_eps, (double*)d_eps_p, (double*)d_ep);
+  return return_map_t<float>(c, (const float*)d_eps, (float*)d_eps_p, (float*)d_ep);
+}
+
+int fvim_commit_state(fvim_ctx* c, const void* d_eps, const void* d_eps_p, const void* d_ep) {
+  if (!c || !d_eps || !d_eps_p) return FVIM_ERR_ARG;
+  if (c->prec == FVIM_FP64)
+    return commit_t<double>(c, (const double*)d_eps, (const double*)d_eps_p, (const double*)d_ep);
+  return commit_t<float>(c, (const float*)d_eps, (const float*)d_eps_p, (const float*)d_ep);
+}
+
+int fvim_get_state(fvim_ctx* c, void* eps_p, void* e_p, void* sigma) {
+  if (!c) return FVIM_ERR_ARG;
+  const size_t es = elem_size(c), nv = nvox(c);
+  if (eps_p && cudaMemcpyAsync(eps_p, c->st_eps_p, nv * 6 * es, cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
+  if (e_p && cudaMemcpyAsync(e_p, c->st_ep, nv * es, cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
+  if (sigma && cudaMemcpyAsync(sigma, c->st_sig, nv * 6 * es, cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
+  return FVIM_OK;
+}
+
+int fvim_set_state(fvim_ctx* c, const void* eps_p, const void* e_p, const void* sigma) {
+  if (!c) return FVIM_ERR_ARG;
+  const size_t es = elem_size(c), nv = nvox(c);
+  if (eps_p && cudaMemcpyAsync(c->st_eps_p, eps_p, nv * 6 * es, cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
+  if (e_p && cudaMemcpyAsync(c->st_ep, e_p, nv * es, cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
+  if (sigma && cudaMemcpyAsync(c->st_sig, sigma, nv * 6 * es, cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
+  return FVIM_OK;
+}
+
+int fvim_sync(fvim_ctx* c) {
+  if (!c) return FVIM_ERR_ARG;
+  return cudaStreamSynchronize(c->stream) == cudaSuccess ? FVIM_OK : FVIM_ERR_CUDA;
+}
+
+int fvim_destroy(fvim_ctx* c) {
+  if (!c) return FVIM_ERR_ARG;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+  return FVIM_OK;
+}
+
+int fvim_last_kernel_count(const fvim_ctx* c) { return c ? c->last_kernels : 0; }
+
+int fvim_profile_enable(fvim_ctx* c, int on) {
+  if (!c) return FVIM_ERR_ARG;
+  if (!c->prof) {
+    c->prof = new (std::nothrow) ProfState();
+    if (!c->prof) return FVIM_ERR_OOM;
+  }
+  ((ProfState*)c->prof)->on = on != 0;
+  return FVIM_OK;
+}
+
+int fvim_profile_read(fvim_ctx* c, double* total_ms, int* launches, int nslots) {
+  if (!c || nslots < 0 || (nslots && (!total_ms || !launches))) return FVIM_ERR_ARG;
+  for (int s = 0; s < nslots; ++s) { total_ms[s] = 0; launches[s] = 0; }
+  ProfState* ps = (ProfState*)c->prof;
+  if (!ps) return FVIM_OK;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
+  for (int s = 0; s < PROF_NSLOTS; ++s) {
+    for (auto& e : ps->ev[s]) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e.first, e.second);
+      if (s < nslots) { total_ms[s] += ms; launches[s] += 1; }
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    ps->ev[s].clear();
+  }
+  return FVIM_OK;
+}
+
+const char* fvim_profile_name(int slot) { return (slot >= 0 && slot < PROF_NSLOTS) ? kProfNames[slot] : nullptr; }
+
+}  // extern "C"

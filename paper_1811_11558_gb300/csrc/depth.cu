@@ -1,0 +1,596 @@
+// Per-wavevector depth operators of the discretised Mindlin and Boussinesq operators.
+//
+// For one in-plane mode q = 2 pi (k1/L1, k2/L2) the Mindlin displacement gradient at the
+// depth node x3^i is (Eq. 2gradient, Eq. jump, Eq. mindlin_B_U, Thm 1)
+//   grad N[w](q, x3^i) = - int grad^2 U_inf(-q, y3 - x3^i) : w_h(q, y3) dy3
+//                        - ([[grad U_inf]] : w(q, x3^i)) x e3  +  image term,
+// with w_h the piecewise-linear interpolant of the nodal coefficients (Sec. 3.2).
+//
+// GB300 formulation (the paper's element integrals, evaluated exactly, reorganised):
+// * Frame: the tensors are rotated so that q lies along x1; with Delta(-q) = (-i, 0, 0)
+//   every kernel coefficient of Table 1 becomes a constant and the contraction of the
+//   4th-order kernels with w collapses to five rotated components of w plus one scalar
+//   (Delta^+-.w.Delta^+-) per branch; the in-plane component perpendicular to q has no
+//   strain (eps_pp = 0).
+// * Depth integral: the g0/g1 kernels are exponentials exp(-q|y3 - x3|) times
+//   polynomials, so the integrals over all elements above (g^- branch) and below (g^+
+//   branch) of node i follow from those of node i-1 / i+1 by the exact one-element
+//   recursions  M0 <- e^{-qh} M0 + element,  M1 <- e^{-qh}(M1 -+ qh M0) + element,
+//   with the linear-element integrals of Eq. (int_g0)/(int_g1) in closed form.  This
+//   replaces the cutoff of Sec. 3.2 (no approximation) and costs O(Nz) per mode.
+// * Parallelism: a CTA holds KT consecutive k1 columns (one k2) for all depth nodes in
+//   shared memory; the depth range is cut into chunks of C nodes, one thread per
+//   (chunk, k1).  Each chunk first computes its local contribution (from zero), the
+//   carries of the two recursions are folded across chunks in shared memory, then every
+//   chunk re-runs its recursion from the exact carries and writes its nodes.
+// * Image term: the surface traction of the full-space field needs the + branch at
+//   x3 = 0, i.e. the fully folded carry; the cancelling Boussinesq field is then a
+//   closed form exp(-q z)(P + q z Q) in the rotated frame.
+// * q = 0 (mode k = 0): laminate solution (sigma_i3 = 0, eps_ab = 0).  k2 = N2/2
+//   (not in Z^2_N): no operator term, so sigma_hat = -w_hat (stress) or 0 (strain).
+#include "fvim_internal.cuh"
+
+namespace {
+
+constexpr int KT_MAX = 16;  // k1 columns per CTA (128-byte rows in FP32)
+
+template <typename T> __device__ __forceinline__ T dexp(T x);
+template <> __device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
+
+// Linear-element integrals of Eq. (int_g0)/(int_g1): with a = q h,
+//   I_n(a) = int_0^1 s^n exp(-a s) ds,  n = 0, 1, 2,
+// closed form for a above a threshold, Taylor series below it (no cancellation).
+template <typename T> struct Elem {
+  T E, a, h, hI0mI1, hI1, ahI1mI2, ahI2;
+};
+
+template <typename T> __device__ __forceinline__ Elem<T> elem_coef(T q, T h) {
+  Elem<T> c;
+  const T a = q * h;
+  const T E = dexp<T>(-a);
+  T I0, I1, I2;
+  const T thr = sizeof(T) == 4 ? (T)1.0 : (T)0.5;
+  if (a < thr) {
+    const int M = sizeof(T) == 4 ? 12 : 18;
+    T t = 1, s0 = 0, s1 = 0, s2 = 0;
+    for (int m = 0; m < M; ++m) {
+      s0 += t / (T)(m + 1);
+      s1 += t / (T)(m + 2);
+      s2 += t / (T)(m + 3);
+      t *= -a / (T)(m + 1);
+    }
+    I0 = s0; I1 = s1; I2 = s2;
+  } else {
+    const T ia = (T)1 / a;
+    I0 = ((T)1 - E) * ia;
+    I1 = ((T)1 - E * ((T)1 + a)) * ia * ia;
+    I2 = ((T)2 - E * (a * a + (T)2 * a + (T)2)) * ia * ia * ia;
+  }
+  c.E = E;
+  c.a = a;
+  c.h = h;
+  c.hI0mI1 = h * (I0 - I1);
+  c.hI1 = h * I1;
+  c.ahI1mI2 = a * h * (I1 - I2);
+  c.ahI2 = a * h * I2;
+  return c;
+}
+
+// moments of one branch: m = int g0 w_h for the rotated components
+// (qq, 33, p3, q3, qp); n = int g1 (D.w_h.D) with D = Delta^{+-}(-q) in the rotated frame
+template <typename V> struct Mom {
+  V m[5];
+  V n;
+};
+
+// rotated storage order: 0 qq, 1 pp, 2 33, 3 p3, 4 q3, 5 qp; moment j -> rotated j ? j + 1 : 0
+
+template <typename V> __device__ __forceinline__ void mom_zero(Mom<V>& M) {
+#pragma unroll
+  for (int j = 0; j < 5; ++j) M.m[j] = mk<V>(0, 0);
+  M.n = mk<V>(0, 0);
+}
+
+// scalar Delta^-.X.Delta^- (A branch, sgn = -1) or Delta^+.X.Delta^+ (P branch, sgn = +1)
+// for the rotated components qq, 33, q3:  -X_qq + X_33 + sgn 2i X_q3
+template <typename V> __device__ __forceinline__ V nscal(V qq, V z33, V q3, int sgn) {
+  V r = csub(z33, qq);
+  V t = cmuli(q3);
+  return sgn > 0 ? caxpy(r, (decltype(V::x))2, t) : caxpy(r, (decltype(V::x))-2, t);
+}
+
+// forward step of the g^- moments from node i to node i+1 over element [i, i+1]
+template <typename T, typename V>
+__device__ __forceinline__ void stepA(Mom<V>& A, const Elem<T>& c, const V* wi, const V* wj) {
+  const V n_old = nscal(A.m[0], A.m[1], A.m[3], -1);
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const int r = (j == 0) ? 0 : j + 1;
+    V v = cscale(A.m[j], c.E);
+    v = caxpy(v, c.hI1, wi[r]);
+    v = caxpy(v, c.hI0mI1, wj[r]);
+    A.m[j] = v;
+  }
+  const V ni = nscal(wi[0], wi[2], wi[4], -1);
+  const V nj = nscal(wj[0], wj[2], wj[4], -1);
+  V v = cscale(caxpy(A.n, -c.a, n_old), c.E);
+  v = caxpy(v, -c.ahI2, ni);
+  v = caxpy(v, -c.ahI1mI2, nj);
+  A.n = v;
+}
+
+// backward step of the g^+ moments from node i+1 to node i over element [i, i+1]
+template <typename T, typename V>
+__device__ __forceinline__ void stepP(Mom<V>& P, const Elem<T>& c, const V* wi, const V* wj) {
+  const V n_old = nscal(P.m[0], P.m[1], P.m[3], +1);
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const int r = (j == 0) ? 0 : j + 1;
+    V v = cscale(P.m[j], c.E);
+    v = caxpy(v, c.hI0mI1, wi[r]);
+    v = caxpy(v, c.hI1, wj[r]);
+    P.m[j] = v;
+  }
+  const V ni = nscal(wi[0], wi[2], wi[4], +1);
+  const V nj = nscal(wj[0], wj[2], wj[4], +1);
+  V v = cscale(caxpy(P.n, c.a, n_old), c.E);
+  v = caxpy(v, c.ahI1mI2, ni);
+  v = caxpy(v, c.ahI2, nj);
+  P.n = v;
+}
+
+// propagate a branch across a depth span with a = q * span (no source inside)
+template <typename T, typename V>
+__device__ __forceinline__ void propA(Mom<V>& A, T a) {
+  const T E = dexp<T>(-a);
+  const V n0 = nscal(A.m[0], A.m[1], A.m[3], -1);
+  A.n = cscale(caxpy(A.n, -a, n0), E);
+#pragma unroll
+  for (int j = 0; j < 5; ++j) A.m[j] = cscale(A.m[j], E);
+}
+template <typename T, typename V>
+__device__ __forceinline__ void propP(Mom<V>& P, T a) {
+  const T E = dexp<T>(-a);
+  const V n0 = nscal(P.m[0], P.m[1], P.m[3], +1);
+  P.n = cscale(caxpy(P.n, a, n0), E);
+#pragma unroll
+  for (int j = 0; j < 5; ++j) P.m[j] = cscale(P.m[j], E);
+}
+template <typename V> __device__ __forceinline__ void mom_add(Mom<V>& a, const Mom<V>& b) {
+#pragma unroll
+  for (int j = 0; j < 5; ++j) a.m[j] = cadd(a.m[j], b.m[j]);
+  a.n = cadd(a.n, b.n);
+}
+
+// Kelvin part of the strain (full-space field, Eq. 2gradient + Eq. jump) in the rotated
+// frame from the two branch moments and the nodal eigenstress w (rotated, 6 comps).
+template <typename T, typename V>
+__device__ __forceinline__ void kelvin_strain(const Mom<V>& A, const Mom<V>& P, const V* w, T q, T nu, T mu,
+                                              V* e) {
+  const T K = (T)1 / ((T)8 * mu * (nu - (T)1));
+  const V S0 = cadd(A.m[0], P.m[0]), S2 = cadd(A.m[1], P.m[1]), S3 = cadd(A.m[2], P.m[2]);
+  const V S4 = cadd(A.m[3], P.m[3]), S5 = cadd(A.m[4], P.m[4]);
+  const V D0 = csub(A.m[0], P.m[0]), D2 = csub(A.m[1], P.m[1]), D3 = csub(A.m[2], P.m[2]);
+  const V D4 = csub(A.m[3], P.m[3]), D5 = csub(A.m[4], P.m[4]);
+  const V An = A.n, Pn = P.n;
+  // eps_qq = q K [(4nu-3) S0 + S2 + 4i(nu-1) D4 + An - Pn]
+  V t = cscale(S0, (T)4 * nu - (T)3);
+  t = cadd(t, S2);
+  t = caxpy(t, (T)4 * (nu - (T)1), cmuli(D4));
+  t = cadd(t, csub(An, Pn));
+  e[0] = cscale(t, q * K);
+  e[1] = mk<V>(0, 0);
+  // eps_33 = K [q (S0 - (4nu-1) S2 + 4i nu D4 - An + Pn) + 4(2nu-1) w33]
+  t = caxpy(S0, -((T)4 * nu - (T)1), S2);
+  t = caxpy(t, (T)4 * nu, cmuli(D4));
+  t = cadd(t, csub(Pn, An));
+  t = cscale(t, q);
+  t = caxpy(t, (T)4 * ((T)2 * nu - (T)1), w[2]);
+  e[2] = cscale(t, K);
+  // eps_p3 = (q(-S3 + i D5) + 2 w_p3) / (4 mu)
+  t = csub(cmuli(D5), S3);
+  t = cscale(t, q);
+  t = caxpy(t, (T)2, w[3]);
+  e[3] = cscale(t, (T)1 / ((T)4 * mu));
+  // eps_q3 = K [q(i(2(nu-1) D0 + 2 nu D2 + An + Pn) + 2 S4) + 4(nu-1) w_q3]
+  V u = cscale(D0, (T)2 * (nu - (T)1));
+  u = caxpy(u, (T)2 * nu, D2);
+  u = cadd(u, cadd(An, Pn));
+  t = caxpy(cmuli(u), (T)2, S4);
+  t = cscale(t, q);
+  t = caxpy(t, (T)4 * (nu - (T)1), w[4]);
+  e[4] = cscale(t, K);
+  // eps_qp = q (i D3 + S5) / (4 mu)
+  t = cadd(cmuli(D3), S5);
+  e[5] = cscale(t, q / ((T)4 * mu));
+}
+
+// strain of the Boussinesq-Cerruti field of a surface traction t (rotated frame, force on
+// the body per unit area, Eq. B:fourier with its gradient recurrence) at zeta = q z
+template <typename T, typename V>
+__device__ __forceinline__ void bous_strain_add(const V* tr, T zeta, T nu, T mu, V* e) {
+  const T ex = dexp<T>(-zeta);
+  const T c1 = ex / mu, c2 = ex / ((T)2 * mu);
+  const V t0 = tr[0], t1 = tr[1], t2 = tr[2];
+  const V it0 = cmuli(t0), it1 = cmuli(t1), it2 = cmuli(t2);
+  // qq: ((1-nu) i t0 + (nu - 1/2) t2 + zeta(-i t0/2 + t2/2)) / mu
+  V v = cscale(it0, (T)1 - nu);
+  v = caxpy(v, nu - (T)0.5, t2);
+  v = caxpy(v, (T)-0.5 * zeta, it0);
+  v = caxpy(v, (T)0.5 * zeta, t2);
+  e[0] = caxpy(e[0], c1, v);
+  // 33: (-2 i nu t0 + (2nu-1) t2 + zeta (i t0 - t2)) / (2 mu)
+  v = cscale(it0, (T)-2 * nu);
+  v = caxpy(v, (T)2 * nu - (T)1, t2);
+  v = caxpy(v, zeta, csub(it0, t2));
+  e[2] = caxpy(e[2], c2, v);
+  // p3: -t1 / (2 mu) ; qp: i t1 / (2 mu)
+  e[3] = caxpy(e[3], -c2, t1);
+  e[5] = caxpy(e[5], c2, it1);
+  // q3: (-t0 + zeta (t0 + i t2)) / (2 mu)
+  v = caxpy(cscale(t0, (T)-1), zeta, cadd(t0, it2));
+  e[4] = caxpy(e[4], c2, v);
+}
+
+// rotate a symmetric tensor (11,22,33,23,13,12) into the (q, p, 3) frame and back
+template <typename T, typename V>
+__device__ __forceinline__ void rotate_in(V* x, T c, T s) {
+  const V X11 = x[0], X22 = x[1], X23 = x[3], X13 = x[4], X12 = x[5];
+  const T cc = c * c, ss = s * s, cs = c * s;
+  x[0] = caxpy(caxpy(cscale(X11, cc), ss, X22), (T)2 * cs, X12);
+  x[1] = caxpy(caxpy(cscale(X11, ss), cc, X22), (T)-2 * cs, X12);
+  x[3] = caxpy(cscale(X13, -s), c, X23);
+  x[4] = caxpy(cscale(X13, c), s, X23);
+  x[5] = caxpy(caxpy(cscale(X11, -cs), cs, X22), cc - ss, X12);
+}
+template <typename T, typename V>
+__device__ __forceinline__ void rotate_out(V* y, T c, T s) {
+  const V qq = y[0], pp = y[1], p3 = y[3], q3 = y[4], qp = y[5];
+  const T cc = c * c, ss = s * s, cs = c * s;
+  y[0] = caxpy(caxpy(cscale(qq, cc), ss, pp), (T)-2 * cs, qp);
+  y[1] = caxpy(caxpy(cscale(qq, ss), cc, pp), (T)2 * cs, qp);
+  y[3] = caxpy(cscale(q3, s), c, p3);
+  y[4] = caxpy(cscale(q3, c), -s, p3);
+  y[5] = caxpy(caxpy(cscale(qq, cs), -cs, pp), cc - ss, qp);
+}
+
+template <typename T> struct ModeGeom {
+  T q, c, s;
+  bool zero, nyq;
+};
+
+template <typename T>
+__device__ __forceinline__ ModeGeom<T> mode_geom(int k1, int k2, int n2, double L1, double L2) {
+  ModeGeom<T> g;
+  const int k2s = k2 < n2 / 2 ? k2 : k2 - n2;
+  g.nyq = (k2 == n2 / 2);
+  g.zero = (k1 == 0 && k2 == 0);
+  const double q1 = 6.283185307179586476925 * (double)k1 / L1;
+  const double q2 = 6.283185307179586476925 * (double)k2s / L2;
+  const double q = sqrt(q1 * q1 + q2 * q2);
+  g.q = (T)q;
+  g.c = q > 0 ? (T)(q1 / q) : (T)1;
+  g.s = q > 0 ? (T)(q2 / q) : (T)0;
+  return g;
+}
+
+// ----------------------------------------------------------------------------------
+// Mindlin depth kernel
+// grid: (h1 / KT, n2); block: KT * nch threads, thread = (chunk, k1 column)
+// smem: W[nz][6][KT] (rotated in place) + Pst[max(nz, 2 nch)][6][KT]
+// ----------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __restrict__ spec, typename Cx<T>::t* __restrict__ surf,
+                                const T* __restrict__ zn, int nz, int n2, int h1, int KT, int C, int nch, double L1,
+                                double L2, T lam, T mu, T nu, int out_kind, int want_u3, int uniform, T hz) {
+  typedef typename Cx<T>::t V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* W = reinterpret_cast<V*>(smraw);                 // [nz][6][KT]
+  V* Pst = W + (size_t)nz * 6 * KT;                   // [max(nz, 2 nch)][6][KT]
+  const int kt = threadIdx.x % KT;
+  const int ch = threadIdx.x / KT;
+  const int k1 = blockIdx.x * KT + kt;
+  const int k2 = blockIdx.y;
+  const size_t plane = (size_t)n2 * h1;
+  const size_t colofs = (size_t)k2 * h1 + blockIdx.x * KT;
+
+  // 1. load the tile (coalesced KT-wide rows)
+  for (int idx = threadIdx.x; idx < nz * 6 * KT; idx += blockDim.x) {
+    const int zc = idx / KT, j = idx - zc * KT;
+    W[idx] = spec[(size_t)zc * plane + colofs + j];
+  }
+  __syncthreads();
+
+  const ModeGeom<T> g = mode_geom<T>(k1, k2, n2, L1, L2);
+  const bool special = g.zero || g.nyq;
+  const int n0 = ch * C;
+  const int nend = min(n0 + C, nz);
+  const int e1 = min(n0 + C, nz - 1);  // elements [n0, e1)
+  const bool active = n0 < nz;
+
+  // 2. rotate own nodes into the (q, p, 3) frame
+  if (active && !special) {
+    for (int i = n0; i < nend; ++i) {
+      V x[6];
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) x[cc] = W[(i * 6 + cc) * KT + kt];
+      rotate_in(x, g.c, g.s);
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) W[(i * 6 + cc) * KT + kt] = x[cc];
+    }
+  }
+  __syncthreads();
+
+  Elem<T> ec;
+  if (uniform) ec = elem_coef<T>(g.q, hz);
+
+  // 3. local summaries of both recursions over the chunk's elements, from zero
+  Mom<V>* SP = reinterpret_cast<Mom<V>*>(Pst);          // [nch][KT]
+  Mom<V>* SA = SP + (size_t)nch * KT;                   // [nch][KT]
+  if (active && !special) {
+    Mom<V> A, P;
+    mom_zero(A);
+    mom_zero(P);
+    for (int e = n0; e < e1; ++e) {
+      if (!uniform) ec = elem_coef<T>(g.q, zn[e + 1] - zn[e]);
+      V wi[6], wj[6];
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) {
+        wi[cc] = W[(e * 6 + cc) * KT + kt];
+        wj[cc] = W[((e + 1) * 6 + cc) * KT + kt];
+      }
+      stepA(A, ec, wi, wj);
+    }
+    for (int e = e1 - 1; e >= n0; --e) {
+      if (!uniform) ec = elem_coef<T>(g.q, zn[e + 1] - zn[e]);
+      V wi[6], wj[6];
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) {
+        wi[cc] = W[(e * 6 + cc) * KT + kt];
+        wj[cc] = W[((e + 1) * 6 + cc) * KT + kt];
+      }
+      stepP(P, ec, wi, wj);
+    }
+    SA[ch * KT + kt] = A;
+    SP[ch * KT + kt] = P;
+  }
+  __syncthreads();
+
+  // 4. carries: A at node n0 from all chunks above, P at node e1 from all chunks below,
+  //    and the complete + branch at x3 = 0 for the image term
+  Mom<V> Ain, Pin, P0;
+  mom_zero(Ain);
+  mom_zero(Pin);
+  mom_zero(P0);
+  if (active && !special) {
+    for (int j = 0; j < ch; ++j) {
+      const int a0 = j * C, a1 = min(j * C + C, nz - 1);
+      propA(Ain, g.q * (zn[a1] - zn[a0]));
+      mom_add(Ain, SA[j * KT + kt]);
+    }
+    for (int j = nch - 1; j >= 0; --j) {
+      const int a0 = j * C, a1 = min(j * C + C, nz - 1);
+      if (a0 >= nz) continue;
+      propP(P0, g.q * (zn[a1] - zn[a0]));
+      mom_add(P0, SP[j * KT + kt]);
+      if (j == ch + 1) Pin = P0;
+    }
+    if (ch == nch - 1) mom_zero(Pin);
+  }
+  // surface traction of the full-space field (A = 0 at x3 = 0), cancelled by the image
+  V tr[3];
+  if (active && !special) {
+    V w0[6];
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) w0[cc] = W[cc * KT + kt];
+    Mom<V> Z;
+    mom_zero(Z);
+    V e0[6];
+    kelvin_strain<T, V>(Z, P0, w0, g.q, nu, mu, e0);
+    const V trc = cadd(e0[0], e0[2]);
+    tr[0] = csub(cscale(e0[4], (T)2 * mu), w0[4]);
+    tr[1] = csub(cscale(e0[3], (T)2 * mu), w0[3]);
+    tr[2] = csub(caxpy(cscale(trc, lam), (T)2 * mu, e0[2]), w0[2]);
+    if (want_u3 && ch == 0) {
+      // u3(0) = N_inf[w].e3 + B^T(q, 0) t . e3 (rotated frame)
+      const T K = (T)1 / ((T)8 * mu * (nu - (T)1));
+      V u = caxpy(cmuli(P0.m[3]), (T)1, P0.m[1]);        // P_33 + i P_q3
+      u = cadd(cscale(u, (T)2 - (T)4 * nu), P0.n);
+      u = cscale(u, K);
+      V ub = cscale(cmuli(tr[0]), (T)0.5 * ((T)2 * nu - (T)1));
+      ub = caxpy(ub, -(nu - (T)1), tr[2]);
+      u = caxpy(u, (T)1 / (g.q * mu), ub);
+      surf[(size_t)k2 * h1 + k1] = u;
+    }
+  }
+  if (want_u3 && ch == 0 && special) surf[(size_t)k2 * h1 + k1] = mk<V>(0, 0);
+  __syncthreads();  // summaries are dead from here on; Pst is reused for P(i)
+
+  if (!active) return;
+  if (special) {
+    for (int i = n0; i < nend; ++i) {
+      V w[6], o[6];
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) w[cc] = W[(i * 6 + cc) * KT + kt];
+      if (g.nyq) {
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) o[cc] = out_kind == FVIM_STRAIN ? mk<V>(0, 0) : cscale(w[cc], (T)-1);
+      } else {
+        // laminate: eps_33 = w_33/(lam+2mu), eps_a3 = w_a3/(2mu), eps_ab = 0
+        V e[6];
+        e[0] = e[1] = e[5] = mk<V>(0, 0);
+        e[2] = cscale(w[2], (T)1 / (lam + (T)2 * mu));
+        e[3] = cscale(w[3], (T)1 / ((T)2 * mu));
+        e[4] = cscale(w[4], (T)1 / ((T)2 * mu));
+        if (out_kind == FVIM_STRAIN) {
+#pragma unroll
+          for (int cc = 0; cc < 6; ++cc) o[cc] = e[cc];
+        } else {
+          const V trc = e[2];
+#pragma unroll
+          for (int cc = 0; cc < 6; ++cc) o[cc] = csub(cscale(e[cc], (T)2 * mu), w[cc]);
+          o[0] = caxpy(o[0], lam, trc);
+          o[1] = caxpy(o[1], lam, trc);
+          o[2] = caxpy(o[2], lam, trc);
+        }
+      }
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) spec[(size_t)(i * 6 + cc) * plane + (size_t)k2 * h1 + k1] = o[cc];
+    }
+    return;
+  }
+
+  // 5. exact + branch at the chunk nodes (backward from the carry), kept in Pst
+  Mom<V>* Pn = reinterpret_cast<Mom<V>*>(Pst);  // [node][KT]
+  {
+    Mom<V> P = Pin;
+    if (e1 < nend) Pn[e1 * KT + kt] = P;   // last chunk: node nz-1 has no element below
+    for (int e = e1 - 1; e >= n0; --e) {
+      if (!uniform) ec = elem_coef<T>(g.q, zn[e + 1] - zn[e]);
+      V wi[6], wj[6];
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) {
+        wi[cc] = W[(e * 6 + cc) * KT + kt];
+        wj[cc] = W[((e + 1) * 6 + cc) * KT + kt];
+      }
+      stepP(P, ec, wi, wj);
+      Pn[e * KT + kt] = P;
+    }
+  }
+  // 6. forward: - branch, combine, image, epilogue, rotate back, store
+  {
+    Mom<V> A = Ain;
+    for (int i = n0; i < nend; ++i) {
+      V w[6];
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) w[cc] = W[(i * 6 + cc) * KT + kt];
+      const Mom<V> P = Pn[i * KT + kt];
+      V e[6];
+      kelvin_strain<T, V>(A, P, w, g.q, nu, mu, e);
+      bous_strain_add<T, V>(tr, g.q * zn[i], nu, mu, e);
+      V o[6];
+      if (out_kind == FVIM_STRAIN) {
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) o[cc] = e[cc];
+      } else {
+        const V trc = cadd(e[0], e[2]);
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) o[cc] = csub(cscale(e[cc], (T)2 * mu), w[cc]);
+        o[0] = caxpy(o[0], lam, trc);
+        o[1] = caxpy(o[1], lam, trc);
+        o[2] = caxpy(o[2], lam, trc);
+      }
+      rotate_out(o, g.c, g.s);
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) spec[(size_t)(i * 6 + cc) * plane + (size_t)k2 * h1 + k1] = o[cc];
+      if (i < e1) {
+        if (!uniform) ec = elem_coef<T>(g.q, zn[i + 1] - zn[i]);
+        V wj[6];
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) wj[cc] = W[((i + 1) * 6 + cc) * KT + kt];
+        stepA(A, ec, w, wj);
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------------
+// Boussinesq operator of a normal pressure (Eq. B:fourier): one thread per mode, loop
+// over depth.  surf holds p_hat on entry and u3_hat = 2 p_hat / (E* q) on exit.
+// ----------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_boussinesq(typename Cx<T>::t* __restrict__ spec, typename Cx<T>::t* __restrict__ surf,
+                             const T* __restrict__ zn, int nz, int n2, int h1, double L1, double L2, T lam, T mu,
+                             T nu, int out_kind, int want_vol, int want_u3) {
+  typedef typename Cx<T>::t V;
+  const int k1 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k2 = blockIdx.y;
+  if (k1 >= h1) return;
+  const ModeGeom<T> g = mode_geom<T>(k1, k2, n2, L1, L2);
+  const size_t plane = (size_t)n2 * h1;
+  const size_t at = (size_t)k2 * h1 + k1;
+  const V p = surf[at];
+  if (want_vol) {
+    for (int i = 0; i < nz; ++i) {
+      V o[6];
+      if (g.nyq) {
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) o[cc] = mk<V>(0, 0);
+      } else if (g.zero) {
+        const V e33 = cscale(p, (T)-1 / (lam + (T)2 * mu));
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) o[cc] = mk<V>(0, 0);
+        if (out_kind == FVIM_STRAIN) {
+          o[2] = e33;
+        } else {
+          o[0] = o[1] = cscale(e33, lam);
+          o[2] = cscale(p, (T)-1);
+        }
+      } else {
+        V e[6];
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) e[cc] = mk<V>(0, 0);
+        V tr[3] = {mk<V>(0, 0), mk<V>(0, 0), p};
+        bous_strain_add<T, V>(tr, g.q * zn[i], nu, mu, e);
+        if (out_kind == FVIM_STRAIN) {
+#pragma unroll
+          for (int cc = 0; cc < 6; ++cc) o[cc] = e[cc];
+        } else {
+          const V trc = cadd(e[0], e[2]);
+#pragma unroll
+          for (int cc = 0; cc < 6; ++cc) o[cc] = cscale(e[cc], (T)2 * mu);
+          o[0] = caxpy(o[0], lam, trc);
+          o[1] = caxpy(o[1], lam, trc);
+          o[2] = caxpy(o[2], lam, trc);
+        }
+        rotate_out(o, g.c, g.s);
+      }
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) spec[(size_t)(i * 6 + cc) * plane + at] = o[cc];
+    }
+  }
+  if (want_u3) {
+    V u = mk<V>(0, 0);
+    if (!g.zero && !g.nyq) u = cscale(p, ((T)1 - nu) / (mu * g.q));
+    surf[at] = u;
+  }
+}
+
+}  // namespace
+
+template <typename T> int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3) {
+  typedef typename Cx<T>::t V;
+  const int nz = c->nz, h1 = c->h1, n2 = c->n2;
+  const int KT = h1 < KT_MAX ? h1 : KT_MAX;  // h1 is a power of two
+  int C = (nz + 15) / 16;
+  if (C < 2) C = 2;
+  const int nch = (nz + C - 1) / C;
+  const int threads = KT * nch;
+  const int prow = nz > 2 * nch ? nz : 2 * nch;
+  const size_t smem = (size_t)nz * 6 * KT * sizeof(V) + (size_t)prow * KT * sizeof(Mom<V>);
+  if (smem > 227 * 1024) return FVIM_ERR_UNSUPPORTED;
+  cudaFuncSetAttribute(k_mindlin_depth<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid(h1 / KT, n2);
+  k_mindlin_depth<T><<<grid, threads, smem, c->stream>>>(
+      (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, n2, h1, KT, C, nch, c->L1, c->L2, (T)c->lam, (T)c->mu,
+      (T)c->nu, out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz);
+  FVIM_CUDA_CHECK_LAUNCH();
+  return FVIM_OK;
+}
+
+template <typename T> int launch_boussinesq(const fvim_ctx* c, int out_kind, bool want_vol, bool want_u3) {
+  typedef typename Cx<T>::t V;
+  const int threads = 128;
+  dim3 grid((c->h1 + threads - 1) / threads, c->n2);
+  k_boussinesq<T><<<grid, threads, 0, c->stream>>>((V*)c->spec, (V*)c->surf, (const T*)c->z_dev, c->nz, c->n2, c->h1,
+                                                   c->L1, c->L2, (T)c->lam, (T)c->mu, (T)c->nu, out_kind,
+                                                   want_vol ? 1 : 0, want_u3 ? 1 : 0);
+  FVIM_CUDA_CHECK_LAUNCH();
+  return FVIM_OK;
+}
+
+template int launch_mindlin_depth<float>(const fvim_ctx*, int, bool);
+template int launch_mindlin_depth<double>(const fvim_ctx*, int, bool);
+template int launch_boussinesq<float>(const fvim_ctx*, int, bool, bool);
+template int launch_boussinesq<double>(const fvim_ctx*, int, bool, bool);

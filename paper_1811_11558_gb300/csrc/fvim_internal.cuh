@@ -1,0 +1,205 @@
+// Internal definitions shared by the CUDA translation units of libfvim.
+// Not part of the public ABI (see include/fvim.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fvim.h"
+
+// ---------------------------------------------------------------------------
+// complex helpers (float2 / double2)
+// ---------------------------------------------------------------------------
+template <typename T> struct Cx;
+template <> struct Cx<float> { typedef float2 t; };
+template <> struct Cx<double> { typedef double2 t; };
+
+template <typename V> __host__ __device__ __forceinline__ V mk(decltype(V::x) a, decltype(V::x) b) {
+  V r; r.x = a; r.y = b; return r;
+}
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return mk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename V> __device__ __forceinline__ V cconj(V a) { return mk<V>(a.x, -a.y); }
+template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V::x) s) { return mk<V>(a.x * s, a.y * s); }
+// multiply by i
+template <typename V> __device__ __forceinline__ V cmuli(V a) { return mk<V>(-a.y, a.x); }
+// a + s*b (s real)
+template <typename V> __device__ __forceinline__ V caxpy(V a, decltype(V::x) s, V b) {
+  return mk<V>(a.x + s * b.x, a.y + s * b.y);
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory FFT: batched, in place, Stockham autosort with radix 8/4/2
+// stages.  Every thread of the block takes part; at most MAXI work items (one
+// radix-R butterfly each) per thread and stage, so the caller must launch at
+// least ceil(nfft * n / rmin(n) / MAXI) threads.  tw[k] = exp(-2 pi i k / n).
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int fft_radix(int m) {
+  // radix of the next stage for a remaining length m (plans 8..8 then 4/4 or 4 or 2)
+  if (m == 2) return 2;
+  if (m == 4) return 4;
+  if (m == 16) return 4;           // 16 = 4 x 4 instead of 8 x 2
+  if (m % 8 == 0) return 8;
+  return 4;
+}
+__host__ __device__ inline int fft_rmin(int n) {
+  int rmin = 8, m = n;
+  while (m > 1) { int r = fft_radix(m); if (r < rmin) rmin = r; m /= r; }
+  return rmin;
+}
+
+template <typename V, bool INV>
+__device__ __forceinline__ V twiddle(const V* tw, int idx) {
+  V w = tw[idx];
+  if (INV) w.y = -w.y;
+  return w;
+}
+
+template <typename V, bool INV>
+__device__ __forceinline__ void dft2(V& a, V& b) { V t = a; a = cadd(t, b); b = csub(t, b); }
+
+template <typename V, bool INV>
+__device__ __forceinline__ void dft4(V* v) {
+  V a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+  V b0 = cadd(v[1], v[3]), b1 = csub(v[1], v[3]);
+  // forward: W4 = -i ; inverse: +i
+  V b1r = INV ? cmuli(b1) : cscale(cmuli(b1), (decltype(V::x))-1);
+  v[0] = cadd(a0, b0);
+  v[2] = csub(a0, b0);
+  v[1] = cadd(a1, b1r);
+  v[3] = csub(a1, b1r);
+}
+
+template <typename V, bool INV>
+__device__ __forceinline__ void dft8(V* v) {
+  typedef decltype(V::x) T;
+  const T r = (T)0.70710678118654752440;
+  V e[4] = {v[0], v[2], v[4], v[6]};
+  V o[4] = {v[1], v[3], v[5], v[7]};
+  dft4<V, INV>(e);
+  dft4<V, INV>(o);
+  // twiddles W8^m, m = 0..3 (forward exp(-i pi m/4))
+  V w1 = INV ? mk<V>(r, r) : mk<V>(r, -r);
+  V w2 = INV ? mk<V>(0, 1) : mk<V>(0, -1);
+  V w3 = INV ? mk<V>(-r, r) : mk<V>(-r, -r);
+  o[1] = cmul(o[1], w1);
+  o[2] = cmul(o[2], w2);
+  o[3] = cmul(o[3], w3);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    v[m] = cadd(e[m], o[m]);
+    v[m + 4] = csub(e[m], o[m]);
+  }
+}
+
+template <typename V, bool INV, int R, int MAXI>
+__device__ __forceinline__ void fft_stage(V* buf, int n, int nfft, int fstride, int Ns, const V* tw) {
+  const int per = n / R;
+  const int items = nfft * per;
+  V v[MAXI][R];
+#pragma unroll
+  for (int it = 0; it < MAXI; ++it) {
+    const int w = threadIdx.x + it * blockDim.x;
+    if (w < items) {
+      const int f = w / per, j = w - f * per;
+      const V* b = buf + (size_t)f * fstride;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[it][r] = b[j + r * per];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < MAXI; ++it) {
+    const int w = threadIdx.x + it * blockDim.x;
+    if (w < items) {
+      const int f = w / per, j = w - f * per;
+      const int k = j % Ns;
+      const int step = n / (Ns * R);
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[it][r] = cmul(v[it][r], twiddle<V, INV>(tw, (r * k * step) & (n - 1)));
+      if (R == 8) dft8<V, INV>(v[it]);
+      else if (R == 4) dft4<V, INV>(v[it]);
+      else dft2<V, INV>(v[it][0], v[it][1]);
+      V* b = buf + (size_t)f * fstride;
+      const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) b[base + r * Ns] = v[it][r];
+    }
+  }
+  __syncthreads();
+}
+
+// nfft transforms of length n (power of two >= 2) in shared memory, FFT f at
+// buf + f * fstride.  Unnormalised; INV uses exp(+2 pi i k/n).
+template <typename V, bool INV, int MAXI>
+__device__ void block_fft(V* buf, int n, int nfft, int fstride, const V* tw) {
+  int Ns = 1;
+  int m = n;
+  while (m > 1) {
+    const int R = fft_radix(m);
+    if (R == 8) fft_stage<V, INV, 8, MAXI>(buf, n, nfft, fstride, Ns, tw);
+    else if (R == 4) fft_stage<V, INV, 4, MAXI>(buf, n, nfft, fstride, Ns, tw);
+    else fft_stage<V, INV, 2, MAXI>(buf, n, nfft, fstride, Ns, tw);
+    Ns *= R;
+    m /= R;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct fvim_ctx {
+  int n1, n2, nz, h1;
+  int prec;  // FVIM_FP32 / FVIM_FP64
+  double L1, L2;
+  double E, nu, sigma_y, E_h, lam, mu;
+  cudaStream_t stream;
+  int device;
+  int uniform;   // depth nodes equally spaced
+  double hz;     // spacing when uniform
+  double* z_host;
+  void* z_dev;   // T[nz]
+  void* tw1;     // complex T[n1]
+  void* tw2;     // complex T[n2]
+  void* spec;    // complex T[nz][6][n2][h1]
+  void* nq;      // T[nz][6][n2] row-Nyquist coefficients
+  void* surf;    // complex T[n2][h1]
+  void* surf_nq; // T[n2]
+  void* st_eps_p; // T[nz][6][n2][n1]
+  void* st_ep;    // T[nz][n2][n1]
+  void* st_sig;   // T[nz][6][n2][n1]
+  int last_kernels;
+  void* prof;  // ProfState* (capi.cu) or NULL
+};
+
+// kernel kinds for fvim_profile_read
+enum ProfSlot {
+  PROF_ROWS_FWD6 = 0, PROF_COLS_FWD, PROF_MINDLIN_DEPTH, PROF_COLS_INV, PROF_ROWS_INV6,
+  PROF_ROWS_FWD1, PROF_ROWS_INV1, PROF_BOUSSINESQ, PROF_RETURN_MAP, PROF_COMMIT, PROF_NSLOTS
+};
+
+// material constants handed to kernels
+template <typename T> struct Mat {
+  T lam, mu, nu, sigma_y, E_h;
+};
+
+// launchers (defined in the .cu files, instantiated for float and double)
+template <typename T> int launch_rows_fwd6(const fvim_ctx* c, const T* eps_p, int z0, int nzs);
+template <typename T> int launch_rows_fwd1(const fvim_ctx* c, const T* f);
+template <typename T> int launch_cols(const fvim_ctx* c, bool inverse, void* planes, int nplanes);
+template <typename T> int launch_rows_inv6(const fvim_ctx* c, T* out, T nq_scale, int z0, int nzs);
+template <typename T> int launch_rows_inv1(const fvim_ctx* c, T* f);
+template <typename T> int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3);
+template <typename T> int launch_boussinesq(const fvim_ctx* c, int out_kind, bool want_vol, bool want_u3);
+template <typename T> int launch_return_map(const fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep);
+template <typename T> int launch_commit(const fvim_ctx* c, const T* d_eps, const T* d_eps_p, const T* d_ep);
+template <typename T> int launch_zero_nq(const fvim_ctx* c);
+
+#define FVIM_CUDA_CHECK_LAUNCH()                          \
+  do {                                                    \
+    cudaError_t e_ = cudaGetLastError();                  \
+    if (e_ != cudaSuccess) return FVIM_ERR_CUDA;          \
+  } while (0)

@@ -1,0 +1,230 @@
+"""Thin Python binding of libfvim (include/fvim.h): argument marshalling only.
+
+Every step of every operator runs in the CUDA kernels of libfvim.so; this module
+checks tensor shapes, dtypes and devices, passes raw device pointers and the
+current torch CUDA stream, and turns status codes into exceptions.  There is no
+CPU fallback: if the library is missing or no GPU is present, calls raise.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libfvim.so")
+
+FVIM_FP32 = 0
+FVIM_FP64 = 1
+FVIM_STRESS = 0
+FVIM_STRAIN = 1
+
+_lib = None
+
+
+class FvimError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__("%s failed: %s (status %d)" % (what, strerror(status), status))
+        self.status = status
+
+
+def lib():
+    """Load libfvim.so (built by paper_1811_11558_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libfvim.so not built (run __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "fvim_create": (i, [ctypes.POINTER(vp), i, i, i, ctypes.POINTER(d), d, d, i, vp]),
+        "fvim_set_material": (i, [vp, d, d, d, d]),
+        "fvim_set_stream": (i, [vp, vp]),
+        "fvim_apply_mindlin": (i, [vp, vp, vp, i, vp]),
+        "fvim_apply_boussinesq": (i, [vp, vp, vp, vp, i]),
+        "fvim_return_map": (i, [vp, vp, vp, vp]),
+        "fvim_commit_state": (i, [vp, vp, vp, vp]),
+        "fvim_get_state": (i, [vp, vp, vp, vp]),
+        "fvim_set_state": (i, [vp, vp, vp, vp]),
+        "fvim_sync": (i, [vp]),
+        "fvim_destroy": (i, [vp]),
+        "fvim_strerror": (ctypes.c_char_p, [i]),
+        "fvim_last_kernel_count": (i, [vp]),
+        "fvim_profile_enable": (i, [vp, i]),
+        "fvim_profile_read": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(i), i]),
+        "fvim_profile_name": (ctypes.c_char_p, [i]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def strerror(status):
+    return lib().fvim_strerror(int(status)).decode()
+
+
+def _check(status, what):
+    if status != 0:
+        raise FvimError(status, what)
+
+
+def _ptr(t, dtype, shape, name):
+    import torch
+
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One periodic half-space grid with its material, precision and plastic state.
+
+    n1, n2: in-plane points (powers of two); z: depth nodes (z[0] = 0, increasing);
+    L1, L2: cell lengths; precision: "fp32" or "fp64".
+    """
+
+    def __init__(self, n1, n2, z, L1=1.0, L2=1.0, precision="fp32", E=1.0, nu=0.3,
+                 sigma_y=math.inf, E_h=0.0):
+        import torch
+
+        self.n1, self.n2 = int(n1), int(n2)
+        z = np.ascontiguousarray(np.asarray(z, dtype=np.float64))
+        self.z = z
+        self.nz = int(z.size)
+        self.L1, self.L2 = float(L1), float(L2)
+        self.precision = precision
+        self.dtype = torch.float32 if precision == "fp32" else torch.float64
+        prec = FVIM_FP32 if precision == "fp32" else FVIM_FP64
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        torch.cuda.init()
+        self._h = ctypes.c_void_p()
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        _check(lib().fvim_create(ctypes.byref(self._h), self.n1, self.n2, self.nz,
+                                 z.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 self.L1, self.L2, prec, stream), "fvim_create")
+        self.set_material(E, nu, sigma_y, E_h)
+
+    # -- plumbing -----------------------------------------------------------------
+    def _stream(self):
+        import torch
+
+        _check(lib().fvim_set_stream(self._h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+               "fvim_set_stream")
+
+    @property
+    def vol_shape(self):
+        return (self.nz, 6, self.n2, self.n1)
+
+    @property
+    def surf_shape(self):
+        return (self.n2, self.n1)
+
+    @property
+    def scal_shape(self):
+        return (self.nz, self.n2, self.n1)
+
+    def profile(self, on=True):
+        """Bracket every kernel launch with CUDA events on the context's stream."""
+        _check(lib().fvim_profile_enable(self._h, 1 if on else 0), "fvim_profile_enable")
+
+    def profile_read(self):
+        """{kernel kind: (total ms, launches)} since the last read (synchronises)."""
+        n = 16
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int * n)()
+        _check(lib().fvim_profile_read(self._h, ms, cnt, n), "fvim_profile_read")
+        out = {}
+        for s in range(n):
+            name = lib().fvim_profile_name(s)
+            if name is None:
+                break
+            if cnt[s]:
+                out[name.decode()] = (ms[s], cnt[s])
+        return out
+
+    def last_kernel_count(self):
+        return lib().fvim_last_kernel_count(self._h)
+
+    def close(self):
+        if self._h:
+            lib().fvim_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- API ----------------------------------------------------------------------
+    def set_material(self, E, nu, sigma_y=math.inf, E_h=0.0):
+        self.E, self.nu, self.sigma_y, self.E_h = float(E), float(nu), float(sigma_y), float(E_h)
+        sy = self.sigma_y if math.isfinite(self.sigma_y) else 1e300
+        _check(lib().fvim_set_material(self._h, self.E, self.nu, sy, self.E_h), "fvim_set_material")
+
+    def apply_mindlin(self, eps_p, out=None, kind="stress", u3=None):
+        import torch
+
+        if out is None:
+            out = torch.empty(self.vol_shape, dtype=self.dtype, device=eps_p.device)
+        k = FVIM_STRESS if kind == "stress" else FVIM_STRAIN
+        a = _ptr(eps_p, self.dtype, self.vol_shape, "eps_p")
+        b = _ptr(out, self.dtype, self.vol_shape, "out")
+        c = _ptr(u3, self.dtype, self.surf_shape, "u3")
+        self._stream()
+        _check(lib().fvim_apply_mindlin(self._h, a, b, k, c), "fvim_apply_mindlin")
+        return out
+
+    def apply_boussinesq(self, p, u3=None, vol=None, kind="stress"):
+        k = FVIM_STRESS if kind == "stress" else FVIM_STRAIN
+        a = _ptr(p, self.dtype, self.surf_shape, "p")
+        b = _ptr(u3, self.dtype, self.surf_shape, "u3")
+        c = _ptr(vol, self.dtype, self.vol_shape, "vol")
+        self._stream()
+        _check(lib().fvim_apply_boussinesq(self._h, a, b, c, k), "fvim_apply_boussinesq")
+        return u3, vol
+
+    def return_map(self, d_eps, d_eps_p, d_ep=None):
+        a = _ptr(d_eps, self.dtype, self.vol_shape, "d_eps")
+        b = _ptr(d_eps_p, self.dtype, self.vol_shape, "d_eps_p")
+        c = _ptr(d_ep, self.dtype, self.scal_shape, "d_ep")
+        self._stream()
+        _check(lib().fvim_return_map(self._h, a, b, c), "fvim_return_map")
+        return d_eps_p, d_ep
+
+    def commit_state(self, d_eps, d_eps_p, d_ep):
+        a = _ptr(d_eps, self.dtype, self.vol_shape, "d_eps")
+        b = _ptr(d_eps_p, self.dtype, self.vol_shape, "d_eps_p")
+        c = _ptr(d_ep, self.dtype, self.scal_shape, "d_ep")
+        self._stream()
+        _check(lib().fvim_commit_state(self._h, a, b, c), "fvim_commit_state")
+
+    def get_state(self, eps_p=None, e_p=None, sigma=None):
+        a = _ptr(eps_p, self.dtype, self.vol_shape, "eps_p")
+        b = _ptr(e_p, self.dtype, self.scal_shape, "e_p")
+        c = _ptr(sigma, self.dtype, self.vol_shape, "sigma")
+        self._stream()
+        _check(lib().fvim_get_state(self._h, a, b, c), "fvim_get_state")
+
+    def set_state(self, eps_p=None, e_p=None, sigma=None):
+        a = _ptr(eps_p, self.dtype, self.vol_shape, "eps_p")
+        b = _ptr(e_p, self.dtype, self.scal_shape, "e_p")
+        c = _ptr(sigma, self.dtype, self.vol_shape, "sigma")
+        self._stream()
+        _check(lib().fvim_set_state(self._h, a, b, c), "fvim_set_state")
+
+    def sync(self):
+        _check(lib().fvim_sync(self._h), "fvim_sync")

@@ -1,0 +1,63 @@
+"""The C ABI library builds, loads without a GPU and exports every declared symbol."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(fvim_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1811_11558_gb300 import build, fvim
+
+    if not os.path.exists(fvim.LIB_PATH):
+        build.build()
+    L = ctypes.CDLL(fvim.LIB_PATH)
+    names = _declared()
+    assert "fvim_apply_mindlin" in names and len(names) >= 12
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_strerror_without_gpu():
+    from paper_1811_11558_gb300 import fvim
+
+    assert fvim.strerror(0) == "ok"
+    assert fvim.strerror(-5) == "not converged"
+
+
+def test_create_rejects_bad_grid_without_launching():
+    """Argument errors are found on the host before anything touches the GPU."""
+    from paper_1811_11558_gb300 import fvim
+    import numpy as np
+
+    L = fvim.lib()
+    h = ctypes.c_void_p()
+    z = np.array([0.0, 0.1])
+    zp = z.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert L.fvim_create(ctypes.byref(h), 6, 8, 2, zp, 1.0, 1.0, 0, None) == -1      # n1 not a power of 2
+    assert L.fvim_create(ctypes.byref(h), 8, 8, 1, zp, 1.0, 1.0, 0, None) == -1      # one node
+    assert L.fvim_create(ctypes.byref(h), 8, 8, 2, zp, -1.0, 1.0, 0, None) == -1     # bad cell
+    assert L.fvim_create(ctypes.byref(h), 8, 8, 2, zp, 1.0, 1.0, 7, None) == -1      # bad precision
+    assert L.fvim_apply_mindlin(None, None, None, 0, None) == -1
+
+
+def test_product_path_does_not_import_oracle():
+    """The product package never names the CPU oracle (no fallback)."""
+    pkg = os.path.join(ROOT, "paper_1811_11558_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle", src, re.M), f
