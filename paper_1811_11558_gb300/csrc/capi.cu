@@ -143,7 +143,9 @@ template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, i
     return rc;
   if ((rc = timed(c, PROF_COLS_INV, nk, [&] { return launch_cols<T>(c, true, c->spec, c->nz * 6); }))) return rc;
   if ((rc = timed(c, PROF_ROWS_INV6, nk, [&] {
-         return launch_rows_inv6<T>(c, out, kind == FVIM_STRESS ? (T)-1 : (T)0, 0, c->nz);
+         // the k1 = N1/2 column never goes through the column transforms, so it carries
+         // the factor N2 that the 1/(N1 N2) normalisation of rows_inv6 removes
+         return launch_rows_inv6<T>(c, out, kind == FVIM_STRESS ? -(T)c->n2 : (T)0, 0, c->nz);
        })))
     return rc;
   if (u3) {

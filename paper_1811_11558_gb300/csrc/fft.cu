@@ -133,8 +133,9 @@ __global__ void __launch_bounds__(MaxT<T>::v) k_cols(typename Cx<T>::t* __restri
 }
 
 // --- inverse rows, six components ------------------------------------------------
-// nq_scale multiplies the stored k1 = N1/2 coefficient (-1 for the stress output of the
-// Mindlin operator, 0 when the operator has no Nyquist term).  scale = 1/(N1 N2).
+// nq_scale multiplies the stored k1 = N1/2 coefficient (-N2 for the stress output of the
+// Mindlin operator, sigma_hat = -w_hat there; 0 when the operator has no Nyquist term).
+// scale = 1/(N1 N2).
 template <typename T, int RB, int MAXI>
 __global__ void __launch_bounds__(MaxT<T>::v) k_rows_inv6(const typename Cx<T>::t* __restrict__ spec, const T* __restrict__ nq, T* __restrict__ out,
                             const typename Cx<T>::t* __restrict__ tw, int n1, int n2, int z0, T nq_scale, T scale) {
@@ -227,8 +228,9 @@ template <typename T> bool fft_shape(int nfft, int n, int& maxi, int& threads) {
 }
 
 // rows per CTA: a few rows when they are short, within the per-thread item budget
-template <typename T> int row_block(int n1) {
+template <typename T> int row_block(int n1, int n2) {
   int rb = n1 <= 256 ? 4 : (n1 <= 512 ? 2 : 1);
+  while (rb > n2) rb >>= 1;
   while (rb > 1 && 3 * rb * n1 / fft_rmin(n1) > 2 * MaxT<T>::v) rb >>= 1;
   return rb;
 }
@@ -242,7 +244,7 @@ template <typename K> void set_smem(K kern, size_t smem) {
 template <typename T> int launch_rows_fwd6(const fvim_ctx* c, const T* eps_p, int z0, int nzs) {
   typedef typename Cx<T>::t V;
   const int n1 = c->n1, n2 = c->n2;
-  const int RB = row_block<T>(n1);
+  const int RB = row_block<T>(n1, n2);
   int maxi, threads;
   if (n2 % RB || !fft_shape<T>(3 * RB, n1, maxi, threads)) return FVIM_ERR_UNSUPPORTED;
   const size_t smem = (size_t)RB * 3 * n1 * sizeof(V);
@@ -302,7 +304,7 @@ template <typename T> int launch_cols(const fvim_ctx* c, bool inverse, void* pla
 template <typename T> int launch_rows_inv6(const fvim_ctx* c, T* out, T nq_scale, int z0, int nzs) {
   typedef typename Cx<T>::t V;
   const int n1 = c->n1, n2 = c->n2;
-  const int RB = row_block<T>(n1);
+  const int RB = row_block<T>(n1, n2);
   int maxi, threads;
   if (n2 % RB || !fft_shape<T>(3 * RB, n1, maxi, threads)) return FVIM_ERR_UNSUPPORTED;
   const size_t smem = (size_t)RB * 3 * n1 * sizeof(V);

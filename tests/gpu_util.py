@@ -16,8 +16,9 @@ def require_gpu():
 
 
 def rel_l2(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
+    """||a - b||_2 / ||b||_2 over all entries (real or complex)."""
+    a = np.asarray(a)
+    b = np.asarray(b)
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
 
 

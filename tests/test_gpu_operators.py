@@ -89,7 +89,7 @@ def test_mindlin_full_size_sampled_modes():
     Q1, Q2, nyq, zero = op.mode_grid(n, n, 1.0, 1.0)
     keep = ~(nyq[k2, k1] | zero[k2, k1])
     k1, k2 = k1[keep], k2[keep]
-    W = np.moveaxis(T.sym6_to_full(w_hat[:, :, k2, k1], axis=1), 2, 0)  # [K, nz, 3, 3]
+    W = np.moveaxis(T.sym6_to_full(w_hat[:, :, k2, k1], axis=1), 1, 0)  # [K, nz, 3, 3]
     Q = np.stack([Q1[k2, k1], Q2[k2, k1]], axis=1)
     H, _, _ = op.mindlin_modes(W, Q, z, E, NU)
     sig = T.hooke_full(T.sym_part(H), lam, mu) - W
