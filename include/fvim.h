@@ -143,6 +143,36 @@ int fvim_profile_enable(fvim_ctx* ctx, int on);
 int fvim_profile_read(fvim_ctx* ctx, double* total_ms, int* launches, int nslots);
 const char* fvim_profile_name(int slot);
 
+/*
+ * fvim_apply_mindlin_noalloc -- the Mindlin apply of fvim_apply_mindlin without a
+ * context and without any device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory while they run (a host
+ * framework that owns all device memory through its own pool, a service that must
+ * never reach cudaMalloc/cudaFree because they can synchronise the whole device, or
+ * code with a fixed memory budget decided at start-up).
+ *
+ * Its scratch (half spectrum, row-Nyquist coefficients, twiddles, depth nodes) lives in
+ * one static device array of FVIM_NOALLOC_SCRATCH_BYTES bytes inside the library; every
+ * GPU that loads the library holds that array until the process exits.  The caller
+ * still owns the input and output buffers.
+ *   n1, n2, nz, z_nodes (HOST), L1, L2, precision: as for fvim_create.
+ *   E, nu: isotropic elasticity as for fvim_set_material.
+ *   eps_p, out, out_kind, u3_surface: as for fvim_apply_mindlin (device buffers).
+ *   stream: cudaStream_t to enqueue on (NULL = legacy default stream).
+ * Returns FVIM_ERR_UNSUPPORTED, before any device work, when the scratch the grid needs
+ * exceeds FVIM_NOALLOC_SCRATCH_BYTES (e.g. 128 x 128 x 32 fits in FP32, 512 x 512 x 64
+ * does not).  It never calls cudaMalloc, cudaFree or any allocating routine.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.
+ * Every call shares the one array and leaves its contents behind (each call overwrites
+ * every region before reading it, so nothing has to be cleared): two calls that overlap
+ * on the GPU (different streams, or different host threads on one device) race on it.
+ */
+#define FVIM_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+int fvim_apply_mindlin_noalloc(int n1, int n2, int nz, const double* z_nodes, double L1, double L2,
+                               double E, double nu, int precision, const void* eps_p, void* out,
+                               int out_kind, void* u3_surface, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
