@@ -111,6 +111,24 @@ def _chunks(Kn, Nz):
     return [slice(s, min(Kn, s + per)) for s in range(0, Kn, per)]
 
 
+_MODE_CACHE = {}
+
+
+def _mode_data(Q, z, mu, nu):
+    """Kelvin tensors at -q (Lemma 1), depth weights and Boussinesq tensors at +q for a
+    batch of modes; memoised per (modes, nodes, material) since repeated applies on one
+    grid (the solvers) use the same values."""
+    key = (Q.tobytes(), np.asarray(z, dtype=np.float64).tobytes(), float(mu), float(nu))
+    hit = _MODE_CACHE.get(key)
+    if hit is None:
+        q = np.hypot(Q[:, 0], Q[:, 1])
+        hit = (K.kelvin_gradient_tensors(-Q, mu, nu), depth_weights(q, z), K.boussinesq_gradient_tensors(Q, mu, nu))
+        if len(_MODE_CACHE) > 64:
+            _MODE_CACHE.clear()
+        _MODE_CACHE[key] = hit
+    return hit
+
+
 def mindlin_modes(W, Q, z, E, nu):
     """Mindlin operator for a batch of non-zero modes.
 
@@ -125,9 +143,7 @@ def mindlin_modes(W, Q, z, E, nu):
     Q = np.atleast_2d(np.asarray(Q, dtype=np.float64))
     W = np.asarray(W, dtype=np.complex128)
     q = np.hypot(Q[:, 0], Q[:, 1])
-    Qm = -Q                                              # Lemma 1: kernel at -q
-    kel = K.kelvin_gradient_tensors(Qm, mu, nu)
-    Lw = depth_weights(q, z)
+    kel, Lw, bou = _mode_data(Q, z, mu, nu)
     M = {key: np.einsum("kij,kjab->kiab", Lw[key], W) for key in Lw}
     # Eq. (2gradient): - int grad^2 U(-q, y3 - x3) : w(y3) dy3, both branches
     G = np.zeros(W.shape, dtype=np.complex128)
@@ -145,7 +161,6 @@ def mindlin_modes(W, Q, z, E, nu):
     # image term (Eq. mindlin_B_U): cancel the surface traction of the full-space field
     sig0 = hooke_full(sym_part(G[:, 0]), lam, mu) - W[:, 0]
     t = sig0[:, :, 2]                                    # applied traction -T_inf = sigma . e3
-    bou = K.boussinesq_gradient_tensors(Q, mu, nu)       # standard convolution: +q
     B00, B10 = bou[0]
     B01, B11 = bou[1]
     zq = q[:, None] * np.asarray(z)[None, :]             # [K, Nz]

@@ -46,3 +46,65 @@ def return_map(d_eps, sigma_n, e_p, E, nu, sigma_y, E_h):
 def von_mises(sig6):
     """f_y(sigma) = sqrt(3/2) ||dev sigma|| (Sec. 4.1)."""
     return np.sqrt(1.5) * norm6(deviator6(sig6, axis=0), axis=0)
+
+
+def dfsane(F, x0, inner, tol_abs, tol_rel, max_iter, M=10, gamma=1e-4, sigma_min=1e-10, sigma_max=1e10,
+           tau_min=0.1, tau_max=0.5, max_backtrack=60):
+    """Derivative-free spectral residual method (DF-SANE) of La Cruz, Martinez & Raydan
+    (2006), the published algorithm used in Sec. 4.3:
+        d_k = -sigma_k F(x_k),  sigma_k = <s, s> / <s, y>  (s = x_k - x_{k-1},
+        y = F(x_k) - F(x_{k-1})), safeguarded into [sigma_min, sigma_max];
+        nonmonotone line search on f = ||F||^2, trying x + alpha d and x - alpha d:
+        accept when f(x +- alpha d) <= max(last M values of f) + eta_k - gamma alpha^2 f(x_k),
+        eta_k = ||F(x_0)|| / (1 + k)^2, otherwise shrink alpha by the safeguarded
+        quadratic model into [tau_min alpha, tau_max alpha].
+    Published defaults (the paper gives none).  Stops when ||F|| <= tol_abs + tol_rel ||F(x_0)||.
+    Returns (x, info)."""
+    x = np.array(x0, dtype=np.float64, copy=True)
+    Fx = F(x)
+    f = inner(Fx, Fx)
+    nF0 = np.sqrt(f)
+    hist = [f]
+    sigma = 1.0
+    evals = 1
+    k = 0
+    for k in range(max_iter):
+        if np.sqrt(f) <= tol_abs + tol_rel * nF0:
+            return x, {"iterations": k, "residual": np.sqrt(f), "residual0": nF0, "evals": evals,
+                       "converged": True}
+        d = -sigma * Fx
+        fmax = max(hist[-M:])
+        eta = nF0 / (1.0 + k) ** 2
+        ap = am = 1.0
+        xn = Fn = fn = None
+        for _ in range(max_backtrack):
+            xp = x + ap * d
+            Fp = F(xp)
+            evals += 1
+            fp = inner(Fp, Fp)
+            if fp <= fmax + eta - gamma * ap * ap * f:
+                xn, Fn, fn = xp, Fp, fp
+                break
+            xm = x - am * d
+            Fm = F(xm)
+            evals += 1
+            fm = inner(Fm, Fm)
+            if fm <= fmax + eta - gamma * am * am * f:
+                xn, Fn, fn = xm, Fm, fm
+                break
+            ap = min(max(ap * ap * f / (fp + (2.0 * ap - 1.0) * f), tau_min * ap), tau_max * ap)
+            am = min(max(am * am * f / (fm + (2.0 * am - 1.0) * f), tau_min * am), tau_max * am)
+        if xn is None:
+            break
+        s = xn - x
+        y = Fn - Fx
+        sy = inner(s, y)
+        ss = inner(s, s)
+        sigma = ss / sy if sy != 0.0 else np.inf
+        if not (sigma_min <= abs(sigma) <= sigma_max):
+            nf = np.sqrt(fn)
+            sigma = 1.0 if nf > 1.0 else (1.0 / nf if nf >= 1e-5 else 1e5)
+        x, Fx, f = xn, Fn, fn
+        hist.append(f)
+    return x, {"iterations": k, "residual": np.sqrt(f), "residual0": nF0, "evals": evals,
+               "converged": bool(np.sqrt(f) <= tol_abs + tol_rel * nF0)}
