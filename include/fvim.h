@@ -143,6 +143,79 @@ int fvim_profile_enable(fvim_ctx* ctx, int on);
 int fvim_profile_read(fvim_ctx* ctx, double* total_ms, int* launches, int nslots);
 const char* fvim_profile_name(int slot);
 
+/* ------------------------------------------------------------------------------------
+ * Solvers.  Vectors live on the device in the context's precision; every reduction
+ * (dot products, norms, the total load) is accumulated in FP64 in a fixed order, so
+ * repeated runs give bitwise identical results.  The loops run on the host and read
+ * back a few FP64 scalars per iteration; every loop has an iteration cap.
+ * ------------------------------------------------------------------------------------ */
+#define FVIM_MAX_INCREMENTS 64
+
+typedef struct {
+  double tol;         /* Algorithm 1: e = ||dU - dU_prev|| / ||H0|| < tol (paper: 1e-9)     */
+  int max_iter;       /* Algorithm 1: N_max                                                  */
+  double relax;       /* Algorithm 1: relaxation lambda in ]0, 1]                           */
+  double cg_tol;      /* contact: dA sum |p - p_prev| / W < cg_tol                            */
+  int cg_max_iter;
+  double df_tol_abs;  /* DF-SANE: ||R|| <= df_tol_abs + df_tol_rel ||R_0|| (discrete L2 norm) */
+  double df_tol_rel;
+  int df_max_iter;
+} fvim_opts;
+
+typedef struct {
+  int status;                                  /* FVIM_OK or FVIM_ERR_NOT_CONVERGED        */
+  int n_increments;                            /* increments completed                      */
+  int alg1_iters[FVIM_MAX_INCREMENTS];         /* Algorithm-1 iterations per increment      */
+  double alg1_error[FVIM_MAX_INCREMENTS];      /* final e per increment                     */
+  double contact_area[FVIM_MAX_INCREMENTS];    /* fraction of surface points with p > 0     */
+  double load_error;                           /* max |dA sum p - W| / W over increments    */
+  long cg_iters;                               /* total contact CG iterations               */
+  long df_iters;                               /* total DF-SANE iterations                  */
+  long residual_evals;                         /* total plastic-residual evaluations        */
+  long mindlin_applies;                        /* total Mindlin-operator applies            */
+} fvim_report;
+
+/* fvim_default_opts -- the defaults: tol 1e-9, max_iter 100, relax 1, cg_tol 1e-12 (FP64) /
+ * 1e-6 (FP32), cg_max_iter 2000, df_tol_abs 0, df_tol_rel 1e-10 (FP64) / 1e-5 (FP32),
+ * df_max_iter 500. */
+int fvim_default_opts(const fvim_ctx* ctx, fvim_opts* opts);
+
+/*
+ * fvim_elastic_contact -- elastic normal contact with the rigid surface h under the total
+ * load W (Sec. 5.1; constrained conjugate gradient of Polonsky & Keer 1999 on the dual
+ * problem, u3 = K*p with K_hat = 2/(E* q)).
+ *   h     device [N2][N1] surface profile (the rigid surface is z = h, e3 into the body).
+ *   p     device [N2][N1]: initial guess on entry (all zero = uniform W/(L1 L2)), contact
+ *         pressure on exit (p >= 0, dA sum p = W).
+ *   iters, err: host outputs (may be NULL).  FVIM_ERR_NOT_CONVERGED at cg_max_iter.
+ */
+int fvim_elastic_contact(fvim_ctx* ctx, const void* h, double W, void* p, const fvim_opts* opts,
+                         int* iters, double* err);
+
+/*
+ * fvim_plasticity_solve -- DF-SANE solve (Sec. 4.3) of the implicit incremental equation
+ *   R[dE] = dE - grad^sym M[dT] - grad^sym N[C:deps_p(dE; S_n)] = 0   (Sec. 4.2)
+ * for a surface pressure increment dT, from the context's state S_n (not updated).
+ *   dT     device [N2][N1];  dE device [Nz][6][N2][N1] (output, strain increment);
+ *   deps_p device [Nz][6][N2][N1] or NULL, dep device [Nz][N2][N1] or NULL: the return
+ *          map of dE.  iters, res: host outputs (may be NULL).
+ */
+int fvim_plasticity_solve(fvim_ctx* ctx, const void* dT, void* dE, void* deps_p, void* dep,
+                          const fvim_opts* opts, int* iters, double* res);
+
+/*
+ * fvim_solve_contact -- elastic-plastic contact, Algorithm 1 of Sec. 5.2, for n_inc load
+ * increments loads[0..n_inc-1] (HOST array, total loads W), from the context's state.
+ *   h      device [N2][N1] surface profile.
+ *   p_out  device [N2][N1] contact pressure after the last increment (or NULL).
+ *   rep    host report (may be NULL).
+ * The plastic state (eps_p, e_p, sigma) and the last pressure are updated in the context
+ * after each converged increment.  Synchronises the stream.  Returns
+ * FVIM_ERR_NOT_CONVERGED if an increment reaches max_iter (the state is still updated).
+ */
+int fvim_solve_contact(fvim_ctx* ctx, const void* h, const double* loads, int n_inc,
+                       const fvim_opts* opts, void* p_out, fvim_report* rep);
+
 /*
  * fvim_apply_mindlin_noalloc -- the Mindlin apply of fvim_apply_mindlin without a
  * context and without any device allocation.  The paper has no counterpart: this entry

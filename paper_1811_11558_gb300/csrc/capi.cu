@@ -101,10 +101,14 @@ size_t nvox(const fvim_ctx* c) { return (size_t)c->nz * c->n2 * c->n1; }
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 void free_all(fvim_ctx* c) {
-  void* bufs[] = {c->z_dev, c->tw1, c->tw2, c->spec, c->nq, c->surf, c->surf_nq, c->st_eps_p, c->st_ep, c->st_sig};
+  void* bufs[] = {c->z_dev, c->tw1, c->tw2, c->spec, c->nq, c->surf, c->surf_nq, c->st_eps_p, c->st_ep, c->st_sig, c->st_T};
   for (void* b : bufs)
     if (b) cudaFree(b);
   free(c->z_host);
+  for (int i = 0; i < FVIM_NSOLVER_BUFS; ++i)
+    if (c->sv[i]) { cudaFree(c->sv[i]); c->sv[i] = nullptr; }
+  free(c->h_part);
+  c->h_part = nullptr;
   ProfState* ps = (ProfState*)c->prof;
   if (ps) {
     for (auto& v : ps->ev)
@@ -133,6 +137,8 @@ template <typename T> int upload_nodes(fvim_ctx* c) {
   if (cudaMemcpy(c->z_dev, h.data(), c->nz * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return FVIM_ERR_CUDA;
   return FVIM_OK;
 }
+
+}  // namespace
 
 template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, int kind, T* u3) {
   int rc;
@@ -207,7 +213,14 @@ template <typename T> int commit_t(fvim_ctx* c, const T* d_eps, const T* d_eps_p
   return rc;
 }
 
-}  // namespace
+template int apply_mindlin_t<float>(fvim_ctx*, const float*, float*, int, float*);
+template int apply_mindlin_t<double>(fvim_ctx*, const double*, double*, int, double*);
+template int apply_boussinesq_t<float>(fvim_ctx*, const float*, float*, float*, int);
+template int apply_boussinesq_t<double>(fvim_ctx*, const double*, double*, double*, int);
+template int return_map_t<float>(fvim_ctx*, const float*, float*, float*);
+template int return_map_t<double>(fvim_ctx*, const double*, double*, double*);
+template int commit_t<float>(fvim_ctx*, const float*, const float*, const float*);
+template int commit_t<double>(fvim_ctx*, const double*, const double*, const double*);
 
 extern "C" {
 
@@ -272,7 +285,7 @@ int fvim_create(fvim_ctx** out, int n1, int n2, int nz, const double* z_nodes, d
       {&c->spec, (size_t)nz * 6 * n2 * c->h1 * cs}, {&c->nq, (size_t)nz * 6 * n2 * es},
       {&c->surf, (size_t)n2 * c->h1 * cs},          {&c->surf_nq, (size_t)n2 * es},
       {&c->st_eps_p, nv * 6 * es},                   {&c->st_ep, nv * es},
-      {&c->st_sig, nv * 6 * es}};
+      {&c->st_sig, nv * 6 * es},                   {&c->st_T, (size_t)n2 * n1 * es}};
   for (auto& a : al) {
     if (cudaMalloc(a.p, a.bytes) != cudaSuccess) { cudaGetLastError(); free_all(c); delete c; return FVIM_ERR_OOM; }
     if (cudaMemset(*a.p, 0, a.bytes) != cudaSuccess) { free_all(c); delete c; return FVIM_ERR_CUDA; }

@@ -278,7 +278,7 @@ __device__ __forceinline__ ModeGeom<T> mode_geom(int k1, int k2, int n2, double 
 // ----------------------------------------------------------------------------------
 // Mindlin depth kernel
 // grid: (h1 / KT, n2); block: KT * nch threads, thread = (chunk, k1 column)
-// smem: W[nz][6][KT] (rotated in place) + Pst[max(nz, 2 nch)][6][KT]
+// smem: W[nz][6][KT] (rotated in place) + Pst[max(nz, 2 nch + 1)][6][KT]
 // ----------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __restrict__ spec, typename Cx<T>::t* __restrict__ surf,
@@ -358,25 +358,46 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
   __syncthreads();
 
   // 4. carries: A at node n0 from all chunks above, P at node e1 from all chunks below,
-  //    and the complete + branch at x3 = 0 for the image term
-  Mom<V> Ain, Pin, P0;
-  mom_zero(Ain);
-  mom_zero(Pin);
-  mom_zero(P0);
+  //    and the complete + branch at x3 = 0 for the image term.  One exclusive scan per
+  //    branch and mode (thread ch 0: downwards, thread ch 1: upwards), in place over the
+  //    chunk summaries: slot j ends up holding the carry into chunk j.
+  Mom<V>* P0s = SA + (size_t)nch * KT;  // [KT]
   if (active && !special) {
-    for (int j = 0; j < ch; ++j) {
-      const int a0 = j * C, a1 = min(j * C + C, nz - 1);
-      propA(Ain, g.q * (zn[a1] - zn[a0]));
-      mom_add(Ain, SA[j * KT + kt]);
+    const int pch = nch > 1 ? 1 : 0;
+    if (ch == 0) {
+      Mom<V> run;
+      mom_zero(run);
+      for (int j = 0; j < nch; ++j) {
+        const int a0 = j * C, a1 = min(j * C + C, nz - 1);
+        const Mom<V> sj = SA[j * KT + kt];
+        SA[j * KT + kt] = run;
+        propA(run, g.q * (zn[a1] - zn[a0]));
+        mom_add(run, sj);
+      }
     }
-    for (int j = nch - 1; j >= 0; --j) {
-      const int a0 = j * C, a1 = min(j * C + C, nz - 1);
-      if (a0 >= nz) continue;
-      propP(P0, g.q * (zn[a1] - zn[a0]));
-      mom_add(P0, SP[j * KT + kt]);
-      if (j == ch + 1) Pin = P0;
+    if (ch == pch) {
+      Mom<V> run;
+      mom_zero(run);
+      for (int j = nch - 1; j >= 0; --j) {
+        const int a0 = j * C, a1 = min(j * C + C, nz - 1);
+        const Mom<V> sj = SP[j * KT + kt];
+        SP[j * KT + kt] = run;
+        propP(run, g.q * (zn[a1] - zn[a0]));
+        mom_add(run, sj);
+      }
+      P0s[kt] = run;
     }
-    if (ch == nch - 1) mom_zero(Pin);
+  }
+  __syncthreads();
+  Mom<V> Ain, Pin, P0;
+  if (active && !special) {
+    Ain = SA[ch * KT + kt];
+    Pin = SP[ch * KT + kt];
+    P0 = P0s[kt];
+  } else {
+    mom_zero(Ain);
+    mom_zero(Pin);
+    mom_zero(P0);
   }
   // surface traction of the full-space field (A = 0 at x3 = 0), cancelled by the image
   V tr[3];
@@ -567,7 +588,7 @@ template <typename T> int launch_mindlin_depth(const fvim_ctx* c, int out_kind, 
   if (C < 2) C = 2;
   const int nch = (nz + C - 1) / C;
   const int threads = KT * nch;
-  const int prow = nz > 2 * nch ? nz : 2 * nch;
+  const int prow = nz > 2 * nch + 1 ? nz : 2 * nch + 1;
   const size_t smem = (size_t)nz * 6 * KT * sizeof(V) + (size_t)prow * KT * sizeof(Mom<V>);
   if (smem > 227 * 1024) return FVIM_ERR_UNSUPPORTED;
   cudaFuncSetAttribute(k_mindlin_depth<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

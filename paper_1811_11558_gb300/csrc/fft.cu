@@ -209,6 +209,198 @@ __global__ void __launch_bounds__(MaxT<T>::v) k_rows_inv1(const typename Cx<T>::
   }
 }
 
+
+// ================================================================================
+// Register-resident kernels (n >= 8): each thread keeps 8 strided elements of its
+// transform in registers for all stages (reg_stage); shared memory is only the
+// exchange between stages.  Columns keep the KC transforms of a CTA interleaved
+// (128-byte rows, conflict-free); rows keep each transform contiguous with one pad
+// slot every 8 entries (conflict-free Stockham scatter).
+// ================================================================================
+__device__ __forceinline__ int padi(int p) { return p + (p >> 3); }
+
+// columns: CTA = KC consecutive k1 columns of one plane, KC * n2/8 threads
+template <typename T, bool INV, int KC>
+__global__ void __launch_bounds__(1024) k_cols8(typename Cx<T>::t* __restrict__ planes,
+                                                const typename Cx<T>::t* __restrict__ tw, int n2, int h1) {
+  typedef typename Cx<T>::t V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* buf = reinterpret_cast<V*>(smraw);  // [n2][KC]
+  const int f = threadIdx.x % KC, t = threadIdx.x / KC;
+  const int T8 = n2 >> 3;
+  V* col = planes + (size_t)blockIdx.y * n2 * h1 + (size_t)blockIdx.x * KC + f;
+  V v[8];
+  int pos[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) v[m] = col[(size_t)(t + m * T8) * h1];
+  int Ns = 1, rem = n2;
+  bool first = true;
+  while (rem > 1) {
+    const int R = fft_radix(rem);
+    const bool last = (rem == R);
+    if (!first) {
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < 8; ++m) v[m] = buf[(t + m * T8) * KC + f];
+      if (!last) __syncthreads();
+    }
+    reg_stage<V, INV>(v, pos, t, n2, R, Ns, tw);
+    if (!last) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) buf[pos[m] * KC + f] = v[m];
+    }
+    first = false;
+    Ns *= R;
+    rem /= R;
+  }
+#pragma unroll
+  for (int m = 0; m < 8; ++m) col[(size_t)(t + m * T8) * h1] = v[m];
+}
+
+// forward rows with the Hooke prologue: CTA = RB rows of one layer, RB * n1/8 threads;
+// a thread runs the three pair transforms (w11 + i w22, w33 + i w23, w13 + i w12)
+template <typename T, int RB>
+__global__ void __launch_bounds__(256) k_rows_fwd6_r8(const T* __restrict__ eps_p, typename Cx<T>::t* __restrict__ spec,
+                                                      T* __restrict__ nq, const typename Cx<T>::t* __restrict__ tw,
+                                                      int n1, int n2, int z0, T lam, T mu) {
+  typedef typename Cx<T>::t V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* buf = reinterpret_cast<V*>(smraw);  // [RB][3][padi(n1)]
+  const int T8 = n1 >> 3;
+  const int ld = n1 + T8;
+  const int r = threadIdx.x / T8, t = threadIdx.x - r * T8;
+  const int z = z0 + blockIdx.y;
+  const int x2 = blockIdx.x * RB + r;
+  const int h1 = n1 >> 1;
+  V v[3][8];
+  int pos[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int x1 = t + m * T8;
+    T e[6], w[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) e[c] = eps_p[(((size_t)z * 6 + c) * n2 + x2) * n1 + x1];
+    hooke6(e, w, lam, mu);
+    v[0][m] = mk<V>(w[0], w[1]);
+    v[1][m] = mk<V>(w[2], w[3]);
+    v[2][m] = mk<V>(w[4], w[5]);
+  }
+  V* rowbuf = buf + (size_t)r * 3 * ld;
+  int Ns = 1, rem = n1;
+  bool first = true;
+  while (rem > 1) {
+    const int R = fft_radix(rem);
+    if (!first) {
+      __syncthreads();
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[p][m] = rowbuf[p * ld + padi(t + m * T8)];
+      __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      reg_stage<V, false>(v[p], pos, t, n1, R, Ns, tw);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) rowbuf[p * ld + padi(pos[m])] = v[p][m];
+    }
+    first = false;
+    Ns *= R;
+    rem /= R;
+  }
+  __syncthreads();
+  // Hermitian split of the natural-order outputs: k in [0, h1]
+  for (int idx = t; idx < 3 * (h1 + 1); idx += T8) {
+    const int p = idx / (h1 + 1), k = idx - p * (h1 + 1);
+    V A, B;
+    split_pair(rowbuf[p * ld + padi(k)], rowbuf[p * ld + padi((n1 - k) & (n1 - 1))], A, B);
+    const int ca = 2 * p, cb = 2 * p + 1;
+    if (k < h1) {
+      spec[(((size_t)z * 6 + ca) * n2 + x2) * h1 + k] = A;
+      spec[(((size_t)z * 6 + cb) * n2 + x2) * h1 + k] = B;
+    } else {
+      nq[((size_t)z * 6 + ca) * n2 + x2] = A.x;
+      nq[((size_t)z * 6 + cb) * n2 + x2] = B.x;
+    }
+  }
+}
+
+// inverse rows: Hermitian rebuild straight from the half spectrum into registers,
+// inverse transforms, scaled real/imaginary parts stored per component
+template <typename T, int RB>
+__global__ void __launch_bounds__(256) k_rows_inv6_r8(const typename Cx<T>::t* __restrict__ spec,
+                                                      const T* __restrict__ nq, T* __restrict__ out,
+                                                      const typename Cx<T>::t* __restrict__ tw, int n1, int n2, int z0,
+                                                      T nq_scale, T scale) {
+  typedef typename Cx<T>::t V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* buf = reinterpret_cast<V*>(smraw);  // [RB][3][padi(n1)]
+  const int T8 = n1 >> 3;
+  const int ld = n1 + T8;
+  const int r = threadIdx.x / T8, t = threadIdx.x - r * T8;
+  const int z = z0 + blockIdx.y;
+  const int x2 = blockIdx.x * RB + r;
+  const int h1 = n1 >> 1;
+  V v[3][8];
+  int pos[8];
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const int ca = 2 * p, cb = 2 * p + 1;
+    const V* sa = spec + (((size_t)z * 6 + ca) * n2 + x2) * h1;
+    const V* sb = spec + (((size_t)z * 6 + cb) * n2 + x2) * h1;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int k = t + m * T8;
+      V A, B;
+      if (k == h1) {
+        A = mk<V>(nq_scale == (T)0 ? (T)0 : nq_scale * nq[((size_t)z * 6 + ca) * n2 + x2], 0);
+        B = mk<V>(nq_scale == (T)0 ? (T)0 : nq_scale * nq[((size_t)z * 6 + cb) * n2 + x2], 0);
+      } else if (k < h1) {
+        A = sa[k];
+        B = sb[k];
+      } else {
+        A = cconj(sa[n1 - k]);
+        B = cconj(sb[n1 - k]);
+      }
+      v[p][m] = cadd(A, cmuli(B));
+    }
+  }
+  V* rowbuf = buf + (size_t)r * 3 * ld;
+  int Ns = 1, rem = n1;
+  bool first = true;
+  while (rem > 1) {
+    const int R = fft_radix(rem);
+    const bool last = (rem == R);
+    if (!first) {
+      __syncthreads();
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[p][m] = rowbuf[p * ld + padi(t + m * T8)];
+      if (!last) __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      reg_stage<V, true>(v[p], pos, t, n1, R, Ns, tw);
+      if (!last) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) rowbuf[p * ld + padi(pos[m])] = v[p][m];
+      }
+    }
+    first = false;
+    Ns *= R;
+    rem /= R;
+  }
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int x1 = t + m * T8;
+      out[(((size_t)z * 6 + 2 * p) * n2 + x2) * n1 + x1] = v[p][m].x * scale;
+      out[(((size_t)z * 6 + 2 * p + 1) * n2 + x2) * n1 + x1] = v[p][m].y * scale;
+    }
+}
+
 inline int round_threads(int t, int cap) {
   t = (t + 31) / 32 * 32;
   if (t < 64) t = 64;
@@ -241,9 +433,34 @@ template <typename K> void set_smem(K kern, size_t smem) {
 
 }  // namespace
 
+// rows per CTA of the register-resident row kernels (256 threads, n1/8 per row)
+inline int r8_rows(int n1, int n2) {
+  int rb = 256 / (n1 >> 3);
+  if (rb > 8) rb = 8;
+  while (rb > n2) rb >>= 1;
+  return rb;
+}
+
 template <typename T> int launch_rows_fwd6(const fvim_ctx* c, const T* eps_p, int z0, int nzs) {
   typedef typename Cx<T>::t V;
   const int n1 = c->n1, n2 = c->n2;
+  if (n1 >= 8 && n1 <= 2048) {
+    const int RB = r8_rows(n1, n2);
+    const int threads = RB * (n1 >> 3);
+    const size_t smem = (size_t)RB * 3 * (n1 + n1 / 8) * sizeof(V);
+    dim3 grid(n2 / RB, nzs);
+    const T lam = (T)c->lam, mu = (T)c->mu;
+#define RF(RBV)                                                                                    \
+  if (RB == RBV) {                                                                                 \
+    set_smem(k_rows_fwd6_r8<T, RBV>, smem);                                                        \
+    k_rows_fwd6_r8<T, RBV><<<grid, threads, smem, c->stream>>>(eps_p, (V*)c->spec, (T*)c->nq,      \
+                                                               (const V*)c->tw1, n1, n2, z0, lam, mu); \
+  }
+    RF(8) RF(4) RF(2) RF(1)
+#undef RF
+    FVIM_CUDA_CHECK_LAUNCH();
+    return FVIM_OK;
+  }
   const int RB = row_block<T>(n1, n2);
   int maxi, threads;
   if (n2 % RB || !fft_shape<T>(3 * RB, n1, maxi, threads)) return FVIM_ERR_UNSUPPORTED;
@@ -281,6 +498,25 @@ template <typename T> int launch_rows_fwd1(const fvim_ctx* c, const T* f) {
 template <typename T> int launch_cols(const fvim_ctx* c, bool inverse, void* planes, int nplanes) {
   typedef typename Cx<T>::t V;
   const int n2 = c->n2, h1 = c->h1;
+  if (n2 >= 8) {
+    // KC columns per CTA: 128-byte rows, at most 1024 threads
+    int kc = (int)(128 / sizeof(V));
+    while (kc > 1 && kc * (n2 >> 3) > 1024) kc >>= 1;
+    if (kc > h1) kc = h1;
+    const int threads = kc * (n2 >> 3);
+    const size_t smem = (size_t)kc * n2 * sizeof(V);
+    dim3 grid(h1 / kc, nplanes);
+#define C8(INV, KCV)                                                                                  \
+  if (inverse == INV && kc == KCV) {                                                                  \
+    set_smem(k_cols8<T, INV, KCV>, smem);                                                             \
+    k_cols8<T, INV, KCV><<<grid, threads, smem, c->stream>>>((V*)planes, (const V*)c->tw2, n2, h1);   \
+  }
+    C8(true, 16) C8(false, 16) C8(true, 8) C8(false, 8) C8(true, 4) C8(false, 4)
+    C8(true, 2) C8(false, 2) C8(true, 1) C8(false, 1)
+#undef C8
+    FVIM_CUDA_CHECK_LAUNCH();
+    return FVIM_OK;
+  }
   // columns per CTA: 128-byte row segments when possible, within smem and item budgets
   int kc = (int)(128 / sizeof(V));
   while (kc > 1 && (size_t)kc * (n2 + 1) * sizeof(V) > 96 * 1024) kc >>= 1;
@@ -304,12 +540,28 @@ template <typename T> int launch_cols(const fvim_ctx* c, bool inverse, void* pla
 template <typename T> int launch_rows_inv6(const fvim_ctx* c, T* out, T nq_scale, int z0, int nzs) {
   typedef typename Cx<T>::t V;
   const int n1 = c->n1, n2 = c->n2;
+  const T scale = (T)(1.0 / ((double)n1 * (double)n2));
+  if (n1 >= 8 && n1 <= 2048) {
+    const int RB = r8_rows(n1, n2);
+    const int threads = RB * (n1 >> 3);
+    const size_t smem = (size_t)RB * 3 * (n1 + n1 / 8) * sizeof(V);
+    dim3 grid(n2 / RB, nzs);
+#define RI(RBV)                                                                                         \
+  if (RB == RBV) {                                                                                      \
+    set_smem(k_rows_inv6_r8<T, RBV>, smem);                                                             \
+    k_rows_inv6_r8<T, RBV><<<grid, threads, smem, c->stream>>>((const V*)c->spec, (const T*)c->nq, out, \
+                                                               (const V*)c->tw1, n1, n2, z0, nq_scale, scale); \
+  }
+    RI(8) RI(4) RI(2) RI(1)
+#undef RI
+    FVIM_CUDA_CHECK_LAUNCH();
+    return FVIM_OK;
+  }
   const int RB = row_block<T>(n1, n2);
   int maxi, threads;
   if (n2 % RB || !fft_shape<T>(3 * RB, n1, maxi, threads)) return FVIM_ERR_UNSUPPORTED;
   const size_t smem = (size_t)RB * 3 * n1 * sizeof(V);
   dim3 grid(n2 / RB, nzs);
-  const T scale = (T)(1.0 / ((double)n1 * (double)n2));
   const V* spec = (const V*)c->spec;
   const T* nq = (const T*)c->nq;
   const V* tw = (const V*)c->tw1;

@@ -149,8 +149,65 @@ __device__ void block_fft(V* buf, int n, int nfft, int fstride, const V* tw) {
 }
 
 // ---------------------------------------------------------------------------
+// Register-resident Stockham FFT (n >= 8): thread t of an FFT holds the 8 strided
+// elements x[t + m n/8], m = 0..7, for the whole transform.  A stage of radix R
+// (8, 4 or 2; plan of fft_radix) runs 1, 2 or 4 butterflies per thread on those
+// registers and reports, for every register slot, the natural index its result
+// belongs to; between stages the values go through shared memory.  After the last
+// stage slot m holds the output at index t + m n/8 (natural order).
+// ---------------------------------------------------------------------------
+template <typename V, bool INV>
+__device__ __forceinline__ void reg_stage(V (&v)[8], int (&pos)[8], int t, int n, int R, int Ns, const V* tw) {
+  const int T8 = n >> 3;
+  if (R == 8) {
+    const int k = t & (Ns - 1);
+    const int step = n / (Ns * 8);
+#pragma unroll
+    for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], twiddle<V, INV>(tw, (r * k * step) & (n - 1)));
+    dft8<V, INV>(v);
+    const int base = (t / Ns) * Ns * 8 + k;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) pos[r] = base + r * Ns;
+  } else if (R == 4) {
+    const int step = n / (Ns * 4);
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const int b = t + g * T8;
+      const int k = b & (Ns - 1);
+      V u[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) u[r] = v[2 * r + g];
+#pragma unroll
+      for (int r = 1; r < 4; ++r) u[r] = cmul(u[r], twiddle<V, INV>(tw, (r * k * step) & (n - 1)));
+      dft4<V, INV>(u);
+      const int base = (b / Ns) * Ns * 4 + k;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        v[2 * r + g] = u[r];
+        pos[2 * r + g] = base + r * Ns;
+      }
+    }
+  } else {
+    const int step = n / (Ns * 2);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int b = t + m * T8;
+      const int k = b & (Ns - 1);
+      V a = v[m], c = cmul(v[m + 4], twiddle<V, INV>(tw, (k * step) & (n - 1)));
+      v[m] = cadd(a, c);
+      v[m + 4] = csub(a, c);
+      const int base = (b / Ns) * Ns * 2 + k;
+      pos[m] = base;
+      pos[m + 4] = base + Ns;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
+#define FVIM_NSOLVER_BUFS 24
+
 struct fvim_ctx {
   int n1, n2, nz, h1;
   int prec;  // FVIM_FP32 / FVIM_FP64
@@ -171,8 +228,13 @@ struct fvim_ctx {
   void* st_eps_p; // T[nz][6][n2][n1]
   void* st_ep;    // T[nz][n2][n1]
   void* st_sig;   // T[nz][6][n2][n1]
+  void* st_T;     // T[n2][n1] contact pressure of the last converged increment
   int last_kernels;
   void* prof;  // ProfState* (capi.cu) or NULL
+  // solver workspace (solvers.cu), allocated on first use
+  void* sv[FVIM_NSOLVER_BUFS];
+  double* h_part;  // host copy of reduction partials
+  long n_applies;  // Mindlin applies issued by the solvers
 };
 
 // kernel kinds for fvim_profile_read
@@ -197,6 +259,12 @@ template <typename T> int launch_boussinesq(const fvim_ctx* c, int out_kind, boo
 template <typename T> int launch_return_map(const fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep);
 template <typename T> int launch_commit(const fvim_ctx* c, const T* d_eps, const T* d_eps_p, const T* d_ep);
 template <typename T> int launch_zero_nq(const fvim_ctx* c);
+
+// launch sequences of the entry points (capi.cu), used by the solvers
+template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, int kind, T* u3);
+template <typename T> int apply_boussinesq_t(fvim_ctx* c, const T* p, T* u3, T* vol, int kind);
+template <typename T> int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep);
+template <typename T> int commit_t(fvim_ctx* c, const T* d_eps, const T* d_eps_p, const T* d_ep);
 
 #define FVIM_CUDA_CHECK_LAUNCH()                          \
   do {                                                    \

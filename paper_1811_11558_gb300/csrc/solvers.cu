@@ -1,0 +1,579 @@
+// Solvers of the elastic-plastic contact problem (declarations in include/fvim.h):
+//   * elastic contact: constrained conjugate gradient of Polonsky & Keer (1999) on the dual
+//     problem with the total-load constraint (Sec. 5.1, Eq. total_pressure);
+//   * plastic increment: DF-SANE of La Cruz, Martinez & Raydan (2006) on the residual of
+//     the implicit incremental equation (Sec. 4.2, Sec. 4.3);
+//   * coupling: Algorithm 1 (Sec. 5.2).
+// Vectors stay on the device in the context's precision.  Every reduction is a grid of
+// fixed blocks writing FP64 partial sums, added on the host in block order, so results
+// are bitwise reproducible.  Loops run on the host and are capped.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "fvim_internal.cuh"
+
+namespace {
+
+constexpr int RT = 256;       // threads of a reduction block
+constexpr int RMAXB = 1024;   // blocks of a reduction grid
+constexpr int NVMAX = 2;      // values reduced per pass
+
+// surface buffers [N2][N1]
+enum { S_P = 0, S_POLD, S_T, S_G, S_U, S_R, S_H, S_H0, S_DU, S_DUPREV, S_TPREV, S_DT, S_NSURF };
+// volume buffers [Nz][6][N2][N1] and the scalar field [Nz][N2][N1]
+enum { V_X = S_NSURF, V_F, V_XT, V_FT, V_B, V_DEP, V_TMP, V_DE, V_EP, V_PART, V_WZ, V_END };
+static_assert(V_END <= FVIM_NSOLVER_BUFS, "workspace slots");
+
+template <typename T> size_t esz() { return sizeof(T); }
+
+template <typename T> int ensure_ws(fvim_ctx* c) {
+  if (c->sv[V_PART]) return FVIM_OK;
+  const size_t ns = (size_t)c->n1 * c->n2, nv = ns * c->nz;
+  for (int i = 0; i < S_NSURF; ++i)
+    if (cudaMalloc(&c->sv[i], ns * sizeof(T)) != cudaSuccess) return FVIM_ERR_OOM;
+  for (int i = V_X; i <= V_DE; ++i)
+    if (cudaMalloc(&c->sv[i], nv * 6 * sizeof(T)) != cudaSuccess) return FVIM_ERR_OOM;
+  if (cudaMalloc(&c->sv[V_EP], nv * sizeof(T)) != cudaSuccess) return FVIM_ERR_OOM;
+  if (cudaMalloc(&c->sv[V_PART], (size_t)RMAXB * NVMAX * sizeof(double)) != cudaSuccess) return FVIM_ERR_OOM;
+  if (cudaMalloc(&c->sv[V_WZ], (size_t)c->nz * sizeof(double)) != cudaSuccess) return FVIM_ERR_OOM;
+  c->h_part = (double*)malloc((size_t)RMAXB * NVMAX * sizeof(double));
+  if (!c->h_part) return FVIM_ERR_OOM;
+  // trapezoid weights of the depth nodes times the cell area dA (discrete L2 product)
+  std::vector<double> wz(c->nz, 0.0);
+  const double dA = c->L1 * c->L2 / (double)ns;
+  for (int i = 0; i + 1 < c->nz; ++i) {
+    const double h = c->z_host[i + 1] - c->z_host[i];
+    wz[i] += 0.5 * h * dA;
+    wz[i + 1] += 0.5 * h * dA;
+  }
+  if (cudaMemcpy(c->sv[V_WZ], wz.data(), c->nz * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return FVIM_ERR_CUDA;
+  for (int i = 0; i < V_PART; ++i)
+    if (cudaMemset(c->sv[i], 0, (i < S_NSURF ? ns : (i == V_EP ? nv : nv * 6)) * sizeof(T)) != cudaSuccess)
+      return FVIM_ERR_CUDA;
+  return FVIM_OK;
+}
+
+template <typename T> T* S(fvim_ctx* c, int i) { return (T*)c->sv[i]; }
+
+// ---- block reduction of NV doubles into partial[blockIdx.x][NV] -------------------
+template <int NV> __device__ __forceinline__ void block_reduce(double (&v)[NV], double* partial) {
+  __shared__ double sh[NV][RT / 32];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double x = v[j];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) sh[j][threadIdx.x >> 5] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double s = 0;
+      for (int w = 0; w < RT / 32; ++w) s += sh[j][w];
+      partial[blockIdx.x * NV + j] = s;
+    }
+  }
+}
+
+inline int rgrid(size_t n) {
+  size_t b = (n + RT - 1) / RT;
+  return (int)std::min<size_t>(std::max<size_t>(b, 1), RMAXB);
+}
+
+// copy the partials of a reduction grid and add them in block order
+template <int NV> int finish(fvim_ctx* c, int nblk, double* out) {
+  if (cudaMemcpyAsync(c->h_part, c->sv[V_PART], (size_t)nblk * NV * sizeof(double), cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess)
+    return FVIM_ERR_CUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
+  for (int j = 0; j < NV; ++j) out[j] = 0;
+  for (int b = 0; b < nblk; ++b)
+    for (int j = 0; j < NV; ++j) out[j] += c->h_part[b * NV + j];
+  return FVIM_OK;
+}
+
+// ---- Polonsky-Keer kernels (surface, n = N1 N2) ------------------------------------
+// sum over the contact set of u - h, and its size
+template <typename T>
+__global__ void k_pk_stats(const T* __restrict__ u, const T* __restrict__ h, const T* __restrict__ p, size_t n,
+                           double* part) {
+  double v[2] = {0, 0};
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT)
+    if (p[i] > 0) { v[0] += (double)u[i] - (double)h[i]; v[1] += 1; }
+  block_reduce<2>(v, part);
+}
+// g = u - h - gbar; sum over the contact set of g^2
+template <typename T>
+__global__ void k_pk_g(const T* __restrict__ u, const T* __restrict__ h, const T* __restrict__ p, T* __restrict__ g,
+                       double gbar, size_t n, double* part) {
+  double v[1] = {0};
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
+    const T gi = (T)((double)u[i] - (double)h[i] - gbar);
+    g[i] = gi;
+    if (p[i] > 0) v[0] += (double)gi * (double)gi;
+  }
+  block_reduce<1>(v, part);
+}
+// conjugate direction t = g + beta t on the contact set, 0 elsewhere
+template <typename T>
+__global__ void k_pk_dir(const T* __restrict__ g, const T* __restrict__ p, T* __restrict__ t, double beta, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT)
+    t[i] = p[i] > 0 ? (T)((double)g[i] + beta * (double)t[i]) : (T)0;
+}
+// sum over the contact set of r
+template <typename T>
+__global__ void k_pk_rsum(const T* __restrict__ r, const T* __restrict__ p, size_t n, double* part) {
+  double v[1] = {0};
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT)
+    if (p[i] > 0) v[0] += (double)r[i];
+  block_reduce<1>(v, part);
+}
+// <g, t> and <r - rbar, t> over the contact set
+template <typename T>
+__global__ void k_pk_dots(const T* __restrict__ g, const T* __restrict__ t, const T* __restrict__ r,
+                          const T* __restrict__ p, double rbar, size_t n, double* part) {
+  double v[2] = {0, 0};
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT)
+    if (p[i] > 0) {
+      v[0] += (double)g[i] * (double)t[i];
+      v[1] += ((double)r[i] - rbar) * (double)t[i];
+    }
+  block_reduce<2>(v, part);
+}
+// p <- max(p - tau t, 0); penetrating points with zero pressure get -tau g
+template <typename T>
+__global__ void k_pk_update(T* __restrict__ p, T* __restrict__ pold, const T* __restrict__ t,
+                            const T* __restrict__ g, double tau, size_t n, double* part) {
+  double v[2] = {0, 0};
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
+    const T po = p[i];
+    T pn = (T)fmax((double)po - tau * (double)t[i], 0.0);
+    const bool ol = (pn == (T)0) && (g[i] < (T)0);
+    if (ol) pn = (T)(-tau * (double)g[i]);
+    pold[i] = po;
+    p[i] = pn;
+    v[0] += (double)pn;
+    v[1] += ol ? 1.0 : 0.0;
+  }
+  block_reduce<2>(v, part);
+}
+// p <- s p; sum |p - p_old| and the size of the contact set
+template <typename T>
+__global__ void k_pk_scale(T* __restrict__ p, const T* __restrict__ pold, double s, size_t n, double* part) {
+  double v[2] = {0, 0};
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
+    const T pn = (T)(s * (double)p[i]);
+    p[i] = pn;
+    v[0] += fabs((double)pn - (double)pold[i]);
+    v[1] += pn > (T)0 ? 1.0 : 0.0;
+  }
+  block_reduce<2>(v, part);
+}
+template <typename T> __global__ void k_fill(T* __restrict__ a, T v, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) a[i] = v;
+}
+// sum of a and of a^2
+template <typename T> __global__ void k_sum2(const T* __restrict__ a, size_t n, double* part) {
+  double v[2] = {0, 0};
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
+    v[0] += (double)a[i];
+    v[1] += (double)a[i] * (double)a[i];
+  }
+  block_reduce<2>(v, part);
+}
+// c = a + s b (elementwise)
+template <typename T>
+__global__ void k_axpby(T* __restrict__ cc, const T* __restrict__ a, double s, const T* __restrict__ b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT)
+    cc[i] = (T)((double)a[i] + s * (double)b[i]);
+}
+// ||a - b||^2
+template <typename T>
+__global__ void k_diff2(const T* __restrict__ a, const T* __restrict__ b, size_t n, double* part) {
+  double v[1] = {0};
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
+    const double d = (double)a[i] - (double)b[i];
+    v[0] += d * d;
+  }
+  block_reduce<1>(v, part);
+}
+
+// Algorithm 1: relaxed = dU_prev + lambda (dU - dU_prev); H = H0 - relaxed; dU_prev = dU
+template <typename T>
+__global__ void k_relax(T* __restrict__ H, const T* __restrict__ H0, T* __restrict__ dUp, const T* __restrict__ dU,
+                        double lam, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
+    const double relaxed = (double)dUp[i] + lam * ((double)dU[i] - (double)dUp[i]);
+    H[i] = (T)((double)H0[i] - relaxed);
+    dUp[i] = dU[i];
+  }
+}
+// number of positive entries
+template <typename T> __global__ void k_count_pos(const T* __restrict__ a, size_t n, double* part) {
+  double v[1] = {0};
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT)
+    v[0] += a[i] > (T)0 ? 1.0 : 0.0;
+  block_reduce<1>(v, part);
+}
+
+// ---- DF-SANE kernels (volume [Nz][6][N2][N1], weighted L2 product) ------------------
+__device__ __forceinline__ double vol_weight(const double* wz, size_t i, size_t nxy) {
+  const size_t zc = i / nxy;
+  const int c = (int)(zc % 6);
+  return wz[zc / 6] * (c < 3 ? 1.0 : 2.0);
+}
+// F = x - b - tmp ; <F, F>
+template <typename T>
+__global__ void k_df_res(const T* __restrict__ x, const T* __restrict__ b, const T* __restrict__ tmp,
+                         T* __restrict__ F, const double* __restrict__ wz, size_t nxy, size_t n, double* part) {
+  double v[1] = {0};
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
+    const T f = x[i] - b[i] - tmp[i];
+    F[i] = f;
+    v[0] += vol_weight(wz, i, nxy) * (double)f * (double)f;
+  }
+  block_reduce<1>(v, part);
+}
+// <s, s> and <s, y> with s = xn - x, y = Fn - F
+template <typename T>
+__global__ void k_df_sy(const T* __restrict__ x, const T* __restrict__ xn, const T* __restrict__ F,
+                        const T* __restrict__ Fn, const double* __restrict__ wz, size_t nxy, size_t n, double* part) {
+  double v[2] = {0, 0};
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
+    const double w = vol_weight(wz, i, nxy);
+    const double s = (double)xn[i] - (double)x[i];
+    const double y = (double)Fn[i] - (double)F[i];
+    v[0] += w * s * s;
+    v[1] += w * s * y;
+  }
+  block_reduce<2>(v, part);
+}
+
+template <typename T> int sum2(fvim_ctx* c, const T* a, size_t n, double* out) {
+  const int g = rgrid(n);
+  k_sum2<T><<<g, RT, 0, c->stream>>>(a, n, (double*)c->sv[V_PART]);
+  FVIM_CUDA_CHECK_LAUNCH();
+  return finish<2>(c, g, out);
+}
+
+template <typename T> int axpby(fvim_ctx* c, T* dst, const T* a, double s, const T* b, size_t n) {
+  k_axpby<T><<<rgrid(n), RT, 0, c->stream>>>(dst, a, s, b, n);
+  FVIM_CUDA_CHECK_LAUNCH();
+  return FVIM_OK;
+}
+
+// surface displacement u = K*p of the Boussinesq operator (u3_hat = 2 p_hat / (E* q))
+template <typename T> int conv(fvim_ctx* c, const T* p, T* u) { return apply_boussinesq_t<T>(c, p, u, nullptr, FVIM_STRAIN); }
+
+// ---- Polonsky-Keer constrained conjugate gradient ----------------------------------
+template <typename T>
+int elastic_contact_t(fvim_ctx* c, const T* h, double W, T* p, const fvim_opts* o, int* iters, double* err_out) {
+  const size_t n = (size_t)c->n1 * c->n2;
+  const double dA = c->L1 * c->L2 / (double)n;
+  double* part = (double*)c->sv[V_PART];
+  T *pold = S<T>(c, S_POLD), *t = S<T>(c, S_T), *g = S<T>(c, S_G), *u = S<T>(c, S_U), *r = S<T>(c, S_R);
+  const int grd = rgrid(n);
+  double v[2];
+  int rc;
+  // initial pressure: the given guess scaled to the load, or uniform
+  if ((rc = sum2<T>(c, p, n, v))) return rc;
+  if (v[0] > 0) {
+    k_axpby<T><<<grd, RT, 0, c->stream>>>(p, p, W / (dA * v[0]) - 1.0, p, n);
+  } else {
+    k_fill<T><<<grd, RT, 0, c->stream>>>(p, (T)(W / (c->L1 * c->L2)), n);
+  }
+  k_fill<T><<<grd, RT, 0, c->stream>>>(t, (T)0, n);
+  FVIM_CUDA_CHECK_LAUNCH();
+  double delta = 0, G_old = 1, err = INFINITY;
+  int it = 0;
+  for (it = 1; it <= o->cg_max_iter; ++it) {
+    if ((rc = conv<T>(c, p, u))) return rc;
+    k_pk_stats<T><<<grd, RT, 0, c->stream>>>(u, h, p, n, part);
+    FVIM_CUDA_CHECK_LAUNCH();
+    if ((rc = finish<2>(c, grd, v))) return rc;
+    const double nIc = v[1];
+    if (nIc <= 0) return FVIM_ERR_NONFINITE;
+    const double gbar = v[0] / nIc;
+    k_pk_g<T><<<grd, RT, 0, c->stream>>>(u, h, p, g, gbar, n, part);
+    FVIM_CUDA_CHECK_LAUNCH();
+    if ((rc = finish<1>(c, grd, v))) return rc;
+    const double G = v[0];
+    k_pk_dir<T><<<grd, RT, 0, c->stream>>>(g, p, t, delta * (G / G_old), n);
+    FVIM_CUDA_CHECK_LAUNCH();
+    G_old = G;
+    if ((rc = conv<T>(c, t, r))) return rc;
+    k_pk_rsum<T><<<grd, RT, 0, c->stream>>>(r, p, n, part);
+    FVIM_CUDA_CHECK_LAUNCH();
+    if ((rc = finish<1>(c, grd, v))) return rc;
+    const double rbar = v[0] / nIc;
+    k_pk_dots<T><<<grd, RT, 0, c->stream>>>(g, t, r, p, rbar, n, part);
+    FVIM_CUDA_CHECK_LAUNCH();
+    if ((rc = finish<2>(c, grd, v))) return rc;
+    const double tau = v[1] != 0 ? v[0] / v[1] : 0.0;
+    k_pk_update<T><<<grd, RT, 0, c->stream>>>(p, pold, t, g, tau, n, part);
+    FVIM_CUDA_CHECK_LAUNCH();
+    if ((rc = finish<2>(c, grd, v))) return rc;
+    delta = v[1] > 0 ? 0.0 : 1.0;
+    if (!(v[0] > 0) || !isfinite(v[0])) return FVIM_ERR_NONFINITE;
+    k_pk_scale<T><<<grd, RT, 0, c->stream>>>(p, pold, W / (dA * v[0]), n, part);
+    FVIM_CUDA_CHECK_LAUNCH();
+    if ((rc = finish<2>(c, grd, v))) return rc;
+    err = dA * v[0] / W;
+    if (err < o->cg_tol) break;
+  }
+  if (iters) *iters = std::min(it, o->cg_max_iter);
+  if (err_out) *err_out = err;
+  return err < o->cg_tol ? FVIM_OK : FVIM_ERR_NOT_CONVERGED;
+}
+
+// ---- DF-SANE on R[x] = x - b - grad^sym N[C:deps_p(x; S)] --------------------------
+template <typename T> struct DF {
+  fvim_ctx* c;
+  size_t n, nxy;
+  int grd;
+  // F(x) into Fx; returns ||F||^2 (weighted)
+  int eval(const T* x, T* Fx, double* f) {
+    int rc;
+    if ((rc = return_map_t<T>(c, x, S<T>(c, V_DEP), S<T>(c, V_EP)))) return rc;
+    if ((rc = apply_mindlin_t<T>(c, S<T>(c, V_DEP), S<T>(c, V_TMP), FVIM_STRAIN, nullptr))) return rc;
+    c->n_applies++;
+    k_df_res<T><<<grd, RT, 0, c->stream>>>(x, S<T>(c, V_B), S<T>(c, V_TMP), Fx, (const double*)c->sv[V_WZ], nxy, n,
+                                          (double*)c->sv[V_PART]);
+    FVIM_CUDA_CHECK_LAUNCH();
+    return finish<1>(c, grd, f);
+  }
+};
+
+template <typename T>
+int plasticity_t(fvim_ctx* c, const T* dT, T* dE, T* deps_p, T* dep, const fvim_opts* o, int* iters, double* res,
+                 long* evals_out) {
+  const size_t nxy = (size_t)c->n1 * c->n2, n = nxy * c->nz * 6;
+  DF<T> df{c, n, nxy, rgrid(n)};
+  int rc;
+  // elastic predictor b = grad^sym M[dT], start x0 = b
+  if ((rc = apply_boussinesq_t<T>(c, dT, nullptr, S<T>(c, V_B), FVIM_STRAIN))) return rc;
+  T* x = S<T>(c, V_X);
+  T* F = S<T>(c, V_F);
+  T* xt = S<T>(c, V_XT);
+  T* Ft = S<T>(c, V_FT);
+  if (cudaMemcpyAsync(x, S<T>(c, V_B), n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+    return FVIM_ERR_CUDA;
+  double f;
+  if ((rc = df.eval(x, F, &f))) return rc;
+  long evals = 1;
+  const double nF0 = sqrt(f);
+  const int M = 10;
+  const double gamma = 1e-4, smin = 1e-10, smax = 1e10, tmin = 0.1, tmax = 0.5;
+  std::vector<double> hist(1, f);
+  double sigma = 1.0;
+  int k = 0;
+  bool conv_ok = false;
+  for (k = 0; k < o->df_max_iter; ++k) {
+    if (!isfinite(f)) return FVIM_ERR_NONFINITE;
+    if (sqrt(f) <= o->df_tol_abs + o->df_tol_rel * nF0) { conv_ok = true; break; }
+    double fmax = 0;
+    for (size_t j = hist.size() > (size_t)M ? hist.size() - M : 0; j < hist.size(); ++j) fmax = std::max(fmax, hist[j]);
+    const double eta = nF0 / ((1.0 + k) * (1.0 + k));
+    double ap = 1, am = 1, fn = 0;
+    bool ok = false;
+    for (int bt = 0; bt < 60 && !ok; ++bt) {
+      double fp, fm;
+      // x + ap d with d = -sigma F
+      if ((rc = axpby<T>(c, xt, x, -ap * sigma, F, n))) return rc;
+      if ((rc = df.eval(xt, Ft, &fp))) return rc;
+      ++evals;
+      if (fp <= fmax + eta - gamma * ap * ap * f) { fn = fp; ok = true; break; }
+      if ((rc = axpby<T>(c, xt, x, am * sigma, F, n))) return rc;
+      if ((rc = df.eval(xt, Ft, &fm))) return rc;
+      ++evals;
+      if (fm <= fmax + eta - gamma * am * am * f) { fn = fm; ok = true; break; }
+      ap = std::min(std::max(ap * ap * f / (fp + (2 * ap - 1) * f), tmin * ap), tmax * ap);
+      am = std::min(std::max(am * am * f / (fm + (2 * am - 1) * f), tmin * am), tmax * am);
+    }
+    if (!ok) break;
+    double sv[2];
+    k_df_sy<T><<<df.grd, RT, 0, c->stream>>>(x, xt, F, Ft, (const double*)c->sv[V_WZ], nxy, n, (double*)c->sv[V_PART]);
+    FVIM_CUDA_CHECK_LAUNCH();
+    if ((rc = finish<2>(c, df.grd, sv))) return rc;
+    sigma = sv[1] != 0 ? sv[0] / sv[1] : INFINITY;
+    if (!(fabs(sigma) >= smin && fabs(sigma) <= smax)) {
+      const double nf = sqrt(fn);
+      sigma = nf > 1 ? 1.0 : (nf >= 1e-5 ? 1.0 / nf : 1e5);
+    }
+    std::swap(x, xt);
+    std::swap(F, Ft);
+    c->sv[V_X] = x;
+    c->sv[V_XT] = xt;
+    c->sv[V_F] = F;
+    c->sv[V_FT] = Ft;
+    f = fn;
+    hist.push_back(f);
+  }
+  if (!conv_ok && sqrt(f) <= o->df_tol_abs + o->df_tol_rel * nF0) conv_ok = true;
+  // outputs: dE = x and its return map
+  if (cudaMemcpyAsync(dE, x, n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
+  if (deps_p || dep) {
+    if ((rc = return_map_t<T>(c, x, deps_p ? deps_p : S<T>(c, V_DEP), dep ? dep : S<T>(c, V_EP)))) return rc;
+  }
+  if (iters) *iters = k;
+  if (res) *res = sqrt(f);
+  if (evals_out) *evals_out += evals;
+  return conv_ok ? FVIM_OK : FVIM_ERR_NOT_CONVERGED;
+}
+
+// ---- Algorithm 1 ---------------------------------------------------------------------
+template <typename T>
+int solve_contact_t(fvim_ctx* c, const T* h, const double* loads, int n_inc, const fvim_opts* o, T* p_out,
+                    fvim_report* rep) {
+  const size_t ns = (size_t)c->n1 * c->n2, nxy = ns, nv = nxy * c->nz;
+  const double dA = c->L1 * c->L2 / (double)ns;
+  int rc;
+  T *H0 = S<T>(c, S_H0), *H = S<T>(c, S_H), *dU = S<T>(c, S_DU), *dUp = S<T>(c, S_DUPREV);
+  T *P = S<T>(c, S_P), *Tprev = S<T>(c, S_TPREV), *dT = S<T>(c, S_DT);
+  T* dE = S<T>(c, V_DE);
+  const int gs = rgrid(ns);
+  double v[2];
+  int status = FVIM_OK;
+  for (int inc = 0; inc < n_inc; ++inc) {
+    const double W = loads[inc];
+    // H0 = h - N[C:eps_p_n].e3 at z = 0 (Rem. modified_contact)
+    if ((rc = apply_mindlin_t<T>(c, (const T*)c->st_eps_p, S<T>(c, V_TMP), FVIM_STRAIN, dU))) return rc;
+    c->n_applies++;
+    if ((rc = axpby<T>(c, H0, h, -1.0, dU, ns))) return rc;
+    if ((rc = sum2<T>(c, H0, ns, v))) return rc;
+    const double hnorm = sqrt(v[1]);
+    if (cudaMemcpyAsync(H, H0, ns * sizeof(T), cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
+    if (cudaMemsetAsync(dUp, 0, ns * sizeof(T), c->stream)) return FVIM_ERR_CUDA;
+    if (cudaMemsetAsync(P, 0, ns * sizeof(T), c->stream)) return FVIM_ERR_CUDA;   // first guess: uniform
+    // T_prev = pressure of the last converged increment
+    if (cudaMemcpyAsync(Tprev, c->st_T, ns * sizeof(T), cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
+    double e = INFINITY;
+    int k = 1;
+    while (true) {
+      int cgi = 0, dfi = 0;
+      rc = elastic_contact_t<T>(c, H, W, P, o, &cgi, nullptr);
+      if (rep) rep->cg_iters += cgi;
+      if (rc && rc != FVIM_ERR_NOT_CONVERGED) return rc;
+      if ((rc = axpby<T>(c, dT, P, -1.0, Tprev, ns))) return rc;
+      long ev = 0;
+      rc = plasticity_t<T>(c, dT, dE, S<T>(c, V_DEP), S<T>(c, V_EP), o, &dfi, nullptr, &ev);
+      if (rep) { rep->df_iters += dfi; rep->residual_evals += ev; }
+      if (rc && rc != FVIM_ERR_NOT_CONVERGED) return rc;
+      // dU = N[C:deps_p].e3 at z = 0
+      if ((rc = apply_mindlin_t<T>(c, S<T>(c, V_DEP), S<T>(c, V_TMP), FVIM_STRAIN, dU))) return rc;
+      c->n_applies++;
+      k_diff2<T><<<gs, RT, 0, c->stream>>>(dU, dUp, ns, (double*)c->sv[V_PART]);
+      FVIM_CUDA_CHECK_LAUNCH();
+      if ((rc = finish<1>(c, gs, v))) return rc;
+      e = sqrt(v[0]) / hnorm;
+      // relaxation, modified surface, then dU_prev <- dU (Algorithm 1, literal order)
+      k_relax<T><<<gs, RT, 0, c->stream>>>(H, H0, dUp, dU, o->relax, ns);
+      FVIM_CUDA_CHECK_LAUNCH();
+      k += 1;
+      if (e < o->tol || k > o->max_iter) break;
+    }
+    // update(S, dE) and the converged pressure
+    if ((rc = commit_t<T>(c, dE, S<T>(c, V_DEP), S<T>(c, V_EP)))) return rc;
+    if (cudaMemcpyAsync(c->st_T, P, ns * sizeof(T), cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
+    if ((rc = sum2<T>(c, P, ns, v))) return rc;
+    double area[1];
+    k_count_pos<T><<<gs, RT, 0, c->stream>>>(P, ns, (double*)c->sv[V_PART]);
+    FVIM_CUDA_CHECK_LAUNCH();
+    if ((rc = finish<1>(c, gs, area))) return rc;
+    if (rep) {
+      if (inc < FVIM_MAX_INCREMENTS) rep->contact_area[inc] = area[0] / (double)ns;
+      rep->n_increments = inc + 1;
+      if (inc < FVIM_MAX_INCREMENTS) {
+        rep->alg1_iters[inc] = k - 1;
+        rep->alg1_error[inc] = e;
+      }
+      rep->load_error = std::max(rep->load_error, fabs(dA * v[0] - W) / W);
+    }
+    if (!(e < o->tol)) status = FVIM_ERR_NOT_CONVERGED;
+  }
+  (void)nv;
+  if (p_out && cudaMemcpyAsync(p_out, P, ns * sizeof(T), cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fvim_default_opts(const fvim_ctx* c, fvim_opts* o) {
+  if (!c || !o) return FVIM_ERR_ARG;
+  const bool dbl = c->prec == FVIM_FP64;
+  o->tol = dbl ? 1e-9 : 1e-7;
+  o->max_iter = 100;
+  o->relax = 1.0;
+  o->cg_tol = dbl ? 1e-12 : 1e-6;
+  o->cg_max_iter = 2000;
+  o->df_tol_abs = 0.0;
+  o->df_tol_rel = dbl ? 1e-10 : 1e-5;
+  o->df_max_iter = 500;
+  return FVIM_OK;
+}
+
+static int check_opts(const fvim_opts* o) {
+  if (!o) return FVIM_ERR_ARG;
+  if (!(o->tol > 0) || o->max_iter < 1 || !(o->relax > 0 && o->relax <= 1) || !(o->cg_tol > 0) ||
+      o->cg_max_iter < 1 || !(o->df_tol_abs >= 0) || !(o->df_tol_rel >= 0) || o->df_max_iter < 0)
+    return FVIM_ERR_ARG;
+  return FVIM_OK;
+}
+
+int fvim_elastic_contact(fvim_ctx* c, const void* h, double W, void* p, const fvim_opts* o, int* iters, double* err) {
+  if (!c || !h || !p || !(W > 0) || check_opts(o)) return FVIM_ERR_ARG;
+  if (c->prec == FVIM_FP64) {
+    int rc = ensure_ws<double>(c);
+    if (rc) return rc;
+    return elastic_contact_t<double>(c, (const double*)h, W, (double*)p, o, iters, err);
+  }
+  int rc = ensure_ws<float>(c);
+  if (rc) return rc;
+  return elastic_contact_t<float>(c, (const float*)h, W, (float*)p, o, iters, err);
+}
+
+int fvim_plasticity_solve(fvim_ctx* c, const void* dT, void* dE, void* deps_p, void* dep, const fvim_opts* o,
+                          int* iters, double* res) {
+  if (!c || !dT || !dE || check_opts(o) || !isfinite(c->sigma_y)) return FVIM_ERR_ARG;
+  int rc;
+  if (c->prec == FVIM_FP64) {
+    if ((rc = ensure_ws<double>(c))) return rc;
+    rc = plasticity_t<double>(c, (const double*)dT, (double*)dE, (double*)deps_p, (double*)dep, o, iters, res, nullptr);
+  } else {
+    if ((rc = ensure_ws<float>(c))) return rc;
+    rc = plasticity_t<float>(c, (const float*)dT, (float*)dE, (float*)deps_p, (float*)dep, o, iters, res, nullptr);
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
+  return rc;
+}
+
+int fvim_solve_contact(fvim_ctx* c, const void* h, const double* loads, int n_inc, const fvim_opts* o, void* p_out,
+                       fvim_report* rep) {
+  if (!c || !h || !loads || n_inc < 1 || check_opts(o) || !isfinite(c->sigma_y)) return FVIM_ERR_ARG;
+  for (int i = 0; i < n_inc; ++i)
+    if (!(loads[i] > 0) || !isfinite(loads[i])) return FVIM_ERR_ARG;
+  if (rep) memset(rep, 0, sizeof(*rep));
+  const long a0 = c->n_applies;
+  int rc;
+  if (c->prec == FVIM_FP64) {
+    if ((rc = ensure_ws<double>(c))) return rc;
+    rc = solve_contact_t<double>(c, (const double*)h, loads, n_inc, o, (double*)p_out, rep);
+  } else {
+    if ((rc = ensure_ws<float>(c))) return rc;
+    rc = solve_contact_t<float>(c, (const float*)h, loads, n_inc, o, (float*)p_out, rep);
+  }
+  if (rep) {
+    rep->status = rc;
+    rep->mindlin_applies = c->n_applies - a0;
+  }
+  return rc;
+}
+
+}  // extern "C"

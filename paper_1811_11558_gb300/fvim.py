@@ -22,6 +22,32 @@ FVIM_STRAIN = 1
 _lib = None
 
 
+MAX_INCREMENTS = 64
+
+
+class Opts(ctypes.Structure):
+    """fvim_opts (include/fvim.h)."""
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("relax", ctypes.c_double),
+                ("cg_tol", ctypes.c_double), ("cg_max_iter", ctypes.c_int), ("df_tol_abs", ctypes.c_double),
+                ("df_tol_rel", ctypes.c_double), ("df_max_iter", ctypes.c_int)]
+
+
+class Report(ctypes.Structure):
+    """fvim_report (include/fvim.h)."""
+    _fields_ = [("status", ctypes.c_int), ("n_increments", ctypes.c_int),
+                ("alg1_iters", ctypes.c_int * MAX_INCREMENTS), ("alg1_error", ctypes.c_double * MAX_INCREMENTS),
+                ("contact_area", ctypes.c_double * MAX_INCREMENTS), ("load_error", ctypes.c_double),
+                ("cg_iters", ctypes.c_long), ("df_iters", ctypes.c_long), ("residual_evals", ctypes.c_long),
+                ("mindlin_applies", ctypes.c_long)]
+
+    def as_dict(self):
+        n = self.n_increments
+        return {"status": self.status, "n_increments": n, "alg1_iters": list(self.alg1_iters[:n]),
+                "alg1_error": list(self.alg1_error[:n]), "contact_area": list(self.contact_area[:n]),
+                "load_error": self.load_error, "cg_iters": self.cg_iters, "df_iters": self.df_iters,
+                "residual_evals": self.residual_evals, "mindlin_applies": self.mindlin_applies}
+
+
 class FvimError(RuntimeError):
     def __init__(self, status, what):
         super().__init__("%s failed: %s (status %d)" % (what, strerror(status), status))
@@ -54,6 +80,11 @@ def lib():
         "fvim_profile_enable": (i, [vp, i]),
         "fvim_profile_read": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(i), i]),
         "fvim_profile_name": (ctypes.c_char_p, [i]),
+        "fvim_default_opts": (i, [vp, ctypes.POINTER(Opts)]),
+        "fvim_elastic_contact": (i, [vp, vp, d, vp, ctypes.POINTER(Opts), ctypes.POINTER(i), ctypes.POINTER(d)]),
+        "fvim_plasticity_solve": (i, [vp, vp, vp, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(i),
+                                      ctypes.POINTER(d)]),
+        "fvim_solve_contact": (i, [vp, vp, ctypes.POINTER(d), i, ctypes.POINTER(Opts), vp, ctypes.POINTER(Report)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -228,3 +259,50 @@ class Context:
 
     def sync(self):
         _check(lib().fvim_sync(self._h), "fvim_sync")
+
+    # -- solvers ------------------------------------------------------------------
+    def default_opts(self, **kw):
+        o = Opts()
+        _check(lib().fvim_default_opts(self._h, ctypes.byref(o)), "fvim_default_opts")
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+    def elastic_contact(self, h, W, p, opts=None, allow_not_converged=False):
+        """Polonsky-Keer contact under load W; p: initial guess in, pressure out."""
+        o = opts or self.default_opts()
+        a = _ptr(h, self.dtype, self.surf_shape, "h")
+        b = _ptr(p, self.dtype, self.surf_shape, "p")
+        it = ctypes.c_int()
+        err = ctypes.c_double()
+        self._stream()
+        st = lib().fvim_elastic_contact(self._h, a, float(W), b, ctypes.byref(o), ctypes.byref(it), ctypes.byref(err))
+        if st != 0 and not (allow_not_converged and st == -5):
+            raise FvimError(st, "fvim_elastic_contact")
+        return it.value, err.value
+
+    def plasticity_solve(self, dT, dE, deps_p=None, dep=None, opts=None):
+        o = opts or self.default_opts()
+        a = _ptr(dT, self.dtype, self.surf_shape, "dT")
+        b = _ptr(dE, self.dtype, self.vol_shape, "dE")
+        c = _ptr(deps_p, self.dtype, self.vol_shape, "deps_p")
+        e = _ptr(dep, self.dtype, self.scal_shape, "dep")
+        it = ctypes.c_int()
+        res = ctypes.c_double()
+        self._stream()
+        _check(lib().fvim_plasticity_solve(self._h, a, b, c, e, ctypes.byref(o), ctypes.byref(it),
+                                           ctypes.byref(res)), "fvim_plasticity_solve")
+        return it.value, res.value
+
+    def solve_contact(self, h, loads, p_out=None, opts=None, allow_not_converged=False):
+        """Algorithm 1 over the load increments; returns the report as a dict."""
+        o = opts or self.default_opts()
+        a = _ptr(h, self.dtype, self.surf_shape, "h")
+        b = _ptr(p_out, self.dtype, self.surf_shape, "p_out")
+        L = (ctypes.c_double * len(loads))(*[float(x) for x in loads])
+        rep = Report()
+        self._stream()
+        st = lib().fvim_solve_contact(self._h, a, L, len(loads), ctypes.byref(o), b, ctypes.byref(rep))
+        if st != 0 and not (allow_not_converged and st == -5):
+            raise FvimError(st, "fvim_solve_contact")
+        return rep.as_dict()

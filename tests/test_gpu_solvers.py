@@ -1,0 +1,145 @@
+"""Parity of the CUDA solvers (through the C ABI) with the FP64 oracle.
+
+The solvers stop at a tolerance, so converged answers are compared with a bound set by
+the two stopping rules (not by rounding): FP64 runs use tight tolerances on both sides;
+FP32 runs use the FP32 defaults and the bars of the FP32 path (2e-5 on stresses where the
+solver tolerance allows it, 1e-4 on the contact area).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import contact as C
+from oracle import operators as op
+from oracle import tensors as T
+from paper_1811_11558_gb300 import inputs
+
+from gpu_util import rel_l2, require_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+E, NU, R = 1.0, 0.3, 0.5
+ES = T.e_star(E, NU)
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "hertz_32x32x16.npz")
+
+
+def _ctx(n, z, prec, **kw):
+    from paper_1811_11558_gb300 import Context
+
+    return Context(n, n, z, 1.0, 1.0, precision=prec, E=E, nu=NU, **kw)
+
+
+@pytest.mark.parametrize("prec,n", [("fp64", 64), ("fp32", 256)])
+def test_elastic_contact_parity(prec, n):
+    torch = require_gpu()
+    z = inputs.uniform_depth(2, 0.1)
+    h = inputs.hertz_profile(n, n, 1.0, 1.0, R)
+    W = 4.7916e-3
+    ref, info = C.polonsky_keer(h, W, 1.0, 1.0, E, NU, tol=1e-13)
+    ctx = _ctx(n, z, prec)
+    dt = ctx.dtype
+    p = torch.zeros(ctx.surf_shape, dtype=dt, device="cuda")
+    opts = ctx.default_opts(cg_tol=1e-13) if prec == "fp64" else ctx.default_opts()
+    it, err = ctx.elastic_contact(to_dev(torch, h, dt), W, p, opts)
+    got = p.cpu().numpy()
+    assert it > 3 and err < opts.cg_tol
+    assert abs(got.sum() / (n * n) - W) < (1e-14 if prec == "fp64" else 1e-7) * 1.0
+    area_ref = (ref > 0).mean()
+    area = (got > 0).mean()
+    if prec == "fp64":
+        assert rel_l2(got, ref) < 1e-9
+        assert area == area_ref
+    else:
+        assert rel_l2(got, ref) < 1e-4
+        assert abs(area - area_ref) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_plasticity_parity(prec):
+    torch = require_gpu()
+    n, nz = 16, 8
+    z = inputs.uniform_depth(nz, 0.5)
+    h = inputs.hertz_profile(n, n, 1.0, 1.0, R)
+    sy, Eh = 0.05 * ES, 0.1
+    dT, _ = C.polonsky_keer(h, 3.0e-3, 1.0, 1.0, E, NU, tol=1e-13)
+    st = C.PlasticState(nz, n, n)
+    dE_ref, dep_ref, dEp_ref, info = C.plasticity_solve(dT, st, z, 1.0, 1.0, E, NU, sy, Eh, tol_rel=1e-12)
+    assert dEp_ref.max() > 0
+    ctx = _ctx(n, z, prec, sigma_y=sy, E_h=Eh)
+    dt = ctx.dtype
+    dE = torch.empty(ctx.vol_shape, dtype=dt, device="cuda")
+    dep = torch.empty(ctx.vol_shape, dtype=dt, device="cuda")
+    dEp = torch.empty(ctx.scal_shape, dtype=dt, device="cuda")
+    opts = ctx.default_opts(df_tol_rel=1e-12) if prec == "fp64" else ctx.default_opts()
+    it, res = ctx.plasticity_solve(to_dev(torch, dT, dt), dE, dep, dEp, opts)
+    tol = 1e-8 if prec == "fp64" else 1e-4
+    assert rel_l2(dE.cpu().numpy(), dE_ref) < tol
+    assert rel_l2(dep.cpu().numpy(), dep_ref) < 10 * tol
+    assert rel_l2(dEp.cpu().numpy(), dEp_ref) < 10 * tol
+
+
+def _golden_run(prec, **opt_kw):
+    torch = require_gpu()
+    g = np.load(GOLDEN)
+    n, nz = 32, 16
+    z = inputs.uniform_depth(nz, 0.5)
+    h = inputs.hertz_profile(n, n, 1.0, 1.0, R)
+    ctx = _ctx(n, z, prec, sigma_y=float(g["sigma_y"]), E_h=float(g["E_h"]))
+    dt = ctx.dtype
+    p = torch.empty(ctx.surf_shape, dtype=dt, device="cuda")
+    opts = ctx.default_opts(**opt_kw)
+    rep = ctx.solve_contact(to_dev(torch, h, dt), list(g["loads"]), p, opts)
+    epp = torch.empty(ctx.vol_shape, dtype=dt, device="cuda")
+    ep = torch.empty(ctx.scal_shape, dtype=dt, device="cuda")
+    ctx.get_state(epp, ep, None)
+    torch.cuda.synchronize()
+    return g, rep, p.cpu().numpy(), epp.cpu().numpy(), ep.cpu().numpy()
+
+
+def test_solve_contact_fp64_matches_oracle_hertz():
+    """The plain FP64 elastic-plastic Hertz case (32 x 32 x 16, five increments to the load
+    of an elastic peak pressure of 3 sigma_y): Algorithm 1 on the GPU against the oracle."""
+    g, rep, p, epp, ep = _golden_run("fp64", cg_tol=1e-13, df_tol_rel=1e-11, max_iter=200)
+    assert rep["status"] == 0 and rep["n_increments"] == 5
+    assert rep["load_error"] < 1e-12
+    assert rel_l2(p, g["p"]) < 1e-7
+    assert rel_l2(ep, g["e_p"]) < 1e-6
+    assert rel_l2(epp, g["eps_p"]) < 1e-6
+    assert np.array_equal(np.array(rep["contact_area"]), g["areas"])
+
+
+def test_solve_contact_fp32_matches_oracle_hertz():
+    g, rep, p, epp, ep = _golden_run("fp32", max_iter=200)
+    assert rep["status"] == 0
+    assert rel_l2(p, g["p"]) < 1e-4
+    assert rel_l2(ep, g["e_p"]) < 1e-3
+    assert np.abs(np.array(rep["contact_area"]) - g["areas"]).max() <= 1e-4 + 1.0 / 1024
+
+
+def test_solve_contact_deterministic_and_caps():
+    torch = require_gpu()
+    n, nz = 16, 8
+    z = inputs.uniform_depth(nz, 0.5)
+    h = to_dev(torch, inputs.hertz_profile(n, n, 1.0, 1.0, R), torch.float64)
+    outs = []
+    for _ in range(2):
+        ctx = _ctx(n, z, "fp64", sigma_y=0.05 * ES, E_h=0.1)
+        p = torch.empty(ctx.surf_shape, dtype=torch.float64, device="cuda")
+        ctx.solve_contact(h, [2e-3, 4e-3], p)
+        outs.append(p.clone())
+    assert torch.equal(outs[0], outs[1])
+    # an iteration cap is reported, not hidden
+    ctx = _ctx(n, z, "fp64", sigma_y=0.05 * ES, E_h=0.1)
+    p = torch.empty(ctx.surf_shape, dtype=torch.float64, device="cuda")
+    rep = ctx.solve_contact(h, [4e-3], p, ctx.default_opts(max_iter=1), allow_not_converged=True)
+    assert rep["status"] == -5 and rep["alg1_iters"][0] == 1
+    # a non-finite surface is refused with a status, the GPU stays usable
+    bad = h.clone()
+    bad[3, 3] = float("nan")
+    from paper_1811_11558_gb300 import FvimError
+
+    with pytest.raises(FvimError):
+        ctx.elastic_contact(bad, 4e-3, torch.zeros_like(p))
+    torch.cuda.synchronize()
+    assert torch.isfinite(outs[0]).all()
