@@ -144,13 +144,14 @@ def mindlin_modes(W, Q, z, E, nu):
     W = np.asarray(W, dtype=np.complex128)
     q = np.hypot(Q[:, 0], Q[:, 1])
     kel, Lw, bou = _mode_data(Q, z, mu, nu)
-    M = {key: np.einsum("kij,kjab->kiab", Lw[key], W) for key in Lw}
+    M = {key: np.einsum("kij,kjab->kiab", Lw[key], W, optimize=True) for key in Lw}
     # Eq. (2gradient): - int grad^2 U(-q, y3 - x3) : w(y3) dy3, both branches
     G = np.zeros(W.shape, dtype=np.complex128)
     for s in (-1, +1):
         U02, U12 = kel[(2, s)]
         G -= q[:, None, None, None] * (
-            np.einsum("kabcd,kibc->kiad", U02, M[(0, s)]) + np.einsum("kabcd,kibc->kiad", U12, M[(1, s)])
+            np.einsum("kabcd,kibc->kiad", U02, M[(0, s)], optimize=True)
+            + np.einsum("kabcd,kibc->kiad", U12, M[(1, s)], optimize=True)
         )
     # jump term of Eq. (jump): - ([[grad U]] : w(x3)) x e3, [[grad U]] = U01^+ - U01^-
     J = kel[(1, +1)][0] - kel[(1, -1)][0]

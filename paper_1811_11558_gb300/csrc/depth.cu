@@ -33,6 +33,7 @@
 namespace {
 
 constexpr int KT_MAX = 16;  // k1 columns per CTA (128-byte rows in FP32)
+constexpr double kTwoPi = 6.283185307179586476925;
 
 template <typename T> __device__ __forceinline__ T dexp(T x);
 template <> __device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
@@ -52,13 +53,15 @@ template <typename T> __device__ __forceinline__ Elem<T> elem_coef(T q, T h) {
   T I0, I1, I2;
   const T thr = sizeof(T) == 4 ? (T)1.0 : (T)0.5;
   if (a < thr) {
-    const int M = sizeof(T) == 4 ? 12 : 18;
-    T t = 1, s0 = 0, s1 = 0, s2 = 0;
+    // I_n(a) = sum_m (-a)^m / (m! (n + m + 1)); the reciprocals are compile-time constants
+    constexpr int M = sizeof(T) == 4 ? 12 : 18;
+    T term = 1, s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
     for (int m = 0; m < M; ++m) {
-      s0 += t / (T)(m + 1);
-      s1 += t / (T)(m + 2);
-      s2 += t / (T)(m + 3);
-      t *= -a / (T)(m + 1);
+      s0 += term * (T)(1.0 / (m + 1));
+      s1 += term * (T)(1.0 / (m + 2));
+      s2 += term * (T)(1.0 / (m + 3));
+      term *= -a * (T)(1.0 / (m + 1));
     }
     I0 = s0; I1 = s1; I2 = s2;
   } else {
@@ -260,18 +263,20 @@ template <typename T> struct ModeGeom {
   bool zero, nyq;
 };
 
+// wavevector of the mode (k1, k2) in the arithmetic of the path: w1 = 2 pi / L1, w2 = 2 pi / L2
 template <typename T>
-__device__ __forceinline__ ModeGeom<T> mode_geom(int k1, int k2, int n2, double L1, double L2) {
+__device__ __forceinline__ ModeGeom<T> mode_geom(int k1, int k2, int n2, T w1, T w2) {
   ModeGeom<T> g;
   const int k2s = k2 < n2 / 2 ? k2 : k2 - n2;
   g.nyq = (k2 == n2 / 2);
   g.zero = (k1 == 0 && k2 == 0);
-  const double q1 = 6.283185307179586476925 * (double)k1 / L1;
-  const double q2 = 6.283185307179586476925 * (double)k2s / L2;
-  const double q = sqrt(q1 * q1 + q2 * q2);
-  g.q = (T)q;
-  g.c = q > 0 ? (T)(q1 / q) : (T)1;
-  g.s = q > 0 ? (T)(q2 / q) : (T)0;
+  const T q1 = w1 * (T)k1;
+  const T q2 = w2 * (T)k2s;
+  const T q = sqrt(q1 * q1 + q2 * q2);
+  const T iq = q > (T)0 ? (T)1 / q : (T)0;
+  g.q = q;
+  g.c = q > (T)0 ? q1 * iq : (T)1;
+  g.s = q2 * iq;
   return g;
 }
 
@@ -282,27 +287,32 @@ __device__ __forceinline__ ModeGeom<T> mode_geom(int k1, int k2, int n2, double 
 // ----------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __restrict__ spec, typename Cx<T>::t* __restrict__ surf,
-                                const T* __restrict__ zn, int nz, int n2, int h1, int KT, int C, int nch, double L1,
-                                double L2, T lam, T mu, T nu, int out_kind, int want_u3, int uniform, T hz) {
+                                const T* __restrict__ zn, int nz, int n2, int h1, int KT, int C, int nch, int prow, T w1,
+                                T w2, T lam, T mu, T nu, int out_kind, int want_u3, int uniform, T hz) {
   typedef typename Cx<T>::t V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* W = reinterpret_cast<V*>(smraw);                 // [nz][6][KT]
-  V* Pst = W + (size_t)nz * 6 * KT;                   // [max(nz, 2 nch)][6][KT]
-  const int kt = threadIdx.x % KT;
-  const int ch = threadIdx.x / KT;
+  V* Pst = W + (size_t)nz * 6 * KT;                   // [max(nz, 2 nch + 1)][6][KT]
+  T* zs = reinterpret_cast<T*>(Pst + (size_t)prow * KT * 6);  // [nz] depth nodes
+  const int lkt = __ffs(KT) - 1;  // KT is a power of two
+  const int kt = threadIdx.x & (KT - 1);
+  const int ch = threadIdx.x >> lkt;
   const int k1 = blockIdx.x * KT + kt;
   const int k2 = blockIdx.y;
   const size_t plane = (size_t)n2 * h1;
   const size_t colofs = (size_t)k2 * h1 + blockIdx.x * KT;
 
-  // 1. load the tile (coalesced KT-wide rows)
+  // 1. load the tile (coalesced KT-wide rows, every copy in flight before one wait) and
+  //    the depth nodes
   for (int idx = threadIdx.x; idx < nz * 6 * KT; idx += blockDim.x) {
-    const int zc = idx / KT, j = idx - zc * KT;
-    W[idx] = spec[(size_t)zc * plane + colofs + j];
+    const int zc = idx >> lkt, j = idx & (KT - 1);
+    cp_async_cx(W + idx, spec + (size_t)zc * plane + colofs + j);
   }
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];
+  cp_async_wait_all();
   __syncthreads();
 
-  const ModeGeom<T> g = mode_geom<T>(k1, k2, n2, L1, L2);
+  const ModeGeom<T> g = mode_geom<T>(k1, k2, n2, w1, w2);
   const bool special = g.zero || g.nyq;
   const int n0 = ch * C;
   const int nend = min(n0 + C, nz);
@@ -333,7 +343,7 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
     mom_zero(A);
     mom_zero(P);
     for (int e = n0; e < e1; ++e) {
-      if (!uniform) ec = elem_coef<T>(g.q, zn[e + 1] - zn[e]);
+      if (!uniform) ec = elem_coef<T>(g.q, zs[e + 1] - zs[e]);
       V wi[6], wj[6];
 #pragma unroll
       for (int cc = 0; cc < 6; ++cc) {
@@ -343,7 +353,7 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
       stepA(A, ec, wi, wj);
     }
     for (int e = e1 - 1; e >= n0; --e) {
-      if (!uniform) ec = elem_coef<T>(g.q, zn[e + 1] - zn[e]);
+      if (!uniform) ec = elem_coef<T>(g.q, zs[e + 1] - zs[e]);
       V wi[6], wj[6];
 #pragma unroll
       for (int cc = 0; cc < 6; ++cc) {
@@ -371,7 +381,7 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
         const int a0 = j * C, a1 = min(j * C + C, nz - 1);
         const Mom<V> sj = SA[j * KT + kt];
         SA[j * KT + kt] = run;
-        propA(run, g.q * (zn[a1] - zn[a0]));
+        propA(run, g.q * (zs[a1] - zs[a0]));
         mom_add(run, sj);
       }
     }
@@ -382,7 +392,7 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
         const int a0 = j * C, a1 = min(j * C + C, nz - 1);
         const Mom<V> sj = SP[j * KT + kt];
         SP[j * KT + kt] = run;
-        propP(run, g.q * (zn[a1] - zn[a0]));
+        propP(run, g.q * (zs[a1] - zs[a0]));
         mom_add(run, sj);
       }
       P0s[kt] = run;
@@ -468,7 +478,7 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
     Mom<V> P = Pin;
     if (e1 < nend) Pn[e1 * KT + kt] = P;   // last chunk: node nz-1 has no element below
     for (int e = e1 - 1; e >= n0; --e) {
-      if (!uniform) ec = elem_coef<T>(g.q, zn[e + 1] - zn[e]);
+      if (!uniform) ec = elem_coef<T>(g.q, zs[e + 1] - zs[e]);
       V wi[6], wj[6];
 #pragma unroll
       for (int cc = 0; cc < 6; ++cc) {
@@ -489,7 +499,7 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
       const Mom<V> P = Pn[i * KT + kt];
       V e[6];
       kelvin_strain<T, V>(A, P, w, g.q, nu, mu, e);
-      bous_strain_add<T, V>(tr, g.q * zn[i], nu, mu, e);
+      bous_strain_add<T, V>(tr, g.q * zs[i], nu, mu, e);
       V o[6];
       if (out_kind == FVIM_STRAIN) {
 #pragma unroll
@@ -506,7 +516,7 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
 #pragma unroll
       for (int cc = 0; cc < 6; ++cc) spec[(size_t)(i * 6 + cc) * plane + (size_t)k2 * h1 + k1] = o[cc];
       if (i < e1) {
-        if (!uniform) ec = elem_coef<T>(g.q, zn[i + 1] - zn[i]);
+        if (!uniform) ec = elem_coef<T>(g.q, zs[i + 1] - zs[i]);
         V wj[6];
 #pragma unroll
         for (int cc = 0; cc < 6; ++cc) wj[cc] = W[((i + 1) * 6 + cc) * KT + kt];
@@ -522,13 +532,13 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
 // ----------------------------------------------------------------------------------
 template <typename T>
 __global__ void k_boussinesq(typename Cx<T>::t* __restrict__ spec, typename Cx<T>::t* __restrict__ surf,
-                             const T* __restrict__ zn, int nz, int n2, int h1, double L1, double L2, T lam, T mu,
+                             const T* __restrict__ zn, int nz, int n2, int h1, T w1, T w2, T lam, T mu,
                              T nu, int out_kind, int want_vol, int want_u3) {
   typedef typename Cx<T>::t V;
   const int k1 = blockIdx.x * blockDim.x + threadIdx.x;
   const int k2 = blockIdx.y;
   if (k1 >= h1) return;
-  const ModeGeom<T> g = mode_geom<T>(k1, k2, n2, L1, L2);
+  const ModeGeom<T> g = mode_geom<T>(k1, k2, n2, w1, w2);
   const size_t plane = (size_t)n2 * h1;
   const size_t at = (size_t)k2 * h1 + k1;
   const V p = surf[at];
@@ -589,12 +599,13 @@ template <typename T> int launch_mindlin_depth(const fvim_ctx* c, int out_kind, 
   const int nch = (nz + C - 1) / C;
   const int threads = KT * nch;
   const int prow = nz > 2 * nch + 1 ? nz : 2 * nch + 1;
-  const size_t smem = (size_t)nz * 6 * KT * sizeof(V) + (size_t)prow * KT * sizeof(Mom<V>);
+  const size_t smem = (size_t)nz * 6 * KT * sizeof(V) + (size_t)prow * KT * sizeof(Mom<V>) + (size_t)nz * sizeof(T);
   if (smem > 227 * 1024) return FVIM_ERR_UNSUPPORTED;
   cudaFuncSetAttribute(k_mindlin_depth<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid(h1 / KT, n2);
   k_mindlin_depth<T><<<grid, threads, smem, c->stream>>>(
-      (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, n2, h1, KT, C, nch, c->L1, c->L2, (T)c->lam, (T)c->mu,
+      (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, n2, h1, KT, C, nch, prow, (T)(kTwoPi / c->L1),
+      (T)(kTwoPi / c->L2), (T)c->lam, (T)c->mu,
       (T)c->nu, out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz);
   FVIM_CUDA_CHECK_LAUNCH();
   return FVIM_OK;
@@ -605,8 +616,8 @@ template <typename T> int launch_boussinesq(const fvim_ctx* c, int out_kind, boo
   const int threads = 128;
   dim3 grid((c->h1 + threads - 1) / threads, c->n2);
   k_boussinesq<T><<<grid, threads, 0, c->stream>>>((V*)c->spec, (V*)c->surf, (const T*)c->z_dev, c->nz, c->n2, c->h1,
-                                                   c->L1, c->L2, (T)c->lam, (T)c->mu, (T)c->nu, out_kind,
-                                                   want_vol ? 1 : 0, want_u3 ? 1 : 0);
+                                                   (T)(kTwoPi / c->L1), (T)(kTwoPi / c->L2), (T)c->lam, (T)c->mu, (T)c->nu,
+                                                   out_kind, want_vol ? 1 : 0, want_u3 ? 1 : 0);
   FVIM_CUDA_CHECK_LAUNCH();
   return FVIM_OK;
 }

@@ -221,7 +221,7 @@ __device__ __forceinline__ int padi(int p) { return p + (p >> 3); }
 
 // columns: CTA = KC consecutive k1 columns of one plane, KC * n2/8 threads
 template <typename T, bool INV, int KC>
-__global__ void __launch_bounds__(1024) k_cols8(typename Cx<T>::t* __restrict__ planes,
+__global__ void __launch_bounds__(512) k_cols8(typename Cx<T>::t* __restrict__ planes,
                                                 const typename Cx<T>::t* __restrict__ tw, int n2, int h1) {
   typedef typename Cx<T>::t V;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -348,20 +348,23 @@ __global__ void __launch_bounds__(256) k_rows_inv6_r8(const typename Cx<T>::t* _
     const int ca = 2 * p, cb = 2 * p + 1;
     const V* sa = spec + (((size_t)z * 6 + ca) * n2 + x2) * h1;
     const V* sb = spec + (((size_t)z * 6 + cb) * n2 + x2) * h1;
+    // unconditional loads first (all in flight), then the Hermitian selection
+    V ra[8], rb[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const int k = t + m * T8;
-      V A, B;
-      if (k == h1) {
-        A = mk<V>(nq_scale == (T)0 ? (T)0 : nq_scale * nq[((size_t)z * 6 + ca) * n2 + x2], 0);
-        B = mk<V>(nq_scale == (T)0 ? (T)0 : nq_scale * nq[((size_t)z * 6 + cb) * n2 + x2], 0);
-      } else if (k < h1) {
-        A = sa[k];
-        B = sb[k];
-      } else {
-        A = cconj(sa[n1 - k]);
-        B = cconj(sb[n1 - k]);
-      }
+      const int kk = k < h1 ? k : (k > h1 ? n1 - k : 0);
+      ra[m] = sa[kk];
+      rb[m] = sb[kk];
+    }
+    const T na = nq_scale == (T)0 ? (T)0 : nq_scale * nq[((size_t)z * 6 + ca) * n2 + x2];
+    const T nb = nq_scale == (T)0 ? (T)0 : nq_scale * nq[((size_t)z * 6 + cb) * n2 + x2];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int k = t + m * T8;
+      V A = ra[m], B = rb[m];
+      if (k > h1) { A = cconj(A); B = cconj(B); }
+      if (k == h1) { A = mk<V>(na, 0); B = mk<V>(nb, 0); }
       v[p][m] = cadd(A, cmuli(B));
     }
   }
@@ -499,9 +502,10 @@ template <typename T> int launch_cols(const fvim_ctx* c, bool inverse, void* pla
   typedef typename Cx<T>::t V;
   const int n2 = c->n2, h1 = c->h1;
   if (n2 >= 8) {
-    // KC columns per CTA: 128-byte rows, at most 1024 threads
-    int kc = (int)(128 / sizeof(V));
-    while (kc > 1 && kc * (n2 >> 3) > 1024) kc >>= 1;
+    // KC columns per CTA: 64-byte rows (full 32-byte sectors), at most 512 threads so
+    // that two CTAs share an SM and overlap their loads with the other's FFT stages
+    int kc = (int)(64 / sizeof(V));
+    while (kc > 1 && kc * (n2 >> 3) > 512) kc >>= 1;
     if (kc > h1) kc = h1;
     const int threads = kc * (n2 >> 3);
     const size_t smem = (size_t)kc * n2 * sizeof(V);

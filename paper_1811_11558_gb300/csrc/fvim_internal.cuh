@@ -204,6 +204,25 @@ __device__ __forceinline__ void reg_stage(V (&v)[8], int (&pos)[8], int t, int n
 }
 
 // ---------------------------------------------------------------------------
+// asynchronous global -> shared copies (cp.async), all in flight before one wait
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+template <typename V> __device__ __forceinline__ void cp_async_cx(V* smem, const V* gmem) {
+  if (sizeof(V) == 16) cp_async_16(smem, gmem);
+  else cp_async_8(smem, gmem);
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
 #define FVIM_NSOLVER_BUFS 24
