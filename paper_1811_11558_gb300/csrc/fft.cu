@@ -447,6 +447,10 @@ inline int r8_rows(int n1, int n2) {
 template <typename T> int launch_rows_fwd6(const fvim_ctx* c, const T* eps_p, int z0, int nzs) {
   typedef typename Cx<T>::t V;
   const int n1 = c->n1, n2 = c->n2;
+  if (launch_rows_fwd6_ct<T>(c, eps_p, z0, nzs)) {
+    FVIM_CUDA_CHECK_LAUNCH();
+    return FVIM_OK;
+  }
   if (n1 >= 8 && n1 <= 2048) {
     const int RB = r8_rows(n1, n2);
     const int threads = RB * (n1 >> 3);
@@ -501,6 +505,10 @@ template <typename T> int launch_rows_fwd1(const fvim_ctx* c, const T* f) {
 template <typename T> int launch_cols(const fvim_ctx* c, bool inverse, void* planes, int nplanes) {
   typedef typename Cx<T>::t V;
   const int n2 = c->n2, h1 = c->h1;
+  if (launch_cols_ct<T>(c, inverse, planes, nplanes)) {
+    FVIM_CUDA_CHECK_LAUNCH();
+    return FVIM_OK;
+  }
   if (n2 >= 8) {
     // KC columns per CTA: 64-byte rows (full 32-byte sectors), at most 512 threads so
     // that two CTAs share an SM and overlap their loads with the other's FFT stages
@@ -545,6 +553,10 @@ template <typename T> int launch_rows_inv6(const fvim_ctx* c, T* out, T nq_scale
   typedef typename Cx<T>::t V;
   const int n1 = c->n1, n2 = c->n2;
   const T scale = (T)(1.0 / ((double)n1 * (double)n2));
+  if (launch_rows_inv6_ct<T>(c, out, nq_scale, z0, nzs)) {
+    FVIM_CUDA_CHECK_LAUNCH();
+    return FVIM_OK;
+  }
   if (n1 >= 8 && n1 <= 2048) {
     const int RB = r8_rows(n1, n2);
     const int threads = RB * (n1 >> 3);

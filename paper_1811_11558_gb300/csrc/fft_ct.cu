@@ -1,0 +1,243 @@
+// Compile-time-length variants of the register-resident in-plane FFT kernels (fft.cu has
+// the runtime-length ones).  Same data layouts, same arithmetic, same results up to the
+// order of operations inside the butterflies; chosen by the launchers for 16 <= N <= 1024.
+#include "fvim_internal.cuh"
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ void hooke6_ct(const T* e, T* w, T lam, T mu) {
+  const T tr = e[0] + e[1] + e[2];
+  w[0] = lam * tr + 2 * mu * e[0];
+  w[1] = lam * tr + 2 * mu * e[1];
+  w[2] = lam * tr + 2 * mu * e[2];
+  w[3] = 2 * mu * e[3];
+  w[4] = 2 * mu * e[4];
+  w[5] = 2 * mu * e[5];
+}
+
+// interleaved columns: entry p of column f at buf[p * KC + f]
+template <typename V> struct ColSm {
+  V* buf;
+  int kc, f;
+  __device__ __forceinline__ void put(int, int p, V x) const { buf[p * kc + f] = x; }
+  __device__ __forceinline__ V get(int, int p) const { return buf[p * kc + f]; }
+};
+// contiguous rows with one pad slot every 8 entries: transform g at buf[g * ld + p + p/8]
+template <typename V> struct RowSm {
+  V* buf;
+  int ld;
+  __device__ __forceinline__ void put(int g, int p, V x) const { buf[g * ld + p + (p >> 3)] = x; }
+  __device__ __forceinline__ V get(int g, int p) const { return buf[g * ld + p + (p >> 3)]; }
+};
+
+template <typename T, bool INV, int N>
+__global__ void __launch_bounds__(512) k_cols_ct(typename Cx<T>::t* __restrict__ planes,
+                                                 const typename Cx<T>::t* __restrict__ tw, int h1, int kc) {
+  typedef typename Cx<T>::t V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int T8 = N / 8;
+  const int f = threadIdx.x % kc, t = threadIdx.x / kc;
+  V* col = planes + (size_t)blockIdx.y * N * h1 + (size_t)blockIdx.x * kc + f;
+  V v[1][8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) v[0][m] = col[(size_t)(t + m * T8) * h1];
+  ColSm<V> sm{reinterpret_cast<V*>(smraw), kc, f};
+  fft_ct<V, INV, N, 1, 1>(v, t, sm, tw);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) col[(size_t)(t + m * T8) * h1] = v[0][m];
+}
+
+template <typename V>
+__device__ __forceinline__ void split_pair_ct(V zk, V zmk, V& A, V& B) {
+  typedef decltype(V::x) T;
+  const V c = cconj(zmk);
+  const V s = cadd(zk, c), d = csub(zk, c);
+  A = cscale(s, (T)0.5);
+  B = mk<V>((T)0.5 * d.y, (T)-0.5 * d.x);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_rows_fwd6_ct(const T* __restrict__ eps_p, typename Cx<T>::t* __restrict__ spec,
+                                                      T* __restrict__ nq, const typename Cx<T>::t* __restrict__ tw,
+                                                      int n2, int rb, int z0, T lam, T mu) {
+  typedef typename Cx<T>::t V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int T8 = N / 8, LD = N + N / 8, H1 = N / 2;
+  const int r = threadIdx.x / T8, t = threadIdx.x % T8;
+  const int z = z0 + blockIdx.y;
+  const int x2 = blockIdx.x * rb + r;
+  V v[3][8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int x1 = t + m * T8;
+    T e[6], w[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) e[c] = eps_p[(((size_t)z * 6 + c) * n2 + x2) * N + x1];
+    hooke6_ct(e, w, lam, mu);
+    v[0][m] = mk<V>(w[0], w[1]);
+    v[1][m] = mk<V>(w[2], w[3]);
+    v[2][m] = mk<V>(w[4], w[5]);
+  }
+  RowSm<V> sm{reinterpret_cast<V*>(smraw) + (size_t)r * 3 * LD, LD};
+  fft_ct<V, false, N, 3, 1>(v, t, sm, tw);
+#pragma unroll
+  for (int g = 0; g < 3; ++g)
+#pragma unroll
+    for (int m = 0; m < 8; ++m) sm.put(g, t + m * T8, v[g][m]);
+  __syncthreads();
+  for (int idx = t; idx < 3 * (H1 + 1); idx += T8) {
+    const int g = idx / (H1 + 1), k = idx - g * (H1 + 1);
+    V A, B;
+    split_pair_ct(sm.get(g, k), sm.get(g, (N - k) & (N - 1)), A, B);
+    const int ca = 2 * g, cb = 2 * g + 1;
+    if (k < H1) {
+      spec[(((size_t)z * 6 + ca) * n2 + x2) * H1 + k] = A;
+      spec[(((size_t)z * 6 + cb) * n2 + x2) * H1 + k] = B;
+    } else {
+      nq[((size_t)z * 6 + ca) * n2 + x2] = A.x;
+      nq[((size_t)z * 6 + cb) * n2 + x2] = B.x;
+    }
+  }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_rows_inv6_ct(const typename Cx<T>::t* __restrict__ spec,
+                                                      const T* __restrict__ nq, T* __restrict__ out,
+                                                      const typename Cx<T>::t* __restrict__ tw, int n2, int rb, int z0,
+                                                      T nq_scale, T scale) {
+  typedef typename Cx<T>::t V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int T8 = N / 8, LD = N + N / 8, H1 = N / 2;
+  const int r = threadIdx.x / T8, t = threadIdx.x % T8;
+  const int z = z0 + blockIdx.y;
+  const int x2 = blockIdx.x * rb + r;
+  V v[3][8];
+#pragma unroll
+  for (int g = 0; g < 3; ++g) {
+    const int ca = 2 * g, cb = 2 * g + 1;
+    const V* sa = spec + (((size_t)z * 6 + ca) * n2 + x2) * H1;
+    const V* sb = spec + (((size_t)z * 6 + cb) * n2 + x2) * H1;
+    V ra[8], rbv[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int k = t + m * T8;
+      const int kk = k < H1 ? k : (k > H1 ? N - k : 0);
+      ra[m] = sa[kk];
+      rbv[m] = sb[kk];
+    }
+    const T na = nq_scale == (T)0 ? (T)0 : nq_scale * nq[((size_t)z * 6 + ca) * n2 + x2];
+    const T nb = nq_scale == (T)0 ? (T)0 : nq_scale * nq[((size_t)z * 6 + cb) * n2 + x2];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int k = t + m * T8;
+      V A = ra[m], B = rbv[m];
+      if (k > H1) { A = cconj(A); B = cconj(B); }
+      if (k == H1) { A = mk<V>(na, 0); B = mk<V>(nb, 0); }
+      v[g][m] = cadd(A, cmuli(B));
+    }
+  }
+  RowSm<V> sm{reinterpret_cast<V*>(smraw) + (size_t)r * 3 * LD, LD};
+  fft_ct<V, true, N, 3, 1>(v, t, sm, tw);
+#pragma unroll
+  for (int g = 0; g < 3; ++g)
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int x1 = t + m * T8;
+      out[(((size_t)z * 6 + 2 * g) * n2 + x2) * N + x1] = v[g][m].x * scale;
+      out[(((size_t)z * 6 + 2 * g + 1) * n2 + x2) * N + x1] = v[g][m].y * scale;
+    }
+}
+
+template <typename K> void smem_attr(K kern, size_t smem) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+inline int ct_rows(int n1, int n2) {
+  int rb = 256 / (n1 >> 3);
+  if (rb > 8) rb = 8;
+  while (rb > n2) rb >>= 1;
+  return rb;
+}
+
+template <typename T, int N> void cols_n(const fvim_ctx* c, bool inverse, void* planes, int nplanes) {
+  typedef typename Cx<T>::t V;
+  int kc = (int)(64 / sizeof(V));
+  while (kc > 1 && kc * (N / 8) > 512) kc >>= 1;
+  if (kc > c->h1) kc = c->h1;
+  const int threads = kc * (N / 8);
+  const size_t smem = (size_t)kc * N * sizeof(V);
+  dim3 grid(c->h1 / kc, nplanes);
+  if (inverse) {
+    smem_attr(k_cols_ct<T, true, N>, smem);
+    k_cols_ct<T, true, N><<<grid, threads, smem, c->stream>>>((V*)planes, (const V*)c->tw2, c->h1, kc);
+  } else {
+    smem_attr(k_cols_ct<T, false, N>, smem);
+    k_cols_ct<T, false, N><<<grid, threads, smem, c->stream>>>((V*)planes, (const V*)c->tw2, c->h1, kc);
+  }
+}
+
+template <typename T, int N> void rows_fwd_n(const fvim_ctx* c, const T* eps_p, int z0, int nzs) {
+  typedef typename Cx<T>::t V;
+  const int rb = ct_rows(N, c->n2);
+  const size_t smem = (size_t)rb * 3 * (N + N / 8) * sizeof(V);
+  dim3 grid(c->n2 / rb, nzs);
+  smem_attr(k_rows_fwd6_ct<T, N>, smem);
+  k_rows_fwd6_ct<T, N><<<grid, rb * (N / 8), smem, c->stream>>>(eps_p, (V*)c->spec, (T*)c->nq, (const V*)c->tw1,
+                                                              c->n2, rb, z0, (T)c->lam, (T)c->mu);
+}
+
+template <typename T, int N> void rows_inv_n(const fvim_ctx* c, T* out, T nq_scale, int z0, int nzs) {
+  typedef typename Cx<T>::t V;
+  const int rb = ct_rows(N, c->n2);
+  const size_t smem = (size_t)rb * 3 * (N + N / 8) * sizeof(V);
+  dim3 grid(c->n2 / rb, nzs);
+  const T scale = (T)(1.0 / ((double)N * (double)c->n2));
+  smem_attr(k_rows_inv6_ct<T, N>, smem);
+  k_rows_inv6_ct<T, N><<<grid, rb * (N / 8), smem, c->stream>>>((const V*)c->spec, (const T*)c->nq, out,
+                                                              (const V*)c->tw1, c->n2, rb, z0, nq_scale, scale);
+}
+
+}  // namespace
+
+#define FVIM_CT_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
+
+template <typename T> bool launch_cols_ct(const fvim_ctx* c, bool inverse, void* planes, int nplanes) {
+#define CASE(N)                                 \
+  if (c->n2 == N) {                             \
+    cols_n<T, N>(c, inverse, planes, nplanes);  \
+    return true;                                \
+  }
+  FVIM_CT_SIZES(CASE)
+#undef CASE
+  return false;
+}
+
+template <typename T> bool launch_rows_fwd6_ct(const fvim_ctx* c, const T* eps_p, int z0, int nzs) {
+#define CASE(N)                              \
+  if (c->n1 == N) {                          \
+    rows_fwd_n<T, N>(c, eps_p, z0, nzs);     \
+    return true;                             \
+  }
+  FVIM_CT_SIZES(CASE)
+#undef CASE
+  return false;
+}
+
+template <typename T> bool launch_rows_inv6_ct(const fvim_ctx* c, T* out, T nq_scale, int z0, int nzs) {
+#define CASE(N)                                     \
+  if (c->n1 == N) {                                 \
+    rows_inv_n<T, N>(c, out, nq_scale, z0, nzs);    \
+    return true;                                    \
+  }
+  FVIM_CT_SIZES(CASE)
+#undef CASE
+  return false;
+}
+
+template bool launch_cols_ct<float>(const fvim_ctx*, bool, void*, int);
+template bool launch_cols_ct<double>(const fvim_ctx*, bool, void*, int);
+template bool launch_rows_fwd6_ct<float>(const fvim_ctx*, const float*, int, int);
+template bool launch_rows_fwd6_ct<double>(const fvim_ctx*, const double*, int, int);
+template bool launch_rows_inv6_ct<float>(const fvim_ctx*, float*, float, int, int);
+template bool launch_rows_inv6_ct<double>(const fvim_ctx*, double*, double, int, int);

@@ -204,6 +204,93 @@ __device__ __forceinline__ void reg_stage(V (&v)[8], int (&pos)[8], int t, int n
 }
 
 // ---------------------------------------------------------------------------
+// The same register-resident Stockham FFT with the length N known at compile time:
+// the stage list is unrolled, the first stage has no twiddles, and every index is a
+// shift or a mask.  NF transforms per thread share each shared-memory exchange; the
+// exchange layout is the caller's (Sm::put / Sm::get).  After the call slot m of
+// transform f holds the output at index t + m N/8.
+// ---------------------------------------------------------------------------
+template <int REM> struct StageRadix {
+  static constexpr int v = (REM == 2) ? 2 : ((REM == 4 || REM == 16) ? 4 : ((REM % 8 == 0) ? 8 : 4));
+};
+
+template <typename V, bool INV, int N, int R, int NS>
+__device__ __forceinline__ void stage_ct(V (&v)[8], int (&pos)[8], int t, const V* __restrict__ tw) {
+  constexpr int T8 = N / 8;
+  if constexpr (R == 8) {
+    const int k = t & (NS - 1);
+    if constexpr (NS > 1) {
+      constexpr int step = N / (NS * 8);
+#pragma unroll
+      for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], twiddle<V, INV>(tw, r * k * step));
+    }
+    dft8<V, INV>(v);
+    const int base = (t / NS) * NS * 8 + k;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) pos[r] = base + r * NS;
+  } else if constexpr (R == 4) {
+    constexpr int step = N / (NS * 4);
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const int b = t + g * T8;
+      const int k = b & (NS - 1);
+      V u[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) u[r] = v[2 * r + g];
+      if constexpr (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < 4; ++r) u[r] = cmul(u[r], twiddle<V, INV>(tw, r * k * step));
+      }
+      dft4<V, INV>(u);
+      const int base = (b / NS) * NS * 4 + k;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        v[2 * r + g] = u[r];
+        pos[2 * r + g] = base + r * NS;
+      }
+    }
+  } else {
+    constexpr int step = N / (NS * 2);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int b = t + m * T8;
+      const int k = b & (NS - 1);
+      V c = v[m + 4];
+      if constexpr (NS > 1) c = cmul(c, twiddle<V, INV>(tw, k * step));
+      const V a = v[m];
+      v[m] = cadd(a, c);
+      v[m + 4] = csub(a, c);
+      const int base = (b / NS) * NS * 2 + k;
+      pos[m] = base;
+      pos[m + 4] = base + NS;
+    }
+  }
+}
+
+template <typename V, bool INV, int N, int NF, int NS, class Sm>
+__device__ __forceinline__ void fft_ct(V (&v)[NF][8], int t, const Sm& sm, const V* __restrict__ tw) {
+  constexpr int R = StageRadix<N / NS>::v;
+  int pos[8];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    stage_ct<V, INV, N, R, NS>(v[f], pos, t, tw);
+    if constexpr (NS * R < N) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) sm.put(f, pos[m], v[f][m]);
+    }
+  }
+  if constexpr (NS * R < N) {
+    __syncthreads();
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int m = 0; m < 8; ++m) v[f][m] = sm.get(f, t + m * (N / 8));
+    __syncthreads();
+    fft_ct<V, INV, N, NF, NS * R>(v, t, sm, tw);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // asynchronous global -> shared copies (cp.async), all in flight before one wait
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
@@ -278,6 +365,11 @@ template <typename T> int launch_boussinesq(const fvim_ctx* c, int out_kind, boo
 template <typename T> int launch_return_map(const fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep);
 template <typename T> int launch_commit(const fvim_ctx* c, const T* d_eps, const T* d_eps_p, const T* d_ep);
 template <typename T> int launch_zero_nq(const fvim_ctx* c);
+
+// compile-time-length FFT kernels (fft_ct.cu); false when the length has no variant
+template <typename T> bool launch_cols_ct(const fvim_ctx* c, bool inverse, void* planes, int nplanes);
+template <typename T> bool launch_rows_fwd6_ct(const fvim_ctx* c, const T* eps_p, int z0, int nzs);
+template <typename T> bool launch_rows_inv6_ct(const fvim_ctx* c, T* out, T nq_scale, int z0, int nzs);
 
 // launch sequences of the entry points (capi.cu), used by the solvers
 template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, int kind, T* u3);
