@@ -212,9 +212,9 @@ __device__ __forceinline__ void kelvin_strain(const Mom<V>& A, const Mom<V>& P, 
 // strain of the Boussinesq-Cerruti field of a surface traction t (rotated frame, force on
 // the body per unit area, Eq. B:fourier with its gradient recurrence) at zeta = q z
 template <typename T, typename V>
-__device__ __forceinline__ void bous_strain_add(const V* tr, T zeta, T nu, T mu, V* e) {
-  const T ex = dexp<T>(-zeta);
-  const T c1 = ex / mu, c2 = ex / ((T)2 * mu);
+__device__ __forceinline__ void bous_strain_add(const V* tr, T zeta, T ex, T nu, T imu, V* e) {
+  // ex = exp(-zeta), imu = 1 / mu
+  const T c1 = ex * imu, c2 = (T)0.5 * ex * imu;
   const V t0 = tr[0], t1 = tr[1], t2 = tr[2];
   const V it0 = cmuli(t0), it1 = cmuli(t1), it2 = cmuli(t2);
   // qq: ((1-nu) i t0 + (nu - 1/2) t2 + zeta(-i t0/2 + t2/2)) / mu
@@ -285,18 +285,17 @@ __device__ __forceinline__ ModeGeom<T> mode_geom(int k1, int k2, int n2, T w1, T
 // grid: (h1 / KT, n2); block: KT * nch threads, thread = (chunk, k1 column)
 // smem: W[nz][6][KT] (rotated in place) + Pst[max(nz, 2 nch + 1)][6][KT]
 // ----------------------------------------------------------------------------------
-template <typename T>
+template <typename T, int KT>
 __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __restrict__ spec, typename Cx<T>::t* __restrict__ surf,
-                                const T* __restrict__ zn, int nz, int n2, int h1, int KT, int C, int nch, int prow, T w1,
+                                const T* __restrict__ zn, int nz, int n2, int h1, int C, int nch, int prow, T w1,
                                 T w2, T lam, T mu, T nu, int out_kind, int want_u3, int uniform, T hz) {
   typedef typename Cx<T>::t V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* W = reinterpret_cast<V*>(smraw);                 // [nz][6][KT]
   V* Pst = W + (size_t)nz * 6 * KT;                   // [max(nz, 2 nch + 1)][6][KT]
   T* zs = reinterpret_cast<T*>(Pst + (size_t)prow * KT * 6);  // [nz] depth nodes
-  const int lkt = __ffs(KT) - 1;  // KT is a power of two
   const int kt = threadIdx.x & (KT - 1);
-  const int ch = threadIdx.x >> lkt;
+  const int ch = threadIdx.x / KT;
   const int k1 = blockIdx.x * KT + kt;
   const int k2 = blockIdx.y;
   const size_t plane = (size_t)n2 * h1;
@@ -305,7 +304,7 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
   // 1. load the tile (coalesced KT-wide rows, every copy in flight before one wait) and
   //    the depth nodes
   for (int idx = threadIdx.x; idx < nz * 6 * KT; idx += blockDim.x) {
-    const int zc = idx >> lkt, j = idx & (KT - 1);
+    const int zc = idx / KT, j = idx & (KT - 1);
     cp_async_cx(W + idx, spec + (size_t)zc * plane + colofs + j);
   }
   for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];
@@ -492,6 +491,10 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
   // 6. forward: - branch, combine, image, epilogue, rotate back, store
   {
     Mom<V> A = Ain;
+    const T imu = (T)1 / mu;
+    // exp(-q z_i): one exponential per chunk, then the element factor e^{-qh} per node
+    // on uniform grids
+    T ex = dexp<T>(-g.q * zs[n0]);
     for (int i = n0; i < nend; ++i) {
       V w[6];
 #pragma unroll
@@ -499,7 +502,9 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
       const Mom<V> P = Pn[i * KT + kt];
       V e[6];
       kelvin_strain<T, V>(A, P, w, g.q, nu, mu, e);
-      bous_strain_add<T, V>(tr, g.q * zs[i], nu, mu, e);
+      if (!uniform && i > n0) ex = dexp<T>(-g.q * zs[i]);
+      bous_strain_add<T, V>(tr, g.q * zs[i], ex, nu, imu, e);
+      if (uniform) ex *= ec.E;
       V o[6];
       if (out_kind == FVIM_STRAIN) {
 #pragma unroll
@@ -563,7 +568,7 @@ __global__ void k_boussinesq(typename Cx<T>::t* __restrict__ spec, typename Cx<T
 #pragma unroll
         for (int cc = 0; cc < 6; ++cc) e[cc] = mk<V>(0, 0);
         V tr[3] = {mk<V>(0, 0), mk<V>(0, 0), p};
-        bous_strain_add<T, V>(tr, g.q * zn[i], nu, mu, e);
+        bous_strain_add<T, V>(tr, g.q * zn[i], dexp<T>(-g.q * zn[i]), nu, (T)1 / mu, e);
         if (out_kind == FVIM_STRAIN) {
 #pragma unroll
           for (int cc = 0; cc < 6; ++cc) o[cc] = e[cc];
@@ -601,12 +606,17 @@ template <typename T> int launch_mindlin_depth(const fvim_ctx* c, int out_kind, 
   const int prow = nz > 2 * nch + 1 ? nz : 2 * nch + 1;
   const size_t smem = (size_t)nz * 6 * KT * sizeof(V) + (size_t)prow * KT * sizeof(Mom<V>) + (size_t)nz * sizeof(T);
   if (smem > 227 * 1024) return FVIM_ERR_UNSUPPORTED;
-  cudaFuncSetAttribute(k_mindlin_depth<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid(h1 / KT, n2);
-  k_mindlin_depth<T><<<grid, threads, smem, c->stream>>>(
-      (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, n2, h1, KT, C, nch, prow, (T)(kTwoPi / c->L1),
-      (T)(kTwoPi / c->L2), (T)c->lam, (T)c->mu,
-      (T)c->nu, out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz);
+  const T w1 = (T)(kTwoPi / c->L1), w2 = (T)(kTwoPi / c->L2);
+#define DEPTH(KTV)                                                                                           \
+  if (KT == KTV) {                                                                                           \
+    cudaFuncSetAttribute(k_mindlin_depth<T, KTV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+    k_mindlin_depth<T, KTV><<<grid, threads, smem, c->stream>>>(                                             \
+        (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, n2, h1, C, nch, prow, w1, w2, (T)c->lam, (T)c->mu, \
+        (T)c->nu, out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz);                                         \
+  }
+  DEPTH(16) DEPTH(8) DEPTH(4) DEPTH(2)
+#undef DEPTH
   FVIM_CUDA_CHECK_LAUNCH();
   return FVIM_OK;
 }
