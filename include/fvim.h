@@ -120,6 +120,14 @@ int fvim_commit_state(fvim_ctx* ctx, const void* d_eps, const void* d_eps_p, con
 int fvim_get_state(fvim_ctx* ctx, void* eps_p, void* e_p, void* sigma);
 int fvim_set_state(fvim_ctx* ctx, const void* eps_p, const void* e_p, const void* sigma);
 
+/* fvim_reset_state -- virgin state: eps_p = 0, e_p = 0, sigma = 0 and no contact pressure
+ * (stream ordered).  Lets one context serve a sequence of independent problems. */
+int fvim_reset_state(fvim_ctx* ctx);
+
+/* fvim_footprint -- device bytes a context of this grid and precision holds once its
+ * solvers have run (scratch, plastic state and solver workspace); host computation only. */
+size_t fvim_footprint(int n1, int n2, int nz, int precision);
+
 /* fvim_sync -- wait for the context's stream; returns FVIM_ERR_CUDA on a device error. */
 int fvim_sync(fvim_ctx* ctx);
 

@@ -362,6 +362,26 @@ int fvim_set_state(fvim_ctx* c, const void* eps_p, const void* e_p, const void* 
   return FVIM_OK;
 }
 
+int fvim_reset_state(fvim_ctx* c) {
+  if (!c) return FVIM_ERR_ARG;
+  const size_t es = elem_size(c), nv = nvox(c);
+  if (cudaMemsetAsync(c->st_eps_p, 0, nv * 6 * es, c->stream) || cudaMemsetAsync(c->st_ep, 0, nv * es, c->stream) ||
+      cudaMemsetAsync(c->st_sig, 0, nv * 6 * es, c->stream) ||
+      cudaMemsetAsync(c->st_T, 0, (size_t)c->n1 * c->n2 * es, c->stream))
+    return FVIM_ERR_CUDA;
+  return FVIM_OK;
+}
+
+size_t fvim_footprint(int n1, int n2, int nz, int precision) {
+  if (n1 < 1 || n2 < 1 || nz < 1) return 0;
+  const size_t es = precision == FVIM_FP64 ? 8 : 4;
+  const size_t ns = (size_t)n1 * n2, nv = ns * nz;
+  const size_t spec = (size_t)nz * 6 * n2 * (n1 / 2) * 2 * es + (size_t)nz * 6 * n2 * es;
+  const size_t state = nv * 6 * es * 2 + nv * es + ns * es;
+  const size_t solver = 8 * nv * 6 * es + nv * es + 13 * ns * es + 64 * 1024;
+  return spec + state + solver + (size_t)(n1 + n2) * 2 * es + ns * 2 * es;
+}
+
 int fvim_sync(fvim_ctx* c) {
   if (!c) return FVIM_ERR_ARG;
   return cudaStreamSynchronize(c->stream) == cudaSuccess ? FVIM_OK : FVIM_ERR_CUDA;

@@ -24,7 +24,7 @@ constexpr int NVMAX = 2;      // values reduced per pass
 // surface buffers [N2][N1]
 enum { S_P = 0, S_POLD, S_T, S_G, S_U, S_R, S_H, S_H0, S_DU, S_DUPREV, S_TPREV, S_DT, S_NSURF };
 // volume buffers [Nz][6][N2][N1] and the scalar field [Nz][N2][N1]
-enum { V_X = S_NSURF, V_F, V_XT, V_FT, V_B, V_DEP, V_TMP, V_DE, V_EP, V_PART, V_WZ, V_END };
+enum { V_X = S_NSURF, V_F, V_XT, V_FT, V_B, V_DEP, V_TMP, V_DE, V_EP, V_PART, V_WZ, V_PKS, V_END };
 static_assert(V_END <= FVIM_NSOLVER_BUFS, "workspace slots");
 
 template <typename T> size_t esz() { return sizeof(T); }
@@ -39,6 +39,7 @@ template <typename T> int ensure_ws(fvim_ctx* c) {
   if (cudaMalloc(&c->sv[V_EP], nv * sizeof(T)) != cudaSuccess) return FVIM_ERR_OOM;
   if (cudaMalloc(&c->sv[V_PART], (size_t)RMAXB * NVMAX * sizeof(double)) != cudaSuccess) return FVIM_ERR_OOM;
   if (cudaMalloc(&c->sv[V_WZ], (size_t)c->nz * sizeof(double)) != cudaSuccess) return FVIM_ERR_OOM;
+  if (cudaMalloc(&c->sv[V_PKS], 256) != cudaSuccess) return FVIM_ERR_OOM;
   c->h_part = (double*)malloc((size_t)RMAXB * NVMAX * sizeof(double));
   if (!c->h_part) return FVIM_ERR_OOM;
   // trapezoid weights of the depth nodes times the cell area dA (discrete L2 product)
@@ -270,11 +271,180 @@ template <typename T> int axpby(fvim_ctx* c, T* dst, const T* a, double s, const
 template <typename T> int conv(fvim_ctx* c, const T* p, T* u) { return apply_boussinesq_t<T>(c, p, u, nullptr, FVIM_STRAIN); }
 
 // ---- Polonsky-Keer constrained conjugate gradient ----------------------------------
+// The scalars of an iteration live on the device (PKS); every reduction is finished by a
+// one-block kernel that also applies the scalar logic, so an iteration is a fixed launch
+// sequence without host round trips.  Once the stop test has fired (or a non-finite value
+// appeared) the update kernels return at entry, so iterations issued after convergence
+// leave the pressure untouched: the host only reads the flag every few iterations.
+struct PKS {
+  double nIc, gbar, G_old, beta, delta, rbar, tau, s, err;
+  int done, it, bad, pad;
+};
+
+// sum the partials [nblk][NV] of a reduction grid in a fixed order (one block)
+template <int NV> __device__ __forceinline__ void fin_sum(const double* part, int nblk, double (&out)[NV]) {
+  __shared__ double sh[NV][RT];
+  double v[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v[j] = 0;
+  for (int b = threadIdx.x; b < nblk; b += RT)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] += part[b * NV + j];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) sh[j][threadIdx.x] = v[j];
+  __syncthreads();
+  for (int w = RT / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int j = 0; j < NV; ++j) sh[j][threadIdx.x] += sh[j][threadIdx.x + w];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < NV; ++j) out[j] = sh[j][0];
+}
+
+__global__ void k_fin_stats(const double* part, int nblk, PKS* S) {
+  if (S->done) return;
+  double v[2];
+  fin_sum<2>(part, nblk, v);
+  if (threadIdx.x == 0) {
+    S->nIc = v[1];
+    if (!(v[1] > 0) || !isfinite(v[0])) { S->bad = 1; S->done = 1; }
+    else S->gbar = v[0] / v[1];
+  }
+}
+__global__ void k_fin_G(const double* part, int nblk, PKS* S) {
+  if (S->done) return;
+  double v[1];
+  fin_sum<1>(part, nblk, v);
+  if (threadIdx.x == 0) {
+    S->beta = S->delta * (v[0] / S->G_old);
+    S->G_old = v[0];
+  }
+}
+__global__ void k_fin_rbar(const double* part, int nblk, PKS* S) {
+  if (S->done) return;
+  double v[1];
+  fin_sum<1>(part, nblk, v);
+  if (threadIdx.x == 0) S->rbar = v[0] / S->nIc;
+}
+__global__ void k_fin_tau(const double* part, int nblk, PKS* S) {
+  if (S->done) return;
+  double v[2];
+  fin_sum<2>(part, nblk, v);
+  if (threadIdx.x == 0) S->tau = v[1] != 0 ? v[0] / v[1] : 0.0;
+}
+__global__ void k_fin_scale(const double* part, int nblk, PKS* S, double W, double dA) {
+  if (S->done) return;
+  double v[2];
+  fin_sum<2>(part, nblk, v);
+  if (threadIdx.x == 0) {
+    S->delta = v[1] > 0 ? 0.0 : 1.0;
+    if (!(v[0] > 0) || !isfinite(v[0])) { S->bad = 1; S->done = 1; }
+    else S->s = W / (dA * v[0]);
+  }
+}
+__global__ void k_fin_err(const double* part, int nblk, PKS* S, double W, double dA, double tol, int max_it) {
+  if (S->done) return;
+  double v[2];
+  fin_sum<2>(part, nblk, v);
+  if (threadIdx.x == 0) {
+    S->err = dA * v[0] / W;
+    S->it += 1;
+    if (S->err < tol || S->it >= max_it) S->done = 1;
+    if (!isfinite(S->err)) { S->bad = 1; S->done = 1; }
+  }
+}
+
+template <typename T>
+__global__ void k_pkd_stats(const T* __restrict__ u, const T* __restrict__ h, const T* __restrict__ p, size_t n,
+                            double* part, const PKS* S) {
+  if (S->done) return;
+  double v[2] = {0, 0};
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT)
+    if (p[i] > 0) { v[0] += (double)u[i] - (double)h[i]; v[1] += 1; }
+  block_reduce<2>(v, part);
+}
+template <typename T>
+__global__ void k_pkd_g(const T* __restrict__ u, const T* __restrict__ h, const T* __restrict__ p, T* __restrict__ g,
+                        size_t n, double* part, const PKS* S) {
+  if (S->done) return;
+  const double gbar = S->gbar;
+  double v[1] = {0};
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
+    const T gi = (T)((double)u[i] - (double)h[i] - gbar);
+    g[i] = gi;
+    if (p[i] > 0) v[0] += (double)gi * (double)gi;
+  }
+  block_reduce<1>(v, part);
+}
+template <typename T>
+__global__ void k_pkd_dir(const T* __restrict__ g, const T* __restrict__ p, T* __restrict__ t, size_t n,
+                          const PKS* S) {
+  if (S->done) return;
+  const double beta = S->beta;
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT)
+    t[i] = p[i] > 0 ? (T)((double)g[i] + beta * (double)t[i]) : (T)0;
+}
+template <typename T>
+__global__ void k_pkd_rsum(const T* __restrict__ r, const T* __restrict__ p, size_t n, double* part, const PKS* S) {
+  if (S->done) return;
+  double v[1] = {0};
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT)
+    if (p[i] > 0) v[0] += (double)r[i];
+  block_reduce<1>(v, part);
+}
+template <typename T>
+__global__ void k_pkd_dots(const T* __restrict__ g, const T* __restrict__ t, const T* __restrict__ r,
+                           const T* __restrict__ p, size_t n, double* part, const PKS* S) {
+  if (S->done) return;
+  const double rbar = S->rbar;
+  double v[2] = {0, 0};
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT)
+    if (p[i] > 0) {
+      v[0] += (double)g[i] * (double)t[i];
+      v[1] += ((double)r[i] - rbar) * (double)t[i];
+    }
+  block_reduce<2>(v, part);
+}
+template <typename T>
+__global__ void k_pkd_update(T* __restrict__ p, T* __restrict__ pold, const T* __restrict__ t,
+                             const T* __restrict__ g, size_t n, double* part, const PKS* S) {
+  if (S->done) return;
+  const double tau = S->tau;
+  double v[2] = {0, 0};
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
+    const T po = p[i];
+    T pn = (T)fmax((double)po - tau * (double)t[i], 0.0);
+    const bool ol = (pn == (T)0) && (g[i] < (T)0);
+    if (ol) pn = (T)(-tau * (double)g[i]);
+    pold[i] = po;
+    p[i] = pn;
+    v[0] += (double)pn;
+    v[1] += ol ? 1.0 : 0.0;
+  }
+  block_reduce<2>(v, part);
+}
+template <typename T>
+__global__ void k_pkd_scale(T* __restrict__ p, const T* __restrict__ pold, size_t n, double* part, const PKS* S) {
+  if (S->done) return;
+  const double s = S->s;
+  double v[2] = {0, 0};
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
+    const T pn = (T)(s * (double)p[i]);
+    p[i] = pn;
+    v[0] += fabs((double)pn - (double)pold[i]);
+    v[1] += pn > (T)0 ? 1.0 : 0.0;
+  }
+  block_reduce<2>(v, part);
+}
+
 template <typename T>
 int elastic_contact_t(fvim_ctx* c, const T* h, double W, T* p, const fvim_opts* o, int* iters, double* err_out) {
   const size_t n = (size_t)c->n1 * c->n2;
   const double dA = c->L1 * c->L2 / (double)n;
   double* part = (double*)c->sv[V_PART];
+  PKS* st = (PKS*)c->sv[V_PKS];
   T *pold = S<T>(c, S_POLD), *t = S<T>(c, S_T), *g = S<T>(c, S_G), *u = S<T>(c, S_U), *r = S<T>(c, S_R);
   const int grd = rgrid(n);
   double v[2];
@@ -288,46 +458,40 @@ int elastic_contact_t(fvim_ctx* c, const T* h, double W, T* p, const fvim_opts* 
   }
   k_fill<T><<<grd, RT, 0, c->stream>>>(t, (T)0, n);
   FVIM_CUDA_CHECK_LAUNCH();
-  double delta = 0, G_old = 1, err = INFINITY;
-  int it = 0;
-  for (it = 1; it <= o->cg_max_iter; ++it) {
-    if ((rc = conv<T>(c, p, u))) return rc;
-    k_pk_stats<T><<<grd, RT, 0, c->stream>>>(u, h, p, n, part);
-    FVIM_CUDA_CHECK_LAUNCH();
-    if ((rc = finish<2>(c, grd, v))) return rc;
-    const double nIc = v[1];
-    if (nIc <= 0) return FVIM_ERR_NONFINITE;
-    const double gbar = v[0] / nIc;
-    k_pk_g<T><<<grd, RT, 0, c->stream>>>(u, h, p, g, gbar, n, part);
-    FVIM_CUDA_CHECK_LAUNCH();
-    if ((rc = finish<1>(c, grd, v))) return rc;
-    const double G = v[0];
-    k_pk_dir<T><<<grd, RT, 0, c->stream>>>(g, p, t, delta * (G / G_old), n);
-    FVIM_CUDA_CHECK_LAUNCH();
-    G_old = G;
-    if ((rc = conv<T>(c, t, r))) return rc;
-    k_pk_rsum<T><<<grd, RT, 0, c->stream>>>(r, p, n, part);
-    FVIM_CUDA_CHECK_LAUNCH();
-    if ((rc = finish<1>(c, grd, v))) return rc;
-    const double rbar = v[0] / nIc;
-    k_pk_dots<T><<<grd, RT, 0, c->stream>>>(g, t, r, p, rbar, n, part);
-    FVIM_CUDA_CHECK_LAUNCH();
-    if ((rc = finish<2>(c, grd, v))) return rc;
-    const double tau = v[1] != 0 ? v[0] / v[1] : 0.0;
-    k_pk_update<T><<<grd, RT, 0, c->stream>>>(p, pold, t, g, tau, n, part);
-    FVIM_CUDA_CHECK_LAUNCH();
-    if ((rc = finish<2>(c, grd, v))) return rc;
-    delta = v[1] > 0 ? 0.0 : 1.0;
-    if (!(v[0] > 0) || !isfinite(v[0])) return FVIM_ERR_NONFINITE;
-    k_pk_scale<T><<<grd, RT, 0, c->stream>>>(p, pold, W / (dA * v[0]), n, part);
-    FVIM_CUDA_CHECK_LAUNCH();
-    if ((rc = finish<2>(c, grd, v))) return rc;
-    err = dA * v[0] / W;
-    if (err < o->cg_tol) break;
+  PKS s0;
+  memset(&s0, 0, sizeof(s0));
+  s0.G_old = 1.0;
+  s0.err = INFINITY;
+  if (cudaMemcpyAsync(st, &s0, sizeof(PKS), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
+  PKS sh = s0;
+  const int batch = 4;  // iterations issued between two reads of the stop flag
+  for (int issued = 0; issued < o->cg_max_iter;) {
+    for (int b = 0; b < batch && issued < o->cg_max_iter; ++b, ++issued) {
+      if ((rc = conv<T>(c, p, u))) return rc;
+      k_pkd_stats<T><<<grd, RT, 0, c->stream>>>(u, h, p, n, part, st);
+      k_fin_stats<<<1, RT, 0, c->stream>>>(part, grd, st);
+      k_pkd_g<T><<<grd, RT, 0, c->stream>>>(u, h, p, g, n, part, st);
+      k_fin_G<<<1, RT, 0, c->stream>>>(part, grd, st);
+      k_pkd_dir<T><<<grd, RT, 0, c->stream>>>(g, p, t, n, st);
+      if ((rc = conv<T>(c, t, r))) return rc;
+      k_pkd_rsum<T><<<grd, RT, 0, c->stream>>>(r, p, n, part, st);
+      k_fin_rbar<<<1, RT, 0, c->stream>>>(part, grd, st);
+      k_pkd_dots<T><<<grd, RT, 0, c->stream>>>(g, t, r, p, n, part, st);
+      k_fin_tau<<<1, RT, 0, c->stream>>>(part, grd, st);
+      k_pkd_update<T><<<grd, RT, 0, c->stream>>>(p, pold, t, g, n, part, st);
+      k_fin_scale<<<1, RT, 0, c->stream>>>(part, grd, st, W, dA);
+      k_pkd_scale<T><<<grd, RT, 0, c->stream>>>(p, pold, n, part, st);
+      k_fin_err<<<1, RT, 0, c->stream>>>(part, grd, st, W, dA, o->cg_tol, o->cg_max_iter);
+      FVIM_CUDA_CHECK_LAUNCH();
+    }
+    if (cudaMemcpyAsync(&sh, st, sizeof(PKS), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
+    if (sh.done) break;
   }
-  if (iters) *iters = std::min(it, o->cg_max_iter);
-  if (err_out) *err_out = err;
-  return err < o->cg_tol ? FVIM_OK : FVIM_ERR_NOT_CONVERGED;
+  if (sh.bad) return FVIM_ERR_NONFINITE;
+  if (iters) *iters = sh.it;
+  if (err_out) *err_out = sh.err;
+  return sh.err < o->cg_tol ? FVIM_OK : FVIM_ERR_NOT_CONVERGED;
 }
 
 // ---- DF-SANE on R[x] = x - b - grad^sym N[C:deps_p(x; S)] --------------------------

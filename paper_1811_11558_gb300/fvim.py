@@ -85,6 +85,8 @@ def lib():
         "fvim_plasticity_solve": (i, [vp, vp, vp, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(i),
                                       ctypes.POINTER(d)]),
         "fvim_solve_contact": (i, [vp, vp, ctypes.POINTER(d), i, ctypes.POINTER(Opts), vp, ctypes.POINTER(Report)]),
+        "fvim_reset_state": (i, [vp]),
+        "fvim_footprint": (ctypes.c_size_t, [i, i, i, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -259,6 +261,10 @@ class Context:
 
     def sync(self):
         _check(lib().fvim_sync(self._h), "fvim_sync")
+
+    def reset_state(self):
+        self._stream()
+        _check(lib().fvim_reset_state(self._h), "fvim_reset_state")
 
     # -- solvers ------------------------------------------------------------------
     def default_opts(self, **kw):

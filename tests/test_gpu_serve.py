@@ -1,0 +1,62 @@
+"""Served solves: results are independent of the mix, requests overlap on the device."""
+import numpy as np
+import pytest
+
+from oracle import tensors as T
+from paper_1811_11558_gb300 import inputs
+
+from gpu_util import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+E, NU = 1.0, 0.3
+ES = T.e_star(E, NU)
+
+
+def _requests(prec):
+    from paper_1811_11558_gb300.serve import Request
+
+    reqs = []
+    rng = np.random.default_rng(1815)
+    for i in range(6):
+        n = (16, 32)[i % 2]
+        nz = (8, 12)[(i // 2) % 2]
+        z = inputs.uniform_depth(nz, 0.5)
+        if i % 3 == 2:
+            h = inputs.self_affine_surface(n, 1.0, 0.8, 2, 4, n // 4, 0.1, seed=1813 + i)
+            wmax = 2e-3
+        else:
+            h = inputs.hertz_profile(n, n, 1.0, 1.0, 0.5)
+            wmax = 4e-3 * float(rng.uniform(0.5, 1.0))
+        loads = [wmax * (k + 1) / 3 for k in range(3)]
+        reqs.append(Request(i, n, z, h, loads, precision=prec, sigma_y=0.05 * ES, E_h=0.1, opts={"max_iter": 200}))
+    return reqs
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_result_alone_equals_result_in_the_mix(prec):
+    require_gpu()
+    from paper_1811_11558_gb300.serve import Server
+
+    reqs = _requests(prec)
+    alone = [Server(slots=1).solve(r) for r in reqs[:2]]
+    mix, wall = Server(slots=4).run(reqs)
+    for a, m in zip(alone, mix[:2]):
+        assert np.array_equal(a.pressure, m.pressure)
+        assert a.report["alg1_iters"] == m.report["alg1_iters"]
+    for m in mix:
+        assert m.report["n_increments"] == 3
+        assert abs(m.pressure.sum() / m.pressure.size - m_load(reqs[m.rid])) < 1e-6 * m_load(reqs[m.rid])
+
+
+def m_load(r):
+    return r.loads[-1] / (r.L * r.L)
+
+
+def test_budget_refuses_oversized_request():
+    require_gpu()
+    from paper_1811_11558_gb300.serve import Server
+
+    r = _requests("fp32")[0]
+    with pytest.raises(ValueError):
+        Server(slots=2, hbm_budget=1024).solve(r)

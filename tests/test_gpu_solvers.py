@@ -88,7 +88,7 @@ def _golden_run(prec, **opt_kw):
     ctx = _ctx(n, z, prec, sigma_y=float(g["sigma_y"]), E_h=float(g["E_h"]))
     dt = ctx.dtype
     p = torch.empty(ctx.surf_shape, dtype=dt, device="cuda")
-    opts = ctx.default_opts(**opt_kw)
+    opts = ctx.default_opts(relax=float(g["relax"]), **opt_kw)
     rep = ctx.solve_contact(to_dev(torch, h, dt), list(g["loads"]), p, opts)
     epp = torch.empty(ctx.vol_shape, dtype=dt, device="cuda")
     ep = torch.empty(ctx.scal_shape, dtype=dt, device="cuda")
