@@ -101,6 +101,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """Slowest rank's value (the timing of a replica run is the slowest replica's)."""
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, steps, ms_max, world):
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest time."""
+    return world * units_per_rank * steps / (ms_max / 1e3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -160,35 +175,45 @@ def run_gpu(args):
     ms = t0.elapsed_time(t1)
     prof = ctx.profile_read()
     ctx.profile(False)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if pg is not None:
-        pg.all_reduce(ms_t, op=pg.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = ws * vox * args.steps / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, pg, "cuda")
+    value = replica_throughput(vox, args.steps, ms_max, ws)
 
     # --- end to end through the same C-ABI call with host buffers -------------------
+    # every step copies its input from pinned host memory, applies the operator and copies
+    # the stress back; two contexts on two streams let the copies of one step overlap the
+    # other step's kernels
     h_in = torch.from_numpy(ep).pin_memory()
-    h_out = torch.empty(h_in.shape, dtype=torch.float32).pin_memory()
-    for _ in range(max(1, args.warmup // 2)):
-        d_in.copy_(h_in, non_blocking=True)
-        ctx.apply_mindlin(d_in, d_out)
-        h_out.copy_(d_out, non_blocking=True)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    ctxs = [ctx, Context(N1, N2, z, 1.0, 1.0, precision="fp32", E=E, nu=NU)]
+    d_ins = [d_in, torch.empty_like(d_in)]
+    d_outs = [d_out, torch.empty_like(d_out)]
+    h_outs = [torch.empty(h_in.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+
+    def e2e_step(i):
+        j = i & 1
+        with torch.cuda.stream(streams[j]):
+            d_ins[j].copy_(h_in, non_blocking=True)
+            ctxs[j].apply_mindlin(d_ins[j], d_outs[j])
+            h_outs[j].copy_(d_outs[j], non_blocking=True)
+
+    for i in range(max(2, args.warmup // 2)):
+        e2e_step(i)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        d_in.copy_(h_in, non_blocking=True)
-        ctx.apply_mindlin(d_in, d_out)
-        h_out.copy_(d_out, non_blocking=True)
-    e1.record(stream)
+    e0.record(streams[0])
+    streams[1].wait_event(e0)
+    for i in range(args.steps):
+        e2e_step(i)
+    ends = []
+    for s in streams:
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(s)
+        ends.append(ev)
     barrier()
-    ems = e0.elapsed_time(e1)
-    ems_t = torch.tensor([ems], dtype=torch.float64, device="cuda")
-    if pg is not None:
-        pg.all_reduce(ems_t, op=pg.ReduceOp.MAX)
-    e2e_value = ws * vox * args.steps / (float(ems_t.item()) / 1e3)
-    assert np.isfinite(h_out[0, 0, :4, :4].numpy()).all()
+    ems = max(e0.elapsed_time(ev) for ev in ends)
+    e2e_value = replica_throughput(vox, args.steps, max_over_ranks(ems, pg, "cuda"), ws)
+    assert all(np.isfinite(h[0, 0, :4, :4].numpy()).all() for h in h_outs)
+    h_out = h_outs[0]
 
     # --- roofline of the dominant kernel ---------------------------------------------
     peak, peak_kind = _peaks()
@@ -228,12 +253,16 @@ def run_gpu(args):
                    "voxels": vox, "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "inputs (402.7 MB) larger than L2, no flush"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h_in.numel() * 4),
-                "d2h_bytes_per_step": int(h_out.numel() * 4)},
+                "d2h_bytes_per_step": int(h_out.numel() * 4),
+                "pipeline": "pinned host -> device, apply, device -> pinned host every step; "
+                            "two contexts on two streams alternate steps"},
         "gpu_launches": kernels_per_step * args.steps,
         "kernel_ms": kernel_ms,
         "roofline": roofline,
         "clocks": clocks,
     }
+    if rank == 0 and not args.no_solves:
+        line["solves"] = solve_metrics()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sample_modes=256, sample_planes=None)
     if pg is not None:
@@ -241,6 +270,66 @@ def run_gpu(args):
         pg.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def hertz_case():
+    """Elastic-plastic Hertz contact: rigid paraboloid R = 0.5 in a unit cell, 32 x 32 surface
+    points, 16 uniform depth nodes to z = 0.5, E = 1, nu = 0.3, sigma_y = 0.05 E*, E_h = 0.1 E,
+    five equal increments up to the load of an elastic Hertz peak pressure of 3 sigma_y."""
+    from paper_1811_11558_gb300 import inputs
+
+    es = E / (1 - NU * NU)
+    sy = 0.05 * es
+    p0 = 3 * sy
+    a = np.pi * 0.5 * p0 / (2 * es)
+    wmax = 2 * np.pi * a * a * p0 / 3
+    return dict(n=32, z=inputs.uniform_depth(16, 0.5), h=inputs.hertz_profile(32, 32, 1.0, 1.0, 0.5),
+                loads=[wmax * (k + 1) / 5 for k in range(5)], sigma_y=sy, E_h=0.1 * E)
+
+
+def solve_metrics(repeats=3, served=16, slots=8):
+    """Contact solves/s of Algorithm 1 (relaxation 0.5) on the Hertz case: FP64 and FP32 one
+    solve at a time, and FP32 served (requests admitted as slots free up, solves overlapping on
+    the device), with p50/p99 latency and the FP32 error against the FP64 solution."""
+    import torch
+
+    from paper_1811_11558_gb300 import Context
+    from paper_1811_11558_gb300.serve import Request, Server, percentiles
+
+    c = hertz_case()
+    out = {"workload": "hertz_32x32x16_5inc", "relax": 0.5}
+    press = {}
+    for prec in ("fp64", "fp32"):
+        ctx = Context(c["n"], c["n"], c["z"], 1.0, 1.0, precision=prec, E=E, nu=NU, sigma_y=c["sigma_y"],
+                      E_h=c["E_h"])
+        h = torch.from_numpy(c["h"]).to("cuda", ctx.dtype)
+        p = torch.empty(ctx.surf_shape, dtype=ctx.dtype, device="cuda")
+        opts = ctx.default_opts(relax=0.5, max_iter=400)
+        times, rep = [], None
+        for r in range(repeats + 1):
+            ctx.reset_state()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = ctx.solve_contact(h, c["loads"], p, opts)
+            times.append(time.perf_counter() - t0)
+        t = float(np.median(times[1:]))
+        press[prec] = p.cpu().numpy().astype(np.float64)
+        out[prec + "_plain"] = {"solves_per_s": 1.0 / t, "ms_per_solve": 1e3 * t, "tol": opts.tol,
+                                "alg1_iters": rep["alg1_iters"], "contact_area": rep["contact_area"][-1]}
+        ctx.close()
+    srv = Server(slots=slots)
+    reqs = [Request(i, c["n"], c["z"], c["h"], c["loads"], precision="fp32", E=E, nu=NU, sigma_y=c["sigma_y"],
+                    E_h=c["E_h"], opts={"relax": 0.5, "max_iter": 400}) for i in range(served)]
+    srv.run(reqs[:slots])                       # warm the context pool
+    res, wall = srv.run(reqs)
+    lat = percentiles([r.latency for r in res])
+    out["fp32_served"] = {"solves_per_s": served / wall, "slots": slots, "requests": served,
+                          "p50_ms": 1e3 * lat[50], "p99_ms": 1e3 * lat[99], "arrivals": "all at t = 0"}
+    out["fp32_vs_fp64"] = {
+        "pressure_rel_l2": float(np.linalg.norm(press["fp32"] - press["fp64"]) / np.linalg.norm(press["fp64"])),
+        "area_diff": float(abs((press["fp32"] > 0).mean() - (press["fp64"] > 0).mean()))}
+    out["served_over_fp64_plain"] = out["fp32_served"]["solves_per_s"] / out["fp64_plain"]["solves_per_s"]
+    return out
 
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each kernel on this
@@ -337,6 +426,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="fvim", choices=["fvim", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solves", action="store_true", help="skip the contact-solve metrics")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
