@@ -57,7 +57,7 @@ typedef struct fvim_ctx fvim_ctx;
  * fvim_create -- grid, depth nodes, periodic cell and precision (Sec. 3.1, Eq.
  * periodic_cell).
  *   out        receives the new context (host pointer to an opaque handle).
- *   n1, n2     in-plane points; powers of two, 4 <= n1 <= 4096, 2 <= n2 <= 4096.
+ *   n1, n2     in-plane points; powers of two, 4 <= n1 <= 1024, 2 <= n2 <= 1024.
  *   nz         depth nodes, 2 <= nz <= 512.
  *   z_nodes    HOST array of nz depths, z_nodes[0] == 0, strictly increasing.
  *   L1, L2     cell lengths (> 0).
@@ -183,8 +183,8 @@ typedef struct {
   long mindlin_applies;                        /* total Mindlin-operator applies            */
 } fvim_report;
 
-/* fvim_default_opts -- the defaults: tol 1e-9, max_iter 100, relax 1, cg_tol 1e-12 (FP64) /
- * 1e-6 (FP32), cg_max_iter 2000, df_tol_abs 0, df_tol_rel 1e-10 (FP64) / 1e-5 (FP32),
+/* fvim_default_opts -- the defaults: tol 1e-9 (FP64) / 1e-8 (FP32), max_iter 100, relax 1,
+ * cg_tol 1e-12 / 1e-7, cg_max_iter 2000, df_tol_abs 0, df_tol_rel 1e-10 / 1e-6,
  * df_max_iter 500. */
 int fvim_default_opts(const fvim_ctx* ctx, fvim_opts* opts);
 

@@ -672,13 +672,13 @@ extern "C" {
 int fvim_default_opts(const fvim_ctx* c, fvim_opts* o) {
   if (!c || !o) return FVIM_ERR_ARG;
   const bool dbl = c->prec == FVIM_FP64;
-  o->tol = dbl ? 1e-9 : 1e-7;
+  o->tol = dbl ? 1e-9 : 1e-8;
   o->max_iter = 100;
   o->relax = 1.0;
-  o->cg_tol = dbl ? 1e-12 : 1e-6;
+  o->cg_tol = dbl ? 1e-12 : 1e-7;
   o->cg_max_iter = 2000;
   o->df_tol_abs = 0.0;
-  o->df_tol_rel = dbl ? 1e-10 : 1e-5;
+  o->df_tol_rel = dbl ? 1e-10 : 1e-6;
   o->df_max_iter = 500;
   return FVIM_OK;
 }

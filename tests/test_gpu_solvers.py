@@ -112,8 +112,8 @@ def test_solve_contact_fp64_matches_oracle_hertz():
 def test_solve_contact_fp32_matches_oracle_hertz():
     g, rep, p, epp, ep = _golden_run("fp32", max_iter=200)
     assert rep["status"] == 0
-    assert rel_l2(p, g["p"]) < 1e-4
-    assert rel_l2(ep, g["e_p"]) < 1e-3
+    assert rel_l2(p, g["p"]) < 2e-5
+    assert rel_l2(ep, g["e_p"]) < 2e-5
     assert np.abs(np.array(rep["contact_area"]) - g["areas"]).max() <= 1e-4 + 1.0 / 1024
 
 
