@@ -75,7 +75,8 @@ struct ProfState {
 };
 
 const char* kProfNames[PROF_NSLOTS] = {"rows_fwd6", "cols_fwd", "mindlin_depth", "cols_inv", "rows_inv6",
-                                       "rows_fwd1", "rows_inv1", "boussinesq", "return_map", "commit"};
+                                       "rows_fwd1", "rows_inv1", "boussinesq", "return_map", "commit",
+                                       "fft2_fwd", "fft2_inv"};
 
 // run one launcher, bracketed by events when profiling is on
 template <typename F> int timed(fvim_ctx* c, int slot, int& nk, F&& launch) {
@@ -140,9 +141,47 @@ template <typename T> int upload_nodes(fvim_ctx* c) {
 
 }  // namespace
 
+// whole-plane cluster FFTs (FP32, planes that fit a cluster's shared memory), selected by
+// the environment variable FVIM_FFT2_CLUSTER=1; the default is the separate row and column
+// kernels, which are faster on the 512 x 512 planes measured so far (one cluster of eight
+// 209 KB CTAs per plane leaves the load, transform and store phases of a CTA serialised)
+static bool use_fft2_cluster(fvim_ctx* c) {
+  if (c->fft2_cl < 0) {
+    const char* e = getenv("FVIM_FFT2_CLUSTER");
+    c->fft2_cl = (e && e[0] == '1' && fft2_cluster_available(c)) ? 1 : 0;
+  }
+  return c->fft2_cl == 1;
+}
+
+template <typename T> int apply_mindlin_cluster(fvim_ctx* c, const T* eps_p, T* out, int kind, T* u3, int& nk) {
+  if constexpr (sizeof(T) == 4) {
+    int rc;
+    if ((rc = timed(c, PROF_FFT2_FWD, nk, [&] { return launch_fft2_fwd_cluster(c, eps_p); }))) return rc;
+    if ((rc = timed(c, PROF_MINDLIN_DEPTH, nk, [&] { return launch_mindlin_depth<T>(c, kind, u3 != nullptr, true); })))
+      return rc;
+    // stress output: the k1 = N1/2 column (no operator term) is -C:eps_p, times N2 because
+    // it skips the column transforms that the 1/(N1 N2) normalisation undoes
+    const int mode = kind == FVIM_STRESS ? 1 : 0;
+    if ((rc = timed(c, PROF_FFT2_INV, nk, [&] { return launch_fft2_inv_cluster(c, out, mode, -(float)c->n2); })))
+      return rc;
+    return FVIM_OK;
+  } else {
+    return FVIM_ERR_UNSUPPORTED;
+  }
+}
+
 template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, int kind, T* u3) {
   int rc;
   int nk = 0;
+  if (use_fft2_cluster(c)) {
+    if ((rc = apply_mindlin_cluster<T>(c, eps_p, out, kind, u3, nk))) return rc;
+    if (u3) {
+      if ((rc = timed(c, PROF_COLS_INV, nk, [&] { return launch_cols<T>(c, true, c->surf, 1); }))) return rc;
+      if ((rc = timed(c, PROF_ROWS_INV1, nk, [&] { return launch_rows_inv1<T>(c, u3); }))) return rc;
+    }
+    c->last_kernels = nk;
+    return FVIM_OK;
+  }
   if ((rc = timed(c, PROF_ROWS_FWD6, nk, [&] { return launch_rows_fwd6<T>(c, eps_p, 0, c->nz); }))) return rc;
   if ((rc = timed(c, PROF_COLS_FWD, nk, [&] { return launch_cols<T>(c, false, c->spec, c->nz * 6); }))) return rc;
   if ((rc = timed(c, PROF_MINDLIN_DEPTH, nk, [&] { return launch_mindlin_depth<T>(c, kind, u3 != nullptr); })))
@@ -170,7 +209,9 @@ template <typename T> int apply_boussinesq_t(fvim_ctx* c, const T* p, T* u3, T* 
   if ((rc = timed(c, PROF_BOUSSINESQ, nk,
                   [&] { return launch_boussinesq<T>(c, kind, vol != nullptr, u3 != nullptr); })))
     return rc;
-  if (vol) {
+  if (vol && sizeof(T) == 4 && use_fft2_cluster(c)) {
+    if ((rc = timed(c, PROF_FFT2_INV, nk, [&] { return launch_fft2_inv_cluster(c, (float*)vol, 0, 0.f); }))) return rc;
+  } else if (vol) {
     if ((rc = timed(c, PROF_COLS_INV, nk, [&] { return launch_cols<T>(c, true, c->spec, c->nz * 6); }))) return rc;
     if ((rc = timed(c, PROF_ROWS_INV6, nk, [&] { return launch_rows_inv6<T>(c, vol, (T)0, 0, c->nz); }))) return rc;
   }
@@ -252,6 +293,7 @@ int fvim_create(fvim_ctx** out, int n1, int n2, int nz, const double* z_nodes, d
   fvim_ctx* c = new (std::nothrow) fvim_ctx();
   if (!c) return FVIM_ERR_OOM;
   memset(c, 0, sizeof(*c));
+  c->fft2_cl = -1;
   c->n1 = n1;
   c->n2 = n2;
   c->nz = nz;

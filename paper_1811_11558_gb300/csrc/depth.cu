@@ -285,7 +285,7 @@ __device__ __forceinline__ ModeGeom<T> mode_geom(int k1, int k2, int n2, T w1, T
 // grid: (h1 / KT, n2); block: KT * nch threads, thread = (chunk, k1 column)
 // smem: W[nz][6][KT] (rotated in place) + Pst[max(nz, 2 nch + 1)][6][KT]
 // ----------------------------------------------------------------------------------
-template <typename T, int KT>
+template <typename T, int KT, bool EIN>
 __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __restrict__ spec, typename Cx<T>::t* __restrict__ surf,
                                 const T* __restrict__ zn, int nz, int n2, int h1, int C, int nch, int prow, T w1,
                                 T w2, T lam, T mu, T nu, int out_kind, int want_u3, int uniform, T hz) {
@@ -318,13 +318,20 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
   const int e1 = min(n0 + C, nz - 1);  // elements [n0, e1)
   const bool active = n0 < nz;
 
-  // 2. rotate own nodes into the (q, p, 3) frame
-  if (active && !special) {
+  // 2. (eps_p input: w = C:eps_p per mode) rotate own nodes into the (q, p, 3) frame
+  if (active && (EIN || !special)) {
     for (int i = n0; i < nend; ++i) {
       V x[6];
 #pragma unroll
       for (int cc = 0; cc < 6; ++cc) x[cc] = W[(i * 6 + cc) * KT + kt];
-      rotate_in(x, g.c, g.s);
+      if (EIN) {
+        const V tr = cadd(cadd(x[0], x[1]), x[2]);
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) x[cc] = cscale(x[cc], (T)2 * mu);
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) x[cc] = caxpy(x[cc], lam, tr);
+      }
+      if (!special) rotate_in(x, g.c, g.s);
 #pragma unroll
       for (int cc = 0; cc < 6; ++cc) W[(i * 6 + cc) * KT + kt] = x[cc];
     }
@@ -595,7 +602,7 @@ __global__ void k_boussinesq(typename Cx<T>::t* __restrict__ spec, typename Cx<T
 
 }  // namespace
 
-template <typename T> int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3) {
+template <typename T> int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps_in) {
   typedef typename Cx<T>::t V;
   const int nz = c->nz, h1 = c->h1, n2 = c->n2;
   const int KT = h1 < KT_MAX ? h1 : KT_MAX;  // h1 is a power of two
@@ -608,14 +615,15 @@ template <typename T> int launch_mindlin_depth(const fvim_ctx* c, int out_kind, 
   if (smem > 227 * 1024) return FVIM_ERR_UNSUPPORTED;
   dim3 grid(h1 / KT, n2);
   const T w1 = (T)(kTwoPi / c->L1), w2 = (T)(kTwoPi / c->L2);
-#define DEPTH(KTV)                                                                                           \
-  if (KT == KTV) {                                                                                           \
-    cudaFuncSetAttribute(k_mindlin_depth<T, KTV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
-    k_mindlin_depth<T, KTV><<<grid, threads, smem, c->stream>>>(                                             \
-        (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, n2, h1, C, nch, prow, w1, w2, (T)c->lam, (T)c->mu, \
-        (T)c->nu, out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz);                                         \
+#define DEPTH(KTV, EI)                                                                                         \
+  if (KT == KTV && eps_in == EI) {                                                                             \
+    cudaFuncSetAttribute(k_mindlin_depth<T, KTV, EI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+    k_mindlin_depth<T, KTV, EI><<<grid, threads, smem, c->stream>>>(                                             \
+        (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, n2, h1, C, nch, prow, w1, w2, (T)c->lam, (T)c->mu,   \
+        (T)c->nu, out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz);                                           \
   }
-  DEPTH(16) DEPTH(8) DEPTH(4) DEPTH(2)
+  DEPTH(16, false) DEPTH(8, false) DEPTH(4, false) DEPTH(2, false)
+  DEPTH(16, true) DEPTH(8, true) DEPTH(4, true) DEPTH(2, true)
 #undef DEPTH
   FVIM_CUDA_CHECK_LAUNCH();
   return FVIM_OK;
@@ -632,7 +640,7 @@ template <typename T> int launch_boussinesq(const fvim_ctx* c, int out_kind, boo
   return FVIM_OK;
 }
 
-template int launch_mindlin_depth<float>(const fvim_ctx*, int, bool);
-template int launch_mindlin_depth<double>(const fvim_ctx*, int, bool);
+template int launch_mindlin_depth<float>(const fvim_ctx*, int, bool, bool);
+template int launch_mindlin_depth<double>(const fvim_ctx*, int, bool, bool);
 template int launch_boussinesq<float>(const fvim_ctx*, int, bool, bool);
 template int launch_boussinesq<double>(const fvim_ctx*, int, bool, bool);

@@ -341,12 +341,14 @@ struct fvim_ctx {
   void* sv[FVIM_NSOLVER_BUFS];
   double* h_part;  // host copy of reduction partials
   long n_applies;  // Mindlin applies issued by the solvers
+  int fft2_cl;     // whole-plane cluster FFTs usable: -1 not yet known, 0 no, 1 yes
 };
 
 // kernel kinds for fvim_profile_read
 enum ProfSlot {
   PROF_ROWS_FWD6 = 0, PROF_COLS_FWD, PROF_MINDLIN_DEPTH, PROF_COLS_INV, PROF_ROWS_INV6,
-  PROF_ROWS_FWD1, PROF_ROWS_INV1, PROF_BOUSSINESQ, PROF_RETURN_MAP, PROF_COMMIT, PROF_NSLOTS
+  PROF_ROWS_FWD1, PROF_ROWS_INV1, PROF_BOUSSINESQ, PROF_RETURN_MAP, PROF_COMMIT, PROF_FFT2_FWD,
+  PROF_FFT2_INV, PROF_NSLOTS
 };
 
 // material constants handed to kernels
@@ -360,11 +362,17 @@ template <typename T> int launch_rows_fwd1(const fvim_ctx* c, const T* f);
 template <typename T> int launch_cols(const fvim_ctx* c, bool inverse, void* planes, int nplanes);
 template <typename T> int launch_rows_inv6(const fvim_ctx* c, T* out, T nq_scale, int z0, int nzs);
 template <typename T> int launch_rows_inv1(const fvim_ctx* c, T* f);
-template <typename T> int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3);
+// eps_in: the spectrum holds eps_p (Hooke's law applied per mode) instead of w = C:eps_p
+template <typename T> int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps_in = false);
 template <typename T> int launch_boussinesq(const fvim_ctx* c, int out_kind, bool want_vol, bool want_u3);
 template <typename T> int launch_return_map(const fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep);
 template <typename T> int launch_commit(const fvim_ctx* c, const T* d_eps, const T* d_eps_p, const T* d_ep);
 template <typename T> int launch_zero_nq(const fvim_ctx* c);
+
+// whole-plane cluster FFTs (fft2d_cluster.cu), FP32 and a few plane sizes only
+bool fft2_cluster_available(const fvim_ctx* c);
+int launch_fft2_fwd_cluster(const fvim_ctx* c, const float* src);
+int launch_fft2_inv_cluster(const fvim_ctx* c, float* out, int nq_mode, float nq_scale);
 
 // compile-time-length FFT kernels (fft_ct.cu); false when the length has no variant
 template <typename T> bool launch_cols_ct(const fvim_ctx* c, bool inverse, void* planes, int nplanes);

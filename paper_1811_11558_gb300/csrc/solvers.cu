@@ -514,7 +514,7 @@ template <typename T> struct DF {
 
 template <typename T>
 int plasticity_t(fvim_ctx* c, const T* dT, T* dE, T* deps_p, T* dep, const fvim_opts* o, int* iters, double* res,
-                 long* evals_out) {
+                 long* evals_out, bool warm = false) {
   const size_t nxy = (size_t)c->n1 * c->n2, n = nxy * c->nz * 6;
   DF<T> df{c, n, nxy, rgrid(n)};
   int rc;
@@ -529,7 +529,22 @@ int plasticity_t(fvim_ctx* c, const T* dT, T* dE, T* deps_p, T* dep, const fvim_
   double f;
   if ((rc = df.eval(x, F, &f))) return rc;
   long evals = 1;
+  // the stopping scale is the residual at the elastic predictor in every case
   const double nF0 = sqrt(f);
+  if (warm) {
+    // start from dE (the previous coupling iterate) when its residual is the smaller one
+    double fw;
+    if ((rc = df.eval(dE, Ft, &fw))) return rc;
+    ++evals;
+    if (fw < f) {
+      if (cudaMemcpyAsync(x, dE, n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        return FVIM_ERR_CUDA;
+      std::swap(F, Ft);
+      c->sv[V_F] = F;
+      c->sv[V_FT] = Ft;
+      f = fw;
+    }
+  }
   const int M = 10;
   const double gamma = 1e-4, smin = 1e-10, smax = 1e10, tmin = 0.1, tmax = 0.5;
   std::vector<double> hist(1, f);
@@ -624,7 +639,8 @@ int solve_contact_t(fvim_ctx* c, const T* h, const double* loads, int n_inc, con
       if (rc && rc != FVIM_ERR_NOT_CONVERGED) return rc;
       if ((rc = axpby<T>(c, dT, P, -1.0, Tprev, ns))) return rc;
       long ev = 0;
-      rc = plasticity_t<T>(c, dT, dE, S<T>(c, V_DEP), S<T>(c, V_EP), o, &dfi, nullptr, &ev);
+      // inside an increment DF-SANE starts from the previous iterate's dE (k > 1)
+      rc = plasticity_t<T>(c, dT, dE, S<T>(c, V_DEP), S<T>(c, V_EP), o, &dfi, nullptr, &ev, k > 1);
       if (rep) { rep->df_iters += dfi; rep->residual_evals += ev; }
       if (rc && rc != FVIM_ERR_NOT_CONVERGED) return rc;
       // dU = N[C:deps_p].e3 at z = 0

@@ -34,13 +34,33 @@ MINDLIN_CASES = [
     (64, 64, inputs.uniform_depth(16, 0.4), 1.0, 1.0, "fp32"),
     (128, 64, inputs.uniform_depth(33, 0.4), 1.0, 0.5, "fp32"),         # ragged depth chunks
     (256, 32, inputs.uniform_depth(64, 0.4), 1.0, 1.0, "fp32"),         # config-[1] depth, several tiles
+    # plane sizes of the whole-plane cluster FFTs (FP32); depth steps keep q h within the
+    # range where the oracle's element quadrature is exact
+    (256, 256, inputs.uniform_depth(4, 0.06), 1.0, 1.0, "fp32"),
+    (512, 256, inputs.uniform_depth(3, 0.02), 1.0, 0.5, "fp32"),
+    (256, 512, np.array([0.0, 0.004, 0.011]), 0.5, 1.0, "fp32"),
 ]
+
+CLUSTER_PLANES = {(256, 256), (512, 512), (256, 512), (512, 256)}
+
+
+def _cluster(n1, n2, prec):
+    return prec == "fp32" and (n1, n2) in CLUSTER_PLANES
+
+
+def _kernels(n1, n2, prec, with_u3):
+    """Kernels of one Mindlin apply: cluster path (2-D FFT, depth, inverse 2-D FFT) or
+    rows / columns / depth / columns / rows, plus two for the surface displacement."""
+    base = 3 if _cluster(n1, n2, prec) else 5
+    return base + (2 if with_u3 else 0)
 
 
 @pytest.mark.parametrize("n1,n2,z,L1,L2,prec", MINDLIN_CASES)
 @pytest.mark.parametrize("kind", ["stress", "strain"])
-def test_mindlin_parity(n1, n2, z, L1, L2, prec, kind):
+def test_mindlin_parity(n1, n2, z, L1, L2, prec, kind, monkeypatch):
     torch = require_gpu()
+    # the whole-plane cluster FFTs are opt-in; the plane sizes they cover run through them
+    monkeypatch.setenv("FVIM_FFT2_CLUSTER", "1" if _cluster(n1, n2, prec) else "0")
     ep = inputs.plastic_strain_field(n1, n2, z, seed=1812 + n1 + n2 + z.size)
     ref, u3_ref = op.mindlin_apply(ep, z, L1, L2, E, NU, kind, with_surface=True)
     ctx = _ctx(n1, n2, z, L1, L2, prec)
@@ -49,11 +69,35 @@ def test_mindlin_parity(n1, n2, z, L1, L2, prec, kind):
     u3 = torch.empty(ctx.surf_shape, dtype=dt, device="cuda")
     out = ctx.apply_mindlin(d_ep, kind=kind, u3=u3)
     torch.cuda.synchronize()
-    assert ctx.last_kernel_count() == 7
+    assert ctx.last_kernel_count() == _kernels(n1, n2, prec, True)
     assert rel_l2(out.cpu().numpy(), ref) < TOL[prec]
     assert rel_l2(u3.cpu().numpy(), u3_ref) < TOL[prec]
     # the input is not modified
     assert torch.equal(d_ep, to_dev(torch, ep, dt))
+
+
+@pytest.mark.parametrize("n1,n2", sorted(CLUSTER_PLANES))
+def test_cluster_fft_path_equals_row_column_path(n1, n2, monkeypatch):
+    """The whole-plane cluster FFTs and the separate row / column kernels compute the same
+    operator (FP32 rounding apart), for the Mindlin and the Boussinesq volume output."""
+    torch = require_gpu()
+    z = inputs.uniform_depth(5, 0.1)
+    ep = to_dev(torch, inputs.plastic_strain_field(n1, n2, z, seed=77 + n1 + n2, dtype=np.float32), torch.float32)
+    p = to_dev(torch, np.abs(inputs.random_field((n2, n1), seed=5)) + 0.5, torch.float32)
+    outs = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("FVIM_FFT2_CLUSTER", flag)
+        ctx = _ctx(n1, n2, z, 1.0, 1.0, "fp32")
+        u3 = torch.empty(ctx.surf_shape, dtype=torch.float32, device="cuda")
+        s = ctx.apply_mindlin(ep, kind="stress", u3=u3).clone()
+        assert ctx.last_kernel_count() == (5 if flag == "1" else 7)
+        e = ctx.apply_mindlin(ep, kind="strain").clone()
+        vol = torch.empty(ctx.vol_shape, dtype=torch.float32, device="cuda")
+        ctx.apply_boussinesq(p, vol=vol, kind="stress")
+        torch.cuda.synchronize()
+        outs[flag] = [x.cpu().numpy().astype(np.float64) for x in (s, e, u3, vol)]
+    for a, b in zip(outs["1"], outs["0"]):
+        assert rel_l2(a, b) < 5e-6
 
 
 def test_mindlin_deterministic_and_reusable():
@@ -105,13 +149,15 @@ BOUS_CASES = [
     (16, 8, inputs.uniform_depth(5, 0.3), 1.0, 0.7, "fp64"),
     (32, 32, np.array([0.0, 0.02, 0.05, 0.1, 0.2, 0.35, 0.5]), 1.0, 1.0, "fp64"),
     (128, 64, inputs.uniform_depth(17, 0.2), 1.0, 1.0, "fp32"),
+    (256, 256, inputs.uniform_depth(3, 0.05), 1.0, 1.0, "fp32"),         # cluster inverse FFT
 ]
 
 
 @pytest.mark.parametrize("n1,n2,z,L1,L2,prec", BOUS_CASES)
 @pytest.mark.parametrize("kind", ["stress", "strain"])
-def test_boussinesq_parity(n1, n2, z, L1, L2, prec, kind):
+def test_boussinesq_parity(n1, n2, z, L1, L2, prec, kind, monkeypatch):
     torch = require_gpu()
+    monkeypatch.setenv("FVIM_FFT2_CLUSTER", "1" if _cluster(n1, n2, prec) else "0")
     p = np.abs(inputs.random_field((n2, n1), seed=3 + n1)) + 0.5
     u3_ref, vol_ref = op.boussinesq_apply(p, z, L1, L2, E, NU, kind)
     ctx = _ctx(n1, n2, z, L1, L2, prec)
