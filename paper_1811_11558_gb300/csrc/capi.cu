@@ -108,8 +108,7 @@ void free_all(fvim_ctx* c) {
   free(c->z_host);
   for (int i = 0; i < FVIM_NSOLVER_BUFS; ++i)
     if (c->sv[i]) { cudaFree(c->sv[i]); c->sv[i] = nullptr; }
-  free(c->h_part);
-  c->h_part = nullptr;
+  solver_release(c);
   ProfState* ps = (ProfState*)c->prof;
   if (ps) {
     for (auto& v : ps->ev)
@@ -332,7 +331,9 @@ int fvim_create(fvim_ctx** out, int n1, int n2, int nz, const double* z_nodes, d
     if (cudaMalloc(a.p, a.bytes) != cudaSuccess) { cudaGetLastError(); free_all(c); delete c; return FVIM_ERR_OOM; }
     if (cudaMemset(*a.p, 0, a.bytes) != cudaSuccess) { free_all(c); delete c; return FVIM_ERR_CUDA; }
   }
-  if (cudaDeviceSynchronize() != cudaSuccess) { free_all(c); delete c; return FVIM_ERR_CUDA; }
+  // the fills above run on the legacy stream; wait for them without touching other streams
+  // (another thread may be capturing a graph on its own non-blocking stream)
+  if (cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) { free_all(c); delete c; return FVIM_ERR_CUDA; }
   *out = c;
   return FVIM_OK;
 }
@@ -340,6 +341,8 @@ int fvim_create(fvim_ctx** out, int n1, int n2, int nz, const double* z_nodes, d
 int fvim_set_material(fvim_ctx* c, double E, double nu, double sigma_y, double E_h) {
   if (!c) return FVIM_ERR_ARG;
   if (!(E > 0) || !(nu > -1.0 && nu < 0.5) || !(sigma_y > 0) || !(E_h >= 0)) return FVIM_ERR_ARG;
+  // captured solver graphs hold the material constants as kernel arguments
+  if (E != c->E || nu != c->nu || sigma_y != c->sigma_y || E_h != c->E_h) solver_drop_graphs(c);
   c->E = E;
   c->nu = nu;
   c->sigma_y = sigma_y;

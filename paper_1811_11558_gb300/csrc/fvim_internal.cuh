@@ -342,6 +342,7 @@ struct fvim_ctx {
   double* h_part;  // host copy of reduction partials
   long n_applies;  // Mindlin applies issued by the solvers
   int fft2_cl;     // whole-plane cluster FFTs usable: -1 not yet known, 0 no, 1 yes
+  void* srt;       // solver runtime (solvers.cu): own stream, events, captured CUDA graphs
 };
 
 // kernel kinds for fvim_profile_read
@@ -368,6 +369,10 @@ template <typename T> int launch_boussinesq(const fvim_ctx* c, int out_kind, boo
 template <typename T> int launch_return_map(const fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep);
 template <typename T> int launch_commit(const fvim_ctx* c, const T* d_eps, const T* d_eps_p, const T* d_ep);
 template <typename T> int launch_zero_nq(const fvim_ctx* c);
+
+// solver runtime (solvers.cu): release, and drop captured graphs after a material change
+void solver_release(fvim_ctx* c);
+void solver_drop_graphs(fvim_ctx* c);
 
 // whole-plane cluster FFTs (fft2d_cluster.cu), FP32 and a few plane sizes only
 bool fft2_cluster_available(const fvim_ctx* c);

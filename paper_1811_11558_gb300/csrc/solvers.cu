@@ -11,6 +11,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <new>
+#include <utility>
 #include <vector>
 
 #include "fvim_internal.cuh"
@@ -40,8 +42,10 @@ template <typename T> int ensure_ws(fvim_ctx* c) {
   if (cudaMalloc(&c->sv[V_PART], (size_t)RMAXB * NVMAX * sizeof(double)) != cudaSuccess) return FVIM_ERR_OOM;
   if (cudaMalloc(&c->sv[V_WZ], (size_t)c->nz * sizeof(double)) != cudaSuccess) return FVIM_ERR_OOM;
   if (cudaMalloc(&c->sv[V_PKS], 256) != cudaSuccess) return FVIM_ERR_OOM;
-  c->h_part = (double*)malloc((size_t)RMAXB * NVMAX * sizeof(double));
-  if (!c->h_part) return FVIM_ERR_OOM;
+  if (cudaMallocHost(&c->h_part, (size_t)RMAXB * NVMAX * sizeof(double) + 256) != cudaSuccess) {
+    c->h_part = nullptr;
+    return FVIM_ERR_OOM;
+  }
   // trapezoid weights of the depth nodes times the cell area dA (discrete L2 product)
   std::vector<double> wz(c->nz, 0.0);
   const double dA = c->L1 * c->L2 / (double)ns;
@@ -59,6 +63,103 @@ template <typename T> int ensure_ws(fvim_ctx* c) {
 }
 
 template <typename T> T* S(fvim_ctx* c, int i) { return (T*)c->sv[i]; }
+
+// ---- solver runtime: an own non-blocking stream (so that the solver loops can be captured
+// into CUDA graphs whatever stream the caller uses) and the captured graphs ---------------
+struct GraphKey {
+  const void* ptr[3];
+  double d[2];
+  int i;
+  bool operator==(const GraphKey& o) const {
+    return ptr[0] == o.ptr[0] && ptr[1] == o.ptr[1] && ptr[2] == o.ptr[2] && d[0] == o.d[0] && d[1] == o.d[1] &&
+           i == o.i;
+  }
+};
+struct SolverRT {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<std::pair<GraphKey, cudaGraphExec_t>> cg, df;  // CG batches, residual evaluations
+};
+constexpr size_t kMaxGraphs = 8;
+
+static void drop(std::vector<std::pair<GraphKey, cudaGraphExec_t>>& v) {
+  for (auto& e : v) cudaGraphExecDestroy(e.second);
+  v.clear();
+}
+
+static SolverRT* rt(fvim_ctx* c) {
+  if (c->srt) return (SolverRT*)c->srt;
+  SolverRT* r = new (std::nothrow) SolverRT();
+  if (!r) return nullptr;
+  if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&r->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&r->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (r->stream) cudaStreamDestroy(r->stream);
+    if (r->ev_in) cudaEventDestroy(r->ev_in);
+    delete r;
+    return nullptr;
+  }
+  c->srt = r;
+  return r;
+}
+
+// Runs body() (a fixed launch sequence on c->stream) through a CUDA graph captured on first
+// use for this key; launches it directly while kernels are being timed one by one.
+template <class F>
+static int graph_run(fvim_ctx* c, std::vector<std::pair<GraphKey, cudaGraphExec_t>>& cache, const GraphKey& key,
+                     F&& body) {
+  if (c->prof) return body();
+  for (auto& e : cache)
+    if (e.first == key) return cudaGraphLaunch(e.second, c->stream) == cudaSuccess ? FVIM_OK : FVIM_ERR_CUDA;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return body();
+  }
+  const int rc = body();
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+  if (ce != cudaSuccess || !g) {
+    // the capture was invalidated (nothing ran): issue the sequence directly
+    cudaGetLastError();
+    return body();
+  }
+  if (rc != FVIM_OK) {
+    cudaGraphDestroy(g);
+    return rc;
+  }
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) return FVIM_ERR_CUDA;
+  if (cache.size() >= kMaxGraphs) {
+    cudaGraphExecDestroy(cache.front().second);
+    cache.erase(cache.begin());
+  }
+  cache.emplace_back(key, ex);
+  return cudaGraphLaunch(ex, c->stream) == cudaSuccess ? FVIM_OK : FVIM_ERR_CUDA;
+}
+
+// The solver entry points run on the runtime's stream, ordered after the caller's stream
+// by an event on entry, and the caller's stream waits for them on exit.
+struct OnSolverStream {
+  fvim_ctx* c;
+  cudaStream_t user;
+  SolverRT* r;
+  explicit OnSolverStream(fvim_ctx* ctx) : c(ctx), user(ctx->stream), r(rt(ctx)) {
+    if (r && cudaEventRecord(r->ev_in, user) == cudaSuccess && cudaStreamWaitEvent(r->stream, r->ev_in, 0) == cudaSuccess)
+      c->stream = r->stream;
+    else
+      r = nullptr;
+  }
+  ~OnSolverStream() {
+    if (!r) return;
+    cudaEventRecord(r->ev_out, r->stream);
+    cudaStreamWaitEvent(user, r->ev_out, 0);
+    c->stream = user;
+  }
+};
+
 
 // ---- block reduction of NV doubles into partial[blockIdx.x][NV] -------------------
 template <int NV> __device__ __forceinline__ void block_reduce(double (&v)[NV], double* partial) {
@@ -445,7 +546,7 @@ int elastic_contact_t(fvim_ctx* c, const T* h, double W, T* p, const fvim_opts* 
   const double dA = c->L1 * c->L2 / (double)n;
   double* part = (double*)c->sv[V_PART];
   PKS* st = (PKS*)c->sv[V_PKS];
-  T *pold = S<T>(c, S_POLD), *t = S<T>(c, S_T), *g = S<T>(c, S_G), *u = S<T>(c, S_U), *r = S<T>(c, S_R);
+  T *pold = S<T>(c, S_POLD), *t = S<T>(c, S_T), *g = S<T>(c, S_G), *u = S<T>(c, S_U), *r_ = S<T>(c, S_R);
   const int grd = rgrid(n);
   double v[2];
   int rc;
@@ -463,35 +564,46 @@ int elastic_contact_t(fvim_ctx* c, const T* h, double W, T* p, const fvim_opts* 
   s0.G_old = 1.0;
   s0.err = INFINITY;
   if (cudaMemcpyAsync(st, &s0, sizeof(PKS), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
-  PKS sh = s0;
+  PKS* sh = reinterpret_cast<PKS*>(c->h_part + (size_t)RMAXB * NVMAX);  // pinned
+  *sh = s0;
   const int batch = 4;  // iterations issued between two reads of the stop flag
+  SolverRT* srt = rt(c);
+  const GraphKey key{{h, p, nullptr}, {W, o->cg_tol}, o->cg_max_iter};
   for (int issued = 0; issued < o->cg_max_iter;) {
-    for (int b = 0; b < batch && issued < o->cg_max_iter; ++b, ++issued) {
-      if ((rc = conv<T>(c, p, u))) return rc;
-      k_pkd_stats<T><<<grd, RT, 0, c->stream>>>(u, h, p, n, part, st);
-      k_fin_stats<<<1, RT, 0, c->stream>>>(part, grd, st);
-      k_pkd_g<T><<<grd, RT, 0, c->stream>>>(u, h, p, g, n, part, st);
-      k_fin_G<<<1, RT, 0, c->stream>>>(part, grd, st);
-      k_pkd_dir<T><<<grd, RT, 0, c->stream>>>(g, p, t, n, st);
-      if ((rc = conv<T>(c, t, r))) return rc;
-      k_pkd_rsum<T><<<grd, RT, 0, c->stream>>>(r, p, n, part, st);
-      k_fin_rbar<<<1, RT, 0, c->stream>>>(part, grd, st);
-      k_pkd_dots<T><<<grd, RT, 0, c->stream>>>(g, t, r, p, n, part, st);
-      k_fin_tau<<<1, RT, 0, c->stream>>>(part, grd, st);
-      k_pkd_update<T><<<grd, RT, 0, c->stream>>>(p, pold, t, g, n, part, st);
-      k_fin_scale<<<1, RT, 0, c->stream>>>(part, grd, st, W, dA);
-      k_pkd_scale<T><<<grd, RT, 0, c->stream>>>(p, pold, n, part, st);
-      k_fin_err<<<1, RT, 0, c->stream>>>(part, grd, st, W, dA, o->cg_tol, o->cg_max_iter);
-      FVIM_CUDA_CHECK_LAUNCH();
-    }
-    if (cudaMemcpyAsync(&sh, st, sizeof(PKS), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
+    const int nb = std::min(batch, o->cg_max_iter - issued);
+    auto iterations = [&]() -> int {
+      int r;
+      for (int b = 0; b < nb; ++b) {
+        if ((r = conv<T>(c, p, u))) return r;
+        k_pkd_stats<T><<<grd, RT, 0, c->stream>>>(u, h, p, n, part, st);
+        k_fin_stats<<<1, RT, 0, c->stream>>>(part, grd, st);
+        k_pkd_g<T><<<grd, RT, 0, c->stream>>>(u, h, p, g, n, part, st);
+        k_fin_G<<<1, RT, 0, c->stream>>>(part, grd, st);
+        k_pkd_dir<T><<<grd, RT, 0, c->stream>>>(g, p, t, n, st);
+        if ((r = conv<T>(c, t, r_))) return r;
+        k_pkd_rsum<T><<<grd, RT, 0, c->stream>>>(r_, p, n, part, st);
+        k_fin_rbar<<<1, RT, 0, c->stream>>>(part, grd, st);
+        k_pkd_dots<T><<<grd, RT, 0, c->stream>>>(g, t, r_, p, n, part, st);
+        k_fin_tau<<<1, RT, 0, c->stream>>>(part, grd, st);
+        k_pkd_update<T><<<grd, RT, 0, c->stream>>>(p, pold, t, g, n, part, st);
+        k_fin_scale<<<1, RT, 0, c->stream>>>(part, grd, st, W, dA);
+        k_pkd_scale<T><<<grd, RT, 0, c->stream>>>(p, pold, n, part, st);
+        k_fin_err<<<1, RT, 0, c->stream>>>(part, grd, st, W, dA, o->cg_tol, o->cg_max_iter);
+        FVIM_CUDA_CHECK_LAUNCH();
+      }
+      return FVIM_OK;
+    };
+    // a full batch is one captured graph per (surface, pressure, load, tolerance)
+    if ((rc = (nb == batch && srt) ? graph_run(c, srt->cg, key, iterations) : iterations())) return rc;
+    issued += nb;
+    if (cudaMemcpyAsync(sh, st, sizeof(PKS), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
-    if (sh.done) break;
+    if (sh->done) break;
   }
-  if (sh.bad) return FVIM_ERR_NONFINITE;
-  if (iters) *iters = sh.it;
-  if (err_out) *err_out = sh.err;
-  return sh.err < o->cg_tol ? FVIM_OK : FVIM_ERR_NOT_CONVERGED;
+  if (sh->bad) return FVIM_ERR_NONFINITE;
+  if (iters) *iters = sh->it;
+  if (err_out) *err_out = sh->err;
+  return sh->err < o->cg_tol ? FVIM_OK : FVIM_ERR_NOT_CONVERGED;
 }
 
 // ---- DF-SANE on R[x] = x - b - grad^sym N[C:deps_p(x; S)] --------------------------
@@ -499,15 +611,23 @@ template <typename T> struct DF {
   fvim_ctx* c;
   size_t n, nxy;
   int grd;
-  // F(x) into Fx; returns ||F||^2 (weighted)
+  // F(x) into Fx; returns ||F||^2 (weighted).  The launch sequence is one captured graph
+  // per (x, Fx) pair.
   int eval(const T* x, T* Fx, double* f) {
-    int rc;
-    if ((rc = return_map_t<T>(c, x, S<T>(c, V_DEP), S<T>(c, V_EP)))) return rc;
-    if ((rc = apply_mindlin_t<T>(c, S<T>(c, V_DEP), S<T>(c, V_TMP), FVIM_STRAIN, nullptr))) return rc;
+    auto seq = [&]() -> int {
+      int r;
+      if ((r = return_map_t<T>(c, x, S<T>(c, V_DEP), S<T>(c, V_EP)))) return r;
+      if ((r = apply_mindlin_t<T>(c, S<T>(c, V_DEP), S<T>(c, V_TMP), FVIM_STRAIN, nullptr))) return r;
+      k_df_res<T><<<grd, RT, 0, c->stream>>>(x, S<T>(c, V_B), S<T>(c, V_TMP), Fx, (const double*)c->sv[V_WZ], nxy,
+                                            n, (double*)c->sv[V_PART]);
+      FVIM_CUDA_CHECK_LAUNCH();
+      return FVIM_OK;
+    };
+    SolverRT* srt = rt(c);
+    const GraphKey key{{x, Fx, nullptr}, {0.0, 0.0}, 0};
+    int rc = srt ? graph_run(c, srt->df, key, seq) : seq();
+    if (rc) return rc;
     c->n_applies++;
-    k_df_res<T><<<grd, RT, 0, c->stream>>>(x, S<T>(c, V_B), S<T>(c, V_TMP), Fx, (const double*)c->sv[V_WZ], nxy, n,
-                                          (double*)c->sv[V_PART]);
-    FVIM_CUDA_CHECK_LAUNCH();
     return finish<1>(c, grd, f);
   }
 };
@@ -683,6 +803,28 @@ int solve_contact_t(fvim_ctx* c, const T* h, const double* loads, int n_inc, con
 
 }  // namespace
 
+void solver_drop_graphs(fvim_ctx* c) {
+  SolverRT* r = (SolverRT*)c->srt;
+  if (!r) return;
+  drop(r->cg);
+  drop(r->df);
+}
+
+void solver_release(fvim_ctx* c) {
+  SolverRT* r = (SolverRT*)c->srt;
+  if (r) {
+    drop(r->cg);
+    drop(r->df);
+    if (r->stream) cudaStreamDestroy(r->stream);
+    if (r->ev_in) cudaEventDestroy(r->ev_in);
+    if (r->ev_out) cudaEventDestroy(r->ev_out);
+    delete r;
+    c->srt = nullptr;
+  }
+  if (c->h_part) cudaFreeHost(c->h_part);
+  c->h_part = nullptr;
+}
+
 extern "C" {
 
 int fvim_default_opts(const fvim_ctx* c, fvim_opts* o) {
@@ -709,27 +851,23 @@ static int check_opts(const fvim_opts* o) {
 
 int fvim_elastic_contact(fvim_ctx* c, const void* h, double W, void* p, const fvim_opts* o, int* iters, double* err) {
   if (!c || !h || !p || !(W > 0) || check_opts(o)) return FVIM_ERR_ARG;
-  if (c->prec == FVIM_FP64) {
-    int rc = ensure_ws<double>(c);
-    if (rc) return rc;
-    return elastic_contact_t<double>(c, (const double*)h, W, (double*)p, o, iters, err);
-  }
-  int rc = ensure_ws<float>(c);
+  int rc = c->prec == FVIM_FP64 ? ensure_ws<double>(c) : ensure_ws<float>(c);
   if (rc) return rc;
+  OnSolverStream on(c);
+  if (c->prec == FVIM_FP64) return elastic_contact_t<double>(c, (const double*)h, W, (double*)p, o, iters, err);
   return elastic_contact_t<float>(c, (const float*)h, W, (float*)p, o, iters, err);
 }
 
 int fvim_plasticity_solve(fvim_ctx* c, const void* dT, void* dE, void* deps_p, void* dep, const fvim_opts* o,
                           int* iters, double* res) {
   if (!c || !dT || !dE || check_opts(o) || !isfinite(c->sigma_y)) return FVIM_ERR_ARG;
-  int rc;
-  if (c->prec == FVIM_FP64) {
-    if ((rc = ensure_ws<double>(c))) return rc;
+  int rc = c->prec == FVIM_FP64 ? ensure_ws<double>(c) : ensure_ws<float>(c);
+  if (rc) return rc;
+  OnSolverStream on(c);
+  if (c->prec == FVIM_FP64)
     rc = plasticity_t<double>(c, (const double*)dT, (double*)dE, (double*)deps_p, (double*)dep, o, iters, res, nullptr);
-  } else {
-    if ((rc = ensure_ws<float>(c))) return rc;
+  else
     rc = plasticity_t<float>(c, (const float*)dT, (float*)dE, (float*)deps_p, (float*)dep, o, iters, res, nullptr);
-  }
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
   return rc;
 }
@@ -741,13 +879,14 @@ int fvim_solve_contact(fvim_ctx* c, const void* h, const double* loads, int n_in
     if (!(loads[i] > 0) || !isfinite(loads[i])) return FVIM_ERR_ARG;
   if (rep) memset(rep, 0, sizeof(*rep));
   const long a0 = c->n_applies;
-  int rc;
-  if (c->prec == FVIM_FP64) {
-    if ((rc = ensure_ws<double>(c))) return rc;
-    rc = solve_contact_t<double>(c, (const double*)h, loads, n_inc, o, (double*)p_out, rep);
-  } else {
-    if ((rc = ensure_ws<float>(c))) return rc;
-    rc = solve_contact_t<float>(c, (const float*)h, loads, n_inc, o, (float*)p_out, rep);
+  int rc = c->prec == FVIM_FP64 ? ensure_ws<double>(c) : ensure_ws<float>(c);
+  if (rc) return rc;
+  {
+    OnSolverStream on(c);
+    if (c->prec == FVIM_FP64)
+      rc = solve_contact_t<double>(c, (const double*)h, loads, n_inc, o, (double*)p_out, rep);
+    else
+      rc = solve_contact_t<float>(c, (const float*)h, loads, n_inc, o, (float*)p_out, rep);
   }
   if (rep) {
     rep->status = rc;
