@@ -539,6 +539,258 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
 }
 
 // ----------------------------------------------------------------------------------
+// Mindlin depth kernel, register variant (C <= 8 nodes per chunk, compile time).  The
+// summary pass keeps the + branch of the chunk's own elements per node in registers, so
+// the final pass adds the propagated carry (one propagation per node) instead of running
+// the + recursion again, and every pass reads each node of the tile once (the other node
+// of an element is carried in registers).
+// smem: W[nz][6][KT] + SA[nch][KT] + SP[nch][KT] + P0[KT] (moments) + zs[nz]
+// ----------------------------------------------------------------------------------
+template <typename V> __device__ __forceinline__ void ld6(V (&w)[6], const V* W, int node, int KT, int kt) {
+#pragma unroll
+  for (int cc = 0; cc < 6; ++cc) w[cc] = W[(node * 6 + cc) * KT + kt];
+}
+
+template <typename T, int KT, int C, bool EIN>
+__global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* __restrict__ spec,
+                                                         typename Cx<T>::t* __restrict__ surf,
+                                                         const T* __restrict__ zn, int nz, int n2, int h1, int nch,
+                                                         T w1, T w2, T lam, T mu, T nu, int out_kind, int want_u3,
+                                                         int uniform, T hz) {
+  typedef typename Cx<T>::t V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* W = reinterpret_cast<V*>(smraw);                               // [nz][6][KT]
+  Mom<V>* SA = reinterpret_cast<Mom<V>*>(W + (size_t)nz * 6 * KT);  // [nch][KT]
+  Mom<V>* SP = SA + (size_t)nch * KT;                               // [nch][KT]
+  Mom<V>* P0s = SP + (size_t)nch * KT;                              // [KT]
+  T* zs = reinterpret_cast<T*>(P0s + KT);                           // [nz]
+  const int kt = threadIdx.x & (KT - 1);
+  const int ch = threadIdx.x / KT;
+  const int k1 = blockIdx.x * KT + kt;
+  const int k2 = blockIdx.y;
+  const size_t plane = (size_t)n2 * h1;
+  const size_t colofs = (size_t)k2 * h1 + blockIdx.x * KT;
+
+  // 1. load the tile and the depth nodes
+  for (int idx = threadIdx.x; idx < nz * 6 * KT; idx += blockDim.x) {
+    const int zc = idx / KT, j = idx & (KT - 1);
+    cp_async_cx(W + idx, spec + (size_t)zc * plane + colofs + j);
+  }
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];
+  cp_async_wait_all();
+  __syncthreads();
+
+  const ModeGeom<T> g = mode_geom<T>(k1, k2, n2, w1, w2);
+  const bool special = g.zero || g.nyq;
+  const int n0 = ch * C;
+  const int nend = min(n0 + C, nz);
+  const int e1 = min(n0 + C, nz - 1);  // elements [n0, e1)
+  const bool active = n0 < nz;
+
+  // 2. (eps_p input: w = C:eps_p per mode) rotate own nodes into the (q, p, 3) frame
+  if (active) {
+    for (int i = n0; i < nend; ++i) {
+      V x[6];
+      ld6(x, W, i, KT, kt);
+      if (EIN) {
+        const V tr = cadd(cadd(x[0], x[1]), x[2]);
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) x[cc] = cscale(x[cc], (T)2 * mu);
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) x[cc] = caxpy(x[cc], lam, tr);
+      }
+      if (!special) rotate_in(x, g.c, g.s);
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) W[(i * 6 + cc) * KT + kt] = x[cc];
+    }
+  }
+  __syncthreads();
+
+  Elem<T> ec;
+  if (uniform) ec = elem_coef<T>(g.q, hz);
+
+  // 3. chunk summaries from zero; the + branch of every own node stays in registers
+  Mom<V> Ploc[C];
+  if (active && !special) {
+    Mom<V> A;
+    mom_zero(A);
+    V wa[6];
+    ld6(wa, W, n0, KT, kt);
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+      const int e = n0 + l;
+      if (e < e1) {
+        if (!uniform) ec = elem_coef<T>(g.q, zs[e + 1] - zs[e]);
+        V wb[6];
+        ld6(wb, W, e + 1, KT, kt);
+        stepA(A, ec, wa, wb);
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) wa[cc] = wb[cc];
+      }
+    }
+    SA[ch * KT + kt] = A;
+    Mom<V> P;
+    mom_zero(P);
+    V wb[6];
+    ld6(wb, W, e1, KT, kt);
+#pragma unroll
+    for (int l = C - 1; l >= 0; --l) {
+      const int e = n0 + l;
+      if (e < e1) {
+        if (!uniform) ec = elem_coef<T>(g.q, zs[e + 1] - zs[e]);
+        V wc[6];
+        ld6(wc, W, e, KT, kt);
+        stepP(P, ec, wc, wb);
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) wb[cc] = wc[cc];
+        Ploc[l] = P;
+      } else {
+        mom_zero(Ploc[l]);
+      }
+    }
+    SP[ch * KT + kt] = P;
+  }
+  __syncthreads();
+
+  // 4. carries: exclusive scans over the chunk summaries, in place (thread ch 0: the -
+  //    branch downwards; thread ch 1: the + branch upwards and the full + branch at x3 = 0)
+  if (active && !special) {
+    const int pch = nch > 1 ? 1 : 0;
+    if (ch == 0) {
+      Mom<V> run;
+      mom_zero(run);
+      for (int j = 0; j < nch; ++j) {
+        const int a0 = j * C, a1 = min(j * C + C, nz - 1);
+        const Mom<V> sj = SA[j * KT + kt];
+        SA[j * KT + kt] = run;
+        propA(run, g.q * (zs[a1] - zs[a0]));
+        mom_add(run, sj);
+      }
+    }
+    if (ch == pch) {
+      Mom<V> run;
+      mom_zero(run);
+      for (int j = nch - 1; j >= 0; --j) {
+        const int a0 = j * C, a1 = min(j * C + C, nz - 1);
+        const Mom<V> sj = SP[j * KT + kt];
+        SP[j * KT + kt] = run;
+        propP(run, g.q * (zs[a1] - zs[a0]));
+        mom_add(run, sj);
+      }
+      P0s[kt] = run;
+    }
+  }
+  __syncthreads();
+
+  if (!active) return;
+  if (special) {
+    if (want_u3 && ch == 0) surf[(size_t)k2 * h1 + k1] = mk<V>(0, 0);
+    for (int i = n0; i < nend; ++i) {
+      V w[6], o[6];
+      ld6(w, W, i, KT, kt);
+      if (g.nyq) {
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) o[cc] = out_kind == FVIM_STRAIN ? mk<V>(0, 0) : cscale(w[cc], (T)-1);
+      } else {
+        // laminate: eps_33 = w_33/(lam+2mu), eps_a3 = w_a3/(2mu), eps_ab = 0
+        V e[6];
+        e[0] = e[1] = e[5] = mk<V>(0, 0);
+        e[2] = cscale(w[2], (T)1 / (lam + (T)2 * mu));
+        e[3] = cscale(w[3], (T)1 / ((T)2 * mu));
+        e[4] = cscale(w[4], (T)1 / ((T)2 * mu));
+        if (out_kind == FVIM_STRAIN) {
+#pragma unroll
+          for (int cc = 0; cc < 6; ++cc) o[cc] = e[cc];
+        } else {
+          const V trc = e[2];
+#pragma unroll
+          for (int cc = 0; cc < 6; ++cc) o[cc] = csub(cscale(e[cc], (T)2 * mu), w[cc]);
+          o[0] = caxpy(o[0], lam, trc);
+          o[1] = caxpy(o[1], lam, trc);
+          o[2] = caxpy(o[2], lam, trc);
+        }
+      }
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) spec[(size_t)(i * 6 + cc) * plane + (size_t)k2 * h1 + k1] = o[cc];
+    }
+    return;
+  }
+
+  // surface traction of the full-space field (A = 0 at x3 = 0), cancelled by the image
+  const Mom<V> P0 = P0s[kt];
+  V tr[3];
+  {
+    V w0[6];
+    ld6(w0, W, 0, KT, kt);
+    Mom<V> Z;
+    mom_zero(Z);
+    V e0[6];
+    kelvin_strain<T, V>(Z, P0, w0, g.q, nu, mu, e0);
+    const V trc = cadd(e0[0], e0[2]);
+    tr[0] = csub(cscale(e0[4], (T)2 * mu), w0[4]);
+    tr[1] = csub(cscale(e0[3], (T)2 * mu), w0[3]);
+    tr[2] = csub(caxpy(cscale(trc, lam), (T)2 * mu, e0[2]), w0[2]);
+    if (want_u3 && ch == 0) {
+      // u3(0) = N_inf[w].e3 + B^T(q, 0) t . e3 (rotated frame)
+      const T K = (T)1 / ((T)8 * mu * (nu - (T)1));
+      V u = caxpy(cmuli(P0.m[3]), (T)1, P0.m[1]);  // P_33 + i P_q3
+      u = cadd(cscale(u, (T)2 - (T)4 * nu), P0.n);
+      u = cscale(u, K);
+      V ub = cscale(cmuli(tr[0]), (T)0.5 * ((T)2 * nu - (T)1));
+      ub = caxpy(ub, -(nu - (T)1), tr[2]);
+      u = caxpy(u, (T)1 / (g.q * mu), ub);
+      surf[(size_t)k2 * h1 + k1] = u;
+    }
+  }
+
+  // 5. forward over the chunk: - branch from its carry, + branch = own part + propagated
+  //    carry, image term, epilogue, rotate back, store
+  Mom<V> A = SA[ch * KT + kt];
+  const Mom<V> Pin = SP[ch * KT + kt];
+  const T imu = (T)1 / mu;
+  T ex = dexp<T>(-g.q * zs[n0]);
+  V w[6];
+  ld6(w, W, n0, KT, kt);
+#pragma unroll
+  for (int l = 0; l < C; ++l) {
+    const int i = n0 + l;
+    if (i < nend) {
+      Mom<V> P = Pin;
+      propP(P, g.q * (zs[e1] - zs[i]));
+      mom_add(P, Ploc[l]);
+      V e[6];
+      kelvin_strain<T, V>(A, P, w, g.q, nu, mu, e);
+      if (!uniform && l > 0) ex = dexp<T>(-g.q * zs[i]);
+      bous_strain_add<T, V>(tr, g.q * zs[i], ex, nu, imu, e);
+      if (uniform) ex *= ec.E;
+      V o[6];
+      if (out_kind == FVIM_STRAIN) {
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) o[cc] = e[cc];
+      } else {
+        const V trc = cadd(e[0], e[2]);
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) o[cc] = csub(cscale(e[cc], (T)2 * mu), w[cc]);
+        o[0] = caxpy(o[0], lam, trc);
+        o[1] = caxpy(o[1], lam, trc);
+        o[2] = caxpy(o[2], lam, trc);
+      }
+      rotate_out(o, g.c, g.s);
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) spec[(size_t)(i * 6 + cc) * plane + (size_t)k2 * h1 + k1] = o[cc];
+      if (i < e1) {
+        if (!uniform) ec = elem_coef<T>(g.q, zs[i + 1] - zs[i]);
+        V wj[6];
+        ld6(wj, W, i + 1, KT, kt);
+        stepA(A, ec, w, wj);
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) w[cc] = wj[cc];
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------------
 // Boussinesq operator of a normal pressure (Eq. B:fourier): one thread per mode, loop
 // over depth.  surf holds p_hat on entry and u3_hat = 2 p_hat / (E* q) on exit.
 // ----------------------------------------------------------------------------------
@@ -615,6 +867,26 @@ template <typename T> int launch_mindlin_depth(const fvim_ctx* c, int out_kind, 
   if (smem > 227 * 1024) return FVIM_ERR_UNSUPPORTED;
   dim3 grid(h1 / KT, n2);
   const T w1 = (T)(kTwoPi / c->L1), w2 = (T)(kTwoPi / c->L2);
+  // FP32, 16-column tiles, at most 8 nodes per chunk: the register variant (C rounded up
+  // to an instantiated chunk length; any C >= 2 is exact)
+  if constexpr (sizeof(T) == 4) if (KT == 16 && C <= 8) {
+    const int CR = C <= 2 ? 2 : (C <= 3 ? 3 : (C <= 4 ? 4 : (C <= 6 ? 6 : 8)));
+    const int nchr = (nz + CR - 1) / CR;
+    const size_t smr = (size_t)nz * 6 * 16 * sizeof(V) + (size_t)(2 * nchr + 1) * 16 * sizeof(Mom<V>) +
+                       (size_t)nz * sizeof(T);
+#define DEPTHR(CV, EI)                                                                                          \
+  if (CR == CV && eps_in == EI) {                                                                               \
+    cudaFuncSetAttribute(k_mindlin_depth_r<T, 16, CV, EI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr); \
+    k_mindlin_depth_r<T, 16, CV, EI><<<grid, 16 * nchr, smr, c->stream>>>(                                       \
+        (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, n2, h1, nchr, w1, w2, (T)c->lam, (T)c->mu, (T)c->nu,  \
+        out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz);                                                        \
+  }
+    DEPTHR(2, false) DEPTHR(3, false) DEPTHR(4, false) DEPTHR(6, false) DEPTHR(8, false)
+    DEPTHR(2, true) DEPTHR(3, true) DEPTHR(4, true) DEPTHR(6, true) DEPTHR(8, true)
+#undef DEPTHR
+    FVIM_CUDA_CHECK_LAUNCH();
+    return FVIM_OK;
+  }
 #define DEPTH(KTV, EI)                                                                                         \
   if (KT == KTV && eps_in == EI) {                                                                             \
     cudaFuncSetAttribute(k_mindlin_depth<T, KTV, EI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
