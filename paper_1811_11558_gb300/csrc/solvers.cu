@@ -323,36 +323,86 @@ template <typename T> __global__ void k_count_pos(const T* __restrict__ a, size_
 }
 
 // ---- DF-SANE kernels (volume [Nz][6][N2][N1], weighted L2 product) ------------------
-__device__ __forceinline__ double vol_weight(const double* wz, size_t i, size_t nxy) {
-  const size_t zc = i / nxy;
-  const int c = (int)(zc % 6);
-  return wz[zc / 6] * (c < 3 ? 1.0 : 2.0);
+// Plane zc = (z, c) of the volume has the trapezoid weight dA w_z, doubled for the three
+// shear components.  N1 N2 is a power of two, so the plane of an index is a shift.  FP32
+// vectors are processed four values at a time: the four products are summed in FP32 and
+// the partial is accumulated in FP64 (one FP64 multiply-add per four values); FP64
+// vectors keep every operation in FP64.
+__device__ __forceinline__ double plane_weight(const double* wz, unsigned zc) {
+  return wz[zc / 6] * ((zc % 6) < 3 ? 1.0 : 2.0);
 }
+
 // F = x - b - tmp ; <F, F>
 template <typename T>
 __global__ void k_df_res(const T* __restrict__ x, const T* __restrict__ b, const T* __restrict__ tmp,
-                         T* __restrict__ F, const double* __restrict__ wz, size_t nxy, size_t n, double* part) {
+                         T* __restrict__ F, const double* __restrict__ wz, int lgxy, size_t n, double* part) {
   double v[1] = {0};
-  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
-    const T f = x[i] - b[i] - tmp[i];
-    F[i] = f;
-    v[0] += vol_weight(wz, i, nxy) * (double)f * (double)f;
+  if constexpr (sizeof(T) == 4) {
+    const size_t n4 = n >> 2;
+    const int lg4 = lgxy - 2;
+    for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n4; i += (size_t)gridDim.x * RT) {
+      const float4 a = reinterpret_cast<const float4*>(x)[i];
+      const float4 c = reinterpret_cast<const float4*>(b)[i];
+      const float4 d = reinterpret_cast<const float4*>(tmp)[i];
+      const float4 f = make_float4(a.x - c.x - d.x, a.y - c.y - d.y, a.z - c.z - d.z, a.w - c.w - d.w);
+      reinterpret_cast<float4*>(F)[i] = f;
+      const float q = f.x * f.x + f.y * f.y + f.z * f.z + f.w * f.w;
+      v[0] += plane_weight(wz, (unsigned)(i >> lg4)) * (double)q;
+    }
+  } else {
+    for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
+      const T f = x[i] - b[i] - tmp[i];
+      F[i] = f;
+      v[0] += plane_weight(wz, (unsigned)(i >> lgxy)) * (double)f * (double)f;
+    }
   }
   block_reduce<1>(v, part);
 }
 // <s, s> and <s, y> with s = xn - x, y = Fn - F
 template <typename T>
 __global__ void k_df_sy(const T* __restrict__ x, const T* __restrict__ xn, const T* __restrict__ F,
-                        const T* __restrict__ Fn, const double* __restrict__ wz, size_t nxy, size_t n, double* part) {
+                        const T* __restrict__ Fn, const double* __restrict__ wz, int lgxy, size_t n, double* part) {
   double v[2] = {0, 0};
-  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
-    const double w = vol_weight(wz, i, nxy);
-    const double s = (double)xn[i] - (double)x[i];
-    const double y = (double)Fn[i] - (double)F[i];
-    v[0] += w * s * s;
-    v[1] += w * s * y;
+  if constexpr (sizeof(T) == 4) {
+    const size_t n4 = n >> 2;
+    const int lg4 = lgxy - 2;
+    for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n4; i += (size_t)gridDim.x * RT) {
+      const float4 a = reinterpret_cast<const float4*>(x)[i];
+      const float4 an = reinterpret_cast<const float4*>(xn)[i];
+      const float4 f = reinterpret_cast<const float4*>(F)[i];
+      const float4 fn = reinterpret_cast<const float4*>(Fn)[i];
+      const float s0 = an.x - a.x, s1 = an.y - a.y, s2 = an.z - a.z, s3 = an.w - a.w;
+      const float y0 = fn.x - f.x, y1 = fn.y - f.y, y2 = fn.z - f.z, y3 = fn.w - f.w;
+      const double w = plane_weight(wz, (unsigned)(i >> lg4));
+      v[0] += w * (double)(s0 * s0 + s1 * s1 + s2 * s2 + s3 * s3);
+      v[1] += w * (double)(s0 * y0 + s1 * y1 + s2 * y2 + s3 * y3);
+    }
+  } else {
+    for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
+      const double w = plane_weight(wz, (unsigned)(i >> lgxy));
+      const double s = (double)xn[i] - (double)x[i];
+      const double y = (double)Fn[i] - (double)F[i];
+      v[0] += w * s * s;
+      v[1] += w * s * y;
+    }
   }
   block_reduce<2>(v, part);
+}
+// dst = a + s b over a volume vector (FP32: four values at a time, FP32 arithmetic)
+template <typename T>
+__global__ void k_axpby_vol(T* __restrict__ dst, const T* __restrict__ a, double s, const T* __restrict__ b,
+                            size_t n) {
+  if constexpr (sizeof(T) == 4) {
+    const float sf = (float)s;
+    for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < (n >> 2); i += (size_t)gridDim.x * RT) {
+      const float4 x = reinterpret_cast<const float4*>(a)[i];
+      const float4 y = reinterpret_cast<const float4*>(b)[i];
+      reinterpret_cast<float4*>(dst)[i] =
+          make_float4(fmaf(sf, y.x, x.x), fmaf(sf, y.y, x.y), fmaf(sf, y.z, x.z), fmaf(sf, y.w, x.w));
+    }
+  } else {
+    for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) dst[i] = a[i] + s * b[i];
+  }
 }
 
 template <typename T> int sum2(fvim_ctx* c, const T* a, size_t n, double* out) {
@@ -364,6 +414,11 @@ template <typename T> int sum2(fvim_ctx* c, const T* a, size_t n, double* out) {
 
 template <typename T> int axpby(fvim_ctx* c, T* dst, const T* a, double s, const T* b, size_t n) {
   k_axpby<T><<<rgrid(n), RT, 0, c->stream>>>(dst, a, s, b, n);
+  FVIM_CUDA_CHECK_LAUNCH();
+  return FVIM_OK;
+}
+template <typename T> int axpby_vol(fvim_ctx* c, T* dst, const T* a, double s, const T* b, size_t n) {
+  k_axpby_vol<T><<<rgrid(sizeof(T) == 4 ? n / 4 : n), RT, 0, c->stream>>>(dst, a, s, b, n);
   FVIM_CUDA_CHECK_LAUNCH();
   return FVIM_OK;
 }
@@ -611,6 +666,7 @@ template <typename T> struct DF {
   fvim_ctx* c;
   size_t n, nxy;
   int grd;
+  int lgxy;  // log2(N1 N2)
   // F(x) into Fx; returns ||F||^2 (weighted).  The launch sequence is one captured graph
   // per (x, Fx) pair.
   int eval(const T* x, T* Fx, double* f) {
@@ -618,7 +674,7 @@ template <typename T> struct DF {
       int r;
       if ((r = return_map_t<T>(c, x, S<T>(c, V_DEP), S<T>(c, V_EP)))) return r;
       if ((r = apply_mindlin_t<T>(c, S<T>(c, V_DEP), S<T>(c, V_TMP), FVIM_STRAIN, nullptr))) return r;
-      k_df_res<T><<<grd, RT, 0, c->stream>>>(x, S<T>(c, V_B), S<T>(c, V_TMP), Fx, (const double*)c->sv[V_WZ], nxy,
+      k_df_res<T><<<grd, RT, 0, c->stream>>>(x, S<T>(c, V_B), S<T>(c, V_TMP), Fx, (const double*)c->sv[V_WZ], lgxy,
                                             n, (double*)c->sv[V_PART]);
       FVIM_CUDA_CHECK_LAUNCH();
       return FVIM_OK;
@@ -636,7 +692,9 @@ template <typename T>
 int plasticity_t(fvim_ctx* c, const T* dT, T* dE, T* deps_p, T* dep, const fvim_opts* o, int* iters, double* res,
                  long* evals_out, bool warm = false) {
   const size_t nxy = (size_t)c->n1 * c->n2, n = nxy * c->nz * 6;
-  DF<T> df{c, n, nxy, rgrid(n)};
+  int lgxy = 0;
+  while (((size_t)1 << lgxy) < nxy) ++lgxy;
+  DF<T> df{c, n, nxy, rgrid(sizeof(T) == 4 ? n / 4 : n), lgxy};
   int rc;
   // elastic predictor b = grad^sym M[dT], start x0 = b
   if ((rc = apply_boussinesq_t<T>(c, dT, nullptr, S<T>(c, V_B), FVIM_STRAIN))) return rc;
@@ -682,11 +740,11 @@ int plasticity_t(fvim_ctx* c, const T* dT, T* dE, T* deps_p, T* dep, const fvim_
     for (int bt = 0; bt < 60 && !ok; ++bt) {
       double fp, fm;
       // x + ap d with d = -sigma F
-      if ((rc = axpby<T>(c, xt, x, -ap * sigma, F, n))) return rc;
+      if ((rc = axpby_vol<T>(c, xt, x, -ap * sigma, F, n))) return rc;
       if ((rc = df.eval(xt, Ft, &fp))) return rc;
       ++evals;
       if (fp <= fmax + eta - gamma * ap * ap * f) { fn = fp; ok = true; break; }
-      if ((rc = axpby<T>(c, xt, x, am * sigma, F, n))) return rc;
+      if ((rc = axpby_vol<T>(c, xt, x, am * sigma, F, n))) return rc;
       if ((rc = df.eval(xt, Ft, &fm))) return rc;
       ++evals;
       if (fm <= fmax + eta - gamma * am * am * f) { fn = fm; ok = true; break; }
@@ -695,7 +753,8 @@ int plasticity_t(fvim_ctx* c, const T* dT, T* dE, T* deps_p, T* dep, const fvim_
     }
     if (!ok) break;
     double sv[2];
-    k_df_sy<T><<<df.grd, RT, 0, c->stream>>>(x, xt, F, Ft, (const double*)c->sv[V_WZ], nxy, n, (double*)c->sv[V_PART]);
+    k_df_sy<T><<<df.grd, RT, 0, c->stream>>>(x, xt, F, Ft, (const double*)c->sv[V_WZ], df.lgxy, n,
+                                             (double*)c->sv[V_PART]);
     FVIM_CUDA_CHECK_LAUNCH();
     if ((rc = finish<2>(c, df.grd, sv))) return rc;
     sigma = sv[1] != 0 ? sv[0] / sv[1] : INFINITY;
