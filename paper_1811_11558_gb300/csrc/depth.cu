@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
 // the final pass adds the propagated carry (one propagation per node) instead of running
 // the + recursion again, and every pass reads each node of the tile once (the other node
 // of an element is carried in registers).
-// smem: W[nz][6][KT] + SA[nch][KT] + SP[nch][KT] + P0[KT] (moments) + zs[nz]
+// smem: W[nz][6][KT] + SA[nch][KT] + SP[nch][KT] (moments) + TR[KT][3] + zs[nz]
 // ----------------------------------------------------------------------------------
 template <typename V> __device__ __forceinline__ void ld6(V (&w)[6], const V* W, int node, int KT, int kt) {
 #pragma unroll
@@ -553,17 +553,18 @@ template <typename V> __device__ __forceinline__ void ld6(V (&w)[6], const V* W,
 
 template <typename T, int KT, int C, bool EIN>
 __global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* __restrict__ spec,
-                                                         typename Cx<T>::t* __restrict__ surf,
-                                                         const T* __restrict__ zn, int nz, int n2, int h1, int nch,
-                                                         T w1, T w2, T lam, T mu, T nu, int out_kind, int want_u3,
-                                                         int uniform, T hz) {
+                                                            typename Cx<T>::t* __restrict__ surf,
+                                                            const T* __restrict__ zn, int nz, int n2, int h1, int nch,
+                                                            T w1, T w2, T lam, T mu, T nu, int out_kind, int want_u3,
+                                                            int uniform, T hz) {
   typedef typename Cx<T>::t V;
+  static_assert(sizeof(V) == 8 && KT % 2 == 0, "FP32 tiles of an even width");
   extern __shared__ __align__(16) unsigned char smraw[];
   V* W = reinterpret_cast<V*>(smraw);                               // [nz][6][KT]
   Mom<V>* SA = reinterpret_cast<Mom<V>*>(W + (size_t)nz * 6 * KT);  // [nch][KT]
   Mom<V>* SP = SA + (size_t)nch * KT;                               // [nch][KT]
-  Mom<V>* P0s = SP + (size_t)nch * KT;                              // [KT]
-  T* zs = reinterpret_cast<T*>(P0s + KT);                           // [nz]
+  V* TR = reinterpret_cast<V*>(SP + (size_t)nch * KT);              // [KT][3] image traction
+  T* zs = reinterpret_cast<T*>(TR + 3 * KT);                        // [nz]
   const int kt = threadIdx.x & (KT - 1);
   const int ch = threadIdx.x / KT;
   const int k1 = blockIdx.x * KT + kt;
@@ -571,10 +572,10 @@ __global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* _
   const size_t plane = (size_t)n2 * h1;
   const size_t colofs = (size_t)k2 * h1 + blockIdx.x * KT;
 
-  // 1. load the tile and the depth nodes
-  for (int idx = threadIdx.x; idx < nz * 6 * KT; idx += blockDim.x) {
-    const int zc = idx / KT, j = idx & (KT - 1);
-    cp_async_cx(W + idx, spec + (size_t)zc * plane + colofs + j);
+  // 1. load the tile (16-byte copies, two FP32 complex values each) and the depth nodes
+  for (int idx = threadIdx.x; idx < nz * 6 * (KT / 2); idx += blockDim.x) {
+    const int zc = idx / (KT / 2), j = 2 * (idx % (KT / 2));
+    cp_async_16(W + zc * KT + j, spec + (size_t)zc * plane + colofs + j);
   }
   for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];
   cp_async_wait_all();
@@ -586,6 +587,7 @@ __global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* _
   const int nend = min(n0 + C, nz);
   const int e1 = min(n0 + C, nz - 1);  // elements [n0, e1)
   const bool active = n0 < nz;
+  const bool work = active && !special;
 
   // 2. (eps_p input: w = C:eps_p per mode) rotate own nodes into the (q, p, 3) frame
   if (active) {
@@ -609,11 +611,13 @@ __global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* _
   Elem<T> ec;
   if (uniform) ec = elem_coef<T>(g.q, hz);
 
-  // 3. chunk summaries from zero; the + branch of every own node stays in registers
+  // 3. chunk summaries from zero (- branch at the chunk's last node e1, + branch at its
+  //    first node n0); the + branch of every own node stays in registers
   Mom<V> Ploc[C];
-  if (active && !special) {
-    Mom<V> A;
-    mom_zero(A);
+  Mom<V> Ta, Up;
+  mom_zero(Ta);
+  mom_zero(Up);
+  if (work) {
     V wa[6];
     ld6(wa, W, n0, KT, kt);
 #pragma unroll
@@ -623,14 +627,11 @@ __global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* _
         if (!uniform) ec = elem_coef<T>(g.q, zs[e + 1] - zs[e]);
         V wb[6];
         ld6(wb, W, e + 1, KT, kt);
-        stepA(A, ec, wa, wb);
+        stepA(Ta, ec, wa, wb);
 #pragma unroll
         for (int cc = 0; cc < 6; ++cc) wa[cc] = wb[cc];
       }
     }
-    SA[ch * KT + kt] = A;
-    Mom<V> P;
-    mom_zero(P);
     V wb[6];
     ld6(wb, W, e1, KT, kt);
 #pragma unroll
@@ -640,51 +641,75 @@ __global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* _
         if (!uniform) ec = elem_coef<T>(g.q, zs[e + 1] - zs[e]);
         V wc[6];
         ld6(wc, W, e, KT, kt);
-        stepP(P, ec, wc, wb);
+        stepP(Up, ec, wc, wb);
 #pragma unroll
         for (int cc = 0; cc < 6; ++cc) wb[cc] = wc[cc];
-        Ploc[l] = P;
+        Ploc[l] = Up;
       } else {
         mom_zero(Ploc[l]);
       }
     }
-    SP[ch * KT + kt] = P;
   }
+
+  // 4. inclusive scans over the chunks, log2(nch) rounds with every chunk thread working:
+  //    - branch downwards, Ta_j = sum_{i<=j} propA(S_i, q (z[e1_j] - z[e1_i]));
+  //    + branch upwards,  Up_j = sum_{i>=j} propP(S_i, q (z[n0_i] - z[n0_j])).
+  //    Propagations compose (prop(prop(M, a), b) = prop(M, a + b)), so the rounds are exact.
+  const int e1c = e1;
+  for (int d = 1; d < nch; d <<= 1) {
+    SA[ch * KT + kt] = Ta;
+    SP[ch * KT + kt] = Up;
+    __syncthreads();
+    if (work && ch >= d) {
+      Mom<V> o = SA[(ch - d) * KT + kt];
+      const int e1o = min((ch - d) * C + C, nz - 1);
+      propA(o, g.q * (zs[e1c] - zs[e1o]));
+      mom_add(Ta, o);
+    }
+    if (work && ch + d < nch) {
+      Mom<V> o = SP[(ch + d) * KT + kt];
+      propP(o, g.q * (zs[(ch + d) * C] - zs[n0]));
+      mom_add(Up, o);
+    }
+    __syncthreads();
+  }
+  SA[ch * KT + kt] = Ta;
+  SP[ch * KT + kt] = Up;
   __syncthreads();
 
-  // 4. carries: exclusive scans over the chunk summaries, in place (thread ch 0: the -
-  //    branch downwards; thread ch 1: the + branch upwards and the full + branch at x3 = 0)
-  if (active && !special) {
-    const int pch = nch > 1 ? 1 : 0;
-    if (ch == 0) {
-      Mom<V> run;
-      mom_zero(run);
-      for (int j = 0; j < nch; ++j) {
-        const int a0 = j * C, a1 = min(j * C + C, nz - 1);
-        const Mom<V> sj = SA[j * KT + kt];
-        SA[j * KT + kt] = run;
-        propA(run, g.q * (zs[a1] - zs[a0]));
-        mom_add(run, sj);
-      }
-    }
-    if (ch == pch) {
-      Mom<V> run;
-      mom_zero(run);
-      for (int j = nch - 1; j >= 0; --j) {
-        const int a0 = j * C, a1 = min(j * C + C, nz - 1);
-        const Mom<V> sj = SP[j * KT + kt];
-        SP[j * KT + kt] = run;
-        propP(run, g.q * (zs[a1] - zs[a0]));
-        mom_add(run, sj);
-      }
-      P0s[kt] = run;
+  // surface traction of the full-space field (A = 0 at x3 = 0, + branch complete: the
+  // scan value of chunk 0), cancelled by the image; one thread per column
+  if (ch == 0 && work) {
+    V w0[6];
+    ld6(w0, W, 0, KT, kt);
+    Mom<V> Z;
+    mom_zero(Z);
+    V e0[6];
+    kelvin_strain<T, V>(Z, Up, w0, g.q, nu, mu, e0);
+    const V trc = cadd(e0[0], e0[2]);
+    const V t0 = csub(cscale(e0[4], (T)2 * mu), w0[4]);
+    const V t1 = csub(cscale(e0[3], (T)2 * mu), w0[3]);
+    const V t2 = csub(caxpy(cscale(trc, lam), (T)2 * mu, e0[2]), w0[2]);
+    TR[3 * kt] = t0;
+    TR[3 * kt + 1] = t1;
+    TR[3 * kt + 2] = t2;
+    if (want_u3) {
+      // u3(0) = N_inf[w].e3 + B^T(q, 0) t . e3 (rotated frame)
+      const T K = (T)1 / ((T)8 * mu * (nu - (T)1));
+      V u = caxpy(cmuli(Up.m[3]), (T)1, Up.m[1]);  // P_33 + i P_q3
+      u = cadd(cscale(u, (T)2 - (T)4 * nu), Up.n);
+      u = cscale(u, K);
+      V ub = cscale(cmuli(t0), (T)0.5 * ((T)2 * nu - (T)1));
+      ub = caxpy(ub, -(nu - (T)1), t2);
+      u = caxpy(u, (T)1 / (g.q * mu), ub);
+      surf[(size_t)k2 * h1 + k1] = u;
     }
   }
+  if (want_u3 && ch == 0 && special) surf[(size_t)k2 * h1 + k1] = mk<V>(0, 0);
   __syncthreads();
 
   if (!active) return;
   if (special) {
-    if (want_u3 && ch == 0) surf[(size_t)k2 * h1 + k1] = mk<V>(0, 0);
     for (int i = n0; i < nend; ++i) {
       V w[6], o[6];
       ld6(w, W, i, KT, kt);
@@ -716,37 +741,17 @@ __global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* _
     return;
   }
 
-  // surface traction of the full-space field (A = 0 at x3 = 0), cancelled by the image
-  const Mom<V> P0 = P0s[kt];
+  // 5. forward over the chunk: - branch from its carry (scan value of the chunk above),
+  //    + branch = own part + carry from below propagated up, image term, epilogue, rotate
+  //    back, store
+  Mom<V> A, Pin;
+  if (ch > 0) A = SA[(ch - 1) * KT + kt];
+  else mom_zero(A);
+  if (ch + 1 < nch) Pin = SP[(ch + 1) * KT + kt];
+  else mom_zero(Pin);
   V tr[3];
-  {
-    V w0[6];
-    ld6(w0, W, 0, KT, kt);
-    Mom<V> Z;
-    mom_zero(Z);
-    V e0[6];
-    kelvin_strain<T, V>(Z, P0, w0, g.q, nu, mu, e0);
-    const V trc = cadd(e0[0], e0[2]);
-    tr[0] = csub(cscale(e0[4], (T)2 * mu), w0[4]);
-    tr[1] = csub(cscale(e0[3], (T)2 * mu), w0[3]);
-    tr[2] = csub(caxpy(cscale(trc, lam), (T)2 * mu, e0[2]), w0[2]);
-    if (want_u3 && ch == 0) {
-      // u3(0) = N_inf[w].e3 + B^T(q, 0) t . e3 (rotated frame)
-      const T K = (T)1 / ((T)8 * mu * (nu - (T)1));
-      V u = caxpy(cmuli(P0.m[3]), (T)1, P0.m[1]);  // P_33 + i P_q3
-      u = cadd(cscale(u, (T)2 - (T)4 * nu), P0.n);
-      u = cscale(u, K);
-      V ub = cscale(cmuli(tr[0]), (T)0.5 * ((T)2 * nu - (T)1));
-      ub = caxpy(ub, -(nu - (T)1), tr[2]);
-      u = caxpy(u, (T)1 / (g.q * mu), ub);
-      surf[(size_t)k2 * h1 + k1] = u;
-    }
-  }
-
-  // 5. forward over the chunk: - branch from its carry, + branch = own part + propagated
-  //    carry, image term, epilogue, rotate back, store
-  Mom<V> A = SA[ch * KT + kt];
-  const Mom<V> Pin = SP[ch * KT + kt];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) tr[j] = TR[3 * kt + j];
   const T imu = (T)1 / mu;
   T ex = dexp<T>(-g.q * zs[n0]);
   V w[6];
@@ -872,8 +877,8 @@ template <typename T> int launch_mindlin_depth(const fvim_ctx* c, int out_kind, 
   if constexpr (sizeof(T) == 4) if (KT == 16 && C <= 8) {
     const int CR = C <= 2 ? 2 : (C <= 3 ? 3 : (C <= 4 ? 4 : (C <= 6 ? 6 : 8)));
     const int nchr = (nz + CR - 1) / CR;
-    const size_t smr = (size_t)nz * 6 * 16 * sizeof(V) + (size_t)(2 * nchr + 1) * 16 * sizeof(Mom<V>) +
-                       (size_t)nz * sizeof(T);
+    const size_t smr = (size_t)nz * 6 * 16 * sizeof(V) + (size_t)(2 * nchr) * 16 * sizeof(Mom<V>) +
+                       (size_t)3 * 16 * sizeof(V) + (size_t)nz * sizeof(T);
 #define DEPTHR(CV, EI)                                                                                          \
   if (CR == CV && eps_in == EI) {                                                                               \
     cudaFuncSetAttribute(k_mindlin_depth_r<T, 16, CV, EI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr); \
