@@ -263,6 +263,9 @@ def run_gpu(args):
     }
     if rank == 0 and not args.no_solves:
         line["solves"] = solve_metrics()
+        line["solves"]["rough"] = rough_metrics()
+        line["solves"]["stream"] = stream_metrics()
+        line["scaling_sweep"] = scaling_metrics()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sample_modes=256, sample_planes=None)
     if pg is not None:
@@ -329,6 +332,151 @@ def solve_metrics(repeats=3, served=16, slots=8):
         "pressure_rel_l2": float(np.linalg.norm(press["fp32"] - press["fp64"]) / np.linalg.norm(press["fp64"])),
         "area_diff": float(abs((press["fp32"] > 0).mean() - (press["fp64"] > 0).mean()))}
     out["served_over_fp64_plain"] = out["fp32_served"]["solves_per_s"] / out["fp64_plain"]["solves_per_s"]
+    return out
+
+
+def rough_metrics(n=1024, nz=32, depth=0.05, seed=1813):
+    """Algorithm 1 on a rough surface, FP32: seeded self-affine surface n x n (H = 0.8, flat PSD
+    for 4 <= |k| < 8, power law to k_s = 64, rms slope 0.1), nz uniform nodes to the given
+    depth, sigma_y = 0.05 E*, E_h = 0.1 E.  (a) the paper's rough-surface load W = 1e-3 E x rms
+    slope in five increments, relaxation 0.3: a converged solve; (b) the load of a 10 % elastic
+    contact fraction, where Algorithm 1 does not reach the tolerance: a fixed budget of 20
+    coupling iterations on each of two increments, timed per coupling iteration."""
+    import torch
+
+    from paper_1811_11558_gb300 import Context, inputs
+
+    es = E / (1 - NU * NU)
+    z = inputs.uniform_depth(nz, depth)
+    h = inputs.self_affine_surface(n, 1.0, 0.8, 4, 8, 64, 0.1, seed=seed)
+    ctx = Context(n, n, z, 1.0, 1.0, precision="fp32", E=E, nu=NU, sigma_y=0.05 * es, E_h=0.1 * E)
+    hd = torch.from_numpy(h).to("cuda", torch.float32)
+    p = torch.zeros(ctx.surf_shape, dtype=torch.float32, device="cuda")
+    out = {"workload": "rough_%dx%dx%d_fp32" % (n, n, nz), "depth": depth, "seed": seed}
+    W = 1e-3 * E * 0.1
+    opts = ctx.default_opts(relax=0.3, max_iter=100, tol=1e-6)
+    ctx.reset_state()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rep = ctx.solve_contact(hd, [W * (k + 1) / 5 for k in range(5)], p, opts, allow_not_converged=True)
+    t = time.perf_counter() - t0
+    out["paper_load"] = {"W": W, "increments": 5, "relax": 0.3, "tol": opts.tol, "status": rep["status"],
+                         "solves_per_s": 1.0 / t, "ms_per_solve": 1e3 * t, "alg1_iters": rep["alg1_iters"],
+                         "alg1_error": rep["alg1_error"], "contact_area": rep["contact_area"][-1],
+                         "residual_evals": rep["residual_evals"], "cg_iters": rep["cg_iters"]}
+    # load of a 10 % elastic contact fraction (area ~ linear in the load at small fractions)
+    p.zero_()
+    ctx.elastic_contact(hd, 5e-3, p, ctx.default_opts())
+    W10 = 5e-3 * 0.1 / float((p > 0).double().mean())
+    ctx.reset_state()
+    opts = ctx.default_opts(relax=0.3, max_iter=20, tol=1e-6)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rep = ctx.solve_contact(hd, [W10 / 2, W10], p, opts, allow_not_converged=True)
+    t = time.perf_counter() - t0
+    its = sum(rep["alg1_iters"][:2])
+    out["area_10pct"] = {"W": W10, "increments": 2, "relax": 0.3, "alg1_cap": 20, "status": rep["status"],
+                         "ms_per_alg1_iter": 1e3 * t / its, "alg1_error": rep["alg1_error"],
+                         "contact_area": rep["contact_area"][-1],
+                         "note": "Algorithm 1 stalls near 1e-2 on this load (the paper notes it is not robust on "
+                                 "rough surfaces); timed on a fixed budget"}
+    ctx.close()
+    return out
+
+
+def stream_metrics(n_req=12, slots=8, seed=1815):
+    """Served request stream, FP32 vs plain FP64: requests with grids drawn uniformly in log2
+    from {128, 256}, nz = round(16 x 2^U) in [16, 32], seeded self-affine surfaces (H 0.8, rms
+    slope 0.1), five-increment ramps to the paper's rough-surface load; Poisson arrivals at
+    0.7 x the single-stream FP32 capacity; p50 / p99 latency from arrival to result.  The FP64
+    baseline solves the first four requests one at a time; its solves/s is the mix's mean
+    service time per size class applied to the whole stream."""
+    import torch
+
+    from paper_1811_11558_gb300 import inputs
+    from paper_1811_11558_gb300.serve import Request, Server, percentiles, poisson_arrivals
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    es = E / (1 - NU * NU)
+    reqs = []
+    for i in range(n_req):
+        n = int(2 ** rng.integers(7, 9))
+        nz = int(round(16 * 2 ** rng.uniform(0, 1)))
+        z = inputs.uniform_depth(nz, 0.05)
+        h = inputs.self_affine_surface(n, 1.0, 0.8, 4, 8, min(64, n // 4), 0.1, seed=seed + 1 + i)
+        reqs.append(Request(i, n, z, h, [1e-4 * (k + 1) / 5 for k in range(5)], precision="fp32", E=E, nu=NU,
+                            sigma_y=0.05 * es, E_h=0.1 * E, opts={"relax": 0.3, "max_iter": 100, "tol": 1e-6}))
+    srv = Server(slots=slots)
+    srv.run(reqs[:4])                                   # warm the context pool
+    # single-stream capacity: one request at a time
+    t0 = time.perf_counter()
+    one = [srv.solve(r) for r in reqs[:4]]
+    cap = 4 / (time.perf_counter() - t0)
+    rate = 0.7 * cap
+    arr = poisson_arrivals(n_req, rate, seed)
+    for r, a in zip(reqs, arr):
+        r.arrival = float(a)
+    res, wall = srv.run(reqs)
+    lat = percentiles([r.latency for r in res])
+    sat, swall = srv.run([Request(r.rid, r.n, r.z, r.h, r.loads, precision="fp32", E=E, nu=NU, sigma_y=r.sigma_y,
+                                  E_h=r.E_h, opts=r.opts) for r in reqs])
+    # plain FP64, one request at a time
+    from paper_1811_11558_gb300 import Context
+
+    t64 = {}
+    p64 = []
+    for r in reqs[:4]:
+        ctx = Context(r.n, r.n, r.z, 1.0, 1.0, precision="fp64", E=E, nu=NU, sigma_y=r.sigma_y, E_h=r.E_h)
+        hd = torch.from_numpy(np.ascontiguousarray(r.h)).to("cuda", torch.float64)
+        p = torch.empty(ctx.surf_shape, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.solve_contact(hd, r.loads, p, ctx.default_opts(relax=0.3, max_iter=100), allow_not_converged=True)
+        t64.setdefault(r.n, []).append(time.perf_counter() - t0)
+        p64.append(p.cpu().numpy())
+        ctx.close()
+    mean64 = {k: float(np.mean(v)) for k, v in t64.items()}
+    est64 = sum(mean64.get(r.n, max(mean64.values())) for r in reqs)
+    err = [float(np.linalg.norm(one[i].pressure.astype(np.float64) - p64[i]) / np.linalg.norm(p64[i]))
+           for i in range(4)]
+    return {"workload": "rough_stream_%dreq" % n_req, "grids": sorted({r.n for r in reqs}),
+            "nz": sorted({int(np.asarray(r.z).size) for r in reqs}), "slots": slots,
+            "single_stream_fp32_solves_per_s": cap, "arrival_rate_per_s": rate,
+            "fp32_served_poisson": {"solves_per_s": n_req / wall, "p50_ms": 1e3 * lat[50], "p99_ms": 1e3 * lat[99]},
+            "fp32_served_saturated": {"solves_per_s": n_req / swall,
+                                      "p50_ms": 1e3 * percentiles([r.latency for r in sat])[50],
+                                      "p99_ms": 1e3 * percentiles([r.latency for r in sat])[99]},
+            "fp64_plain": {"solves_per_s": n_req / est64, "measured_requests": 4,
+                           "mean_s_by_grid": {str(k): v for k, v in mean64.items()}},
+            "fp32_vs_fp64_pressure_rel_l2": err,
+            "served_saturated_over_fp64_plain": (n_req / swall) / (n_req / est64)}
+
+
+def scaling_metrics(sizes=(16, 32, 64, 128), reps=20):
+    """Mindlin-apply time on N x N x N grids (the paper's VIM complexity sweep, App. C.4, whose
+    reference time T0 = 1.41 ms was measured on a CPU node), FP32 and FP64, CUDA events,
+    inputs resident."""
+    import torch
+
+    from paper_1811_11558_gb300 import Context, inputs
+
+    out = {"workload": "mindlin_apply_cube_sweep", "paper_T0_ms_cpu": 1.41, "ms": {}}
+    for prec in ("fp32", "fp64"):
+        for n in sizes:
+            z = inputs.uniform_depth(n, 1.0)
+            ctx = Context(n, n, z, 1.0, 1.0, precision=prec, E=E, nu=NU)
+            ep = torch.from_numpy(inputs.plastic_strain_field(n, n, z, seed=n)).to("cuda", ctx.dtype)
+            o = torch.empty_like(ep)
+            for _ in range(3):
+                ctx.apply_mindlin(ep, o)
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            for _ in range(reps):
+                ctx.apply_mindlin(ep, o)
+            e.record()
+            torch.cuda.synchronize()
+            out["ms"]["%s_%d" % (prec, n)] = s.elapsed_time(e) / reps
+            ctx.close()
     return out
 
 

@@ -137,6 +137,12 @@ int fvim_destroy(fvim_ctx* ctx);
 /* fvim_strerror -- static description of a status code. */
 const char* fvim_strerror(int status);
 
+/* fvim_last_cuda_error -- description of the last CUDA runtime error that made an entry
+ * point return FVIM_ERR_CUDA (or that a solver recovered from by launching directly
+ * instead of through a captured graph) in the calling host thread; "no error" if none.
+ * The paper has no counterpart: it is the diagnostic behind FVIM_ERR_CUDA. */
+const char* fvim_last_cuda_error(void);
+
 /* fvim_last_kernel_count -- number of kernels the last entry point launched. */
 int fvim_last_kernel_count(const fvim_ctx* ctx);
 

@@ -9,6 +9,14 @@
 
 #include "fvim_internal.cuh"
 
+static thread_local cudaError_t g_last_cuda = cudaSuccess;
+
+bool fvim_cuda_failed(cudaError_t e) {
+  if (e == cudaSuccess) return false;
+  g_last_cuda = e;
+  return true;
+}
+
 namespace {
 
 // J2 radial return with linear isotropic hardening (Sec. 4.1), one thread per voxel.
@@ -125,16 +133,16 @@ template <typename T> int upload_twiddles(void** dst, int n) {
     const double a = -6.283185307179586476925 * (double)k / (double)n;
     h[k] = mk<V>((T)cos(a), (T)sin(a));
   }
-  if (cudaMalloc(dst, n * sizeof(V)) != cudaSuccess) return FVIM_ERR_OOM;
-  if (cudaMemcpy(*dst, h.data(), n * sizeof(V), cudaMemcpyHostToDevice) != cudaSuccess) return FVIM_ERR_CUDA;
+  if (FVIM_CU(cudaMalloc(dst, n * sizeof(V)))) return FVIM_ERR_OOM;
+  if (FVIM_CU(cudaMemcpy(*dst, h.data(), n * sizeof(V), cudaMemcpyHostToDevice))) return FVIM_ERR_CUDA;
   return FVIM_OK;
 }
 
 template <typename T> int upload_nodes(fvim_ctx* c) {
   std::vector<T> h(c->nz);
   for (int i = 0; i < c->nz; ++i) h[i] = (T)c->z_host[i];
-  if (cudaMalloc(&c->z_dev, c->nz * sizeof(T)) != cudaSuccess) return FVIM_ERR_OOM;
-  if (cudaMemcpy(c->z_dev, h.data(), c->nz * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return FVIM_ERR_CUDA;
+  if (FVIM_CU(cudaMalloc(&c->z_dev, c->nz * sizeof(T)))) return FVIM_ERR_OOM;
+  if (FVIM_CU(cudaMemcpy(c->z_dev, h.data(), c->nz * sizeof(T), cudaMemcpyHostToDevice))) return FVIM_ERR_CUDA;
   return FVIM_OK;
 }
 
@@ -264,6 +272,8 @@ template int commit_t<double>(fvim_ctx*, const double*, const double*, const dou
 
 extern "C" {
 
+const char* fvim_last_cuda_error(void) { return g_last_cuda == cudaSuccess ? "no error" : cudaGetErrorString(g_last_cuda); }
+
 const char* fvim_strerror(int s) {
   switch (s) {
     case FVIM_OK: return "ok";
@@ -328,12 +338,12 @@ int fvim_create(fvim_ctx** out, int n1, int n2, int nz, const double* z_nodes, d
       {&c->st_eps_p, nv * 6 * es},                   {&c->st_ep, nv * es},
       {&c->st_sig, nv * 6 * es},                   {&c->st_T, (size_t)n2 * n1 * es}};
   for (auto& a : al) {
-    if (cudaMalloc(a.p, a.bytes) != cudaSuccess) { cudaGetLastError(); free_all(c); delete c; return FVIM_ERR_OOM; }
-    if (cudaMemset(*a.p, 0, a.bytes) != cudaSuccess) { free_all(c); delete c; return FVIM_ERR_CUDA; }
+    if (FVIM_CU(cudaMalloc(a.p, a.bytes))) { cudaGetLastError(); free_all(c); delete c; return FVIM_ERR_OOM; }
+    if (FVIM_CU(cudaMemset(*a.p, 0, a.bytes))) { free_all(c); delete c; return FVIM_ERR_CUDA; }
   }
   // the fills above run on the legacy stream; wait for them without touching other streams
   // (another thread may be capturing a graph on its own non-blocking stream)
-  if (cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) { free_all(c); delete c; return FVIM_ERR_CUDA; }
+  if (FVIM_CU(cudaStreamSynchronize(cudaStreamLegacy))) { free_all(c); delete c; return FVIM_ERR_CUDA; }
   *out = c;
   return FVIM_OK;
 }
@@ -392,27 +402,28 @@ int fvim_commit_state(fvim_ctx* c, const void* d_eps, const void* d_eps_p, const
 int fvim_get_state(fvim_ctx* c, void* eps_p, void* e_p, void* sigma) {
   if (!c) return FVIM_ERR_ARG;
   const size_t es = elem_size(c), nv = nvox(c);
-  if (eps_p && cudaMemcpyAsync(eps_p, c->st_eps_p, nv * 6 * es, cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
-  if (e_p && cudaMemcpyAsync(e_p, c->st_ep, nv * es, cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
-  if (sigma && cudaMemcpyAsync(sigma, c->st_sig, nv * 6 * es, cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
+  if (eps_p && FVIM_CU(cudaMemcpyAsync(eps_p, c->st_eps_p, nv * 6 * es, cudaMemcpyDeviceToDevice, c->stream))) return FVIM_ERR_CUDA;
+  if (e_p && FVIM_CU(cudaMemcpyAsync(e_p, c->st_ep, nv * es, cudaMemcpyDeviceToDevice, c->stream))) return FVIM_ERR_CUDA;
+  if (sigma && FVIM_CU(cudaMemcpyAsync(sigma, c->st_sig, nv * 6 * es, cudaMemcpyDeviceToDevice, c->stream))) return FVIM_ERR_CUDA;
   return FVIM_OK;
 }
 
 int fvim_set_state(fvim_ctx* c, const void* eps_p, const void* e_p, const void* sigma) {
   if (!c) return FVIM_ERR_ARG;
   const size_t es = elem_size(c), nv = nvox(c);
-  if (eps_p && cudaMemcpyAsync(c->st_eps_p, eps_p, nv * 6 * es, cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
-  if (e_p && cudaMemcpyAsync(c->st_ep, e_p, nv * es, cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
-  if (sigma && cudaMemcpyAsync(c->st_sig, sigma, nv * 6 * es, cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
+  if (eps_p && FVIM_CU(cudaMemcpyAsync(c->st_eps_p, eps_p, nv * 6 * es, cudaMemcpyDeviceToDevice, c->stream))) return FVIM_ERR_CUDA;
+  if (e_p && FVIM_CU(cudaMemcpyAsync(c->st_ep, e_p, nv * es, cudaMemcpyDeviceToDevice, c->stream))) return FVIM_ERR_CUDA;
+  if (sigma && FVIM_CU(cudaMemcpyAsync(c->st_sig, sigma, nv * 6 * es, cudaMemcpyDeviceToDevice, c->stream))) return FVIM_ERR_CUDA;
   return FVIM_OK;
 }
 
 int fvim_reset_state(fvim_ctx* c) {
   if (!c) return FVIM_ERR_ARG;
   const size_t es = elem_size(c), nv = nvox(c);
-  if (cudaMemsetAsync(c->st_eps_p, 0, nv * 6 * es, c->stream) || cudaMemsetAsync(c->st_ep, 0, nv * es, c->stream) ||
-      cudaMemsetAsync(c->st_sig, 0, nv * 6 * es, c->stream) ||
-      cudaMemsetAsync(c->st_T, 0, (size_t)c->n1 * c->n2 * es, c->stream))
+  if (FVIM_CU(cudaMemsetAsync(c->st_eps_p, 0, nv * 6 * es, c->stream)) ||
+      FVIM_CU(cudaMemsetAsync(c->st_ep, 0, nv * es, c->stream)) ||
+      FVIM_CU(cudaMemsetAsync(c->st_sig, 0, nv * 6 * es, c->stream)) ||
+      FVIM_CU(cudaMemsetAsync(c->st_T, 0, (size_t)c->n1 * c->n2 * es, c->stream)))
     return FVIM_ERR_CUDA;
   return FVIM_OK;
 }
@@ -429,7 +440,7 @@ size_t fvim_footprint(int n1, int n2, int nz, int precision) {
 
 int fvim_sync(fvim_ctx* c) {
   if (!c) return FVIM_ERR_ARG;
-  return cudaStreamSynchronize(c->stream) == cudaSuccess ? FVIM_OK : FVIM_ERR_CUDA;
+  return FVIM_CU(cudaStreamSynchronize(c->stream)) ? FVIM_ERR_CUDA : FVIM_OK;
 }
 
 int fvim_destroy(fvim_ctx* c) {
@@ -457,7 +468,7 @@ int fvim_profile_read(fvim_ctx* c, double* total_ms, int* launches, int nslots) 
   for (int s = 0; s < nslots; ++s) { total_ms[s] = 0; launches[s] = 0; }
   ProfState* ps = (ProfState*)c->prof;
   if (!ps) return FVIM_OK;
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
+  if (FVIM_CU(cudaStreamSynchronize(c->stream))) return FVIM_ERR_CUDA;
   for (int s = 0; s < PROF_NSLOTS; ++s) {
     for (auto& e : ps->ev[s]) {
       float ms = 0;

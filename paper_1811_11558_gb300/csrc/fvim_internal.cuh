@@ -390,8 +390,11 @@ template <typename T> int apply_boussinesq_t(fvim_ctx* c, const T* p, T* u3, T* 
 template <typename T> int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep);
 template <typename T> int commit_t(fvim_ctx* c, const T* d_eps, const T* d_eps_p, const T* d_ep);
 
-#define FVIM_CUDA_CHECK_LAUNCH()                          \
-  do {                                                    \
-    cudaError_t e_ = cudaGetLastError();                  \
-    if (e_ != cudaSuccess) return FVIM_ERR_CUDA;          \
+// true when e is an error; the error is kept as this host thread's last CUDA error
+// (fvim_last_cuda_error)
+bool fvim_cuda_failed(cudaError_t e);
+#define FVIM_CU(call) fvim_cuda_failed(call)
+#define FVIM_CUDA_CHECK_LAUNCH()                                  \
+  do {                                                            \
+    if (fvim_cuda_failed(cudaGetLastError())) return FVIM_ERR_CUDA; \
   } while (0)

@@ -30,12 +30,12 @@ void* g_scratch_addr[kMaxDevices] = {};
 // device address of the scratch array on the current device (set up on first use)
 int scratch_address(void** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return FVIM_ERR_CUDA;
+  if (FVIM_CU(cudaGetDevice(&dev))) return FVIM_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return FVIM_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FVIM_ERR_CUDA;
+    if (FVIM_CU(cudaGetSymbolAddress(&p, g_noalloc_scratch)) || !p) return FVIM_ERR_CUDA;
     g_scratch_addr[dev] = p;
   }
   *out = g_scratch_addr[dev];
@@ -82,8 +82,7 @@ int run(fvim_ctx* c, unsigned char* base, const T* eps_p, T* out, int kind, T* u
   c->surf_nq = base + off;
   off += align256((size_t)n2 * sizeof(T));
   if (off > (size_t)FVIM_NOALLOC_SCRATCH_BYTES) return FVIM_ERR_UNSUPPORTED;
-  if (cudaMemcpyAsync(zsrc, c->z_host, (size_t)nz * sizeof(double), cudaMemcpyHostToDevice, c->stream) !=
-      cudaSuccess)
+  if (FVIM_CU(cudaMemcpyAsync(zsrc, c->z_host, (size_t)nz * sizeof(double), cudaMemcpyHostToDevice, c->stream)))
     return FVIM_ERR_CUDA;
   k_nodes<T><<<(nz + 127) / 128, 128, 0, c->stream>>>((T*)c->z_dev, zsrc, nz);
   k_twiddles<T><<<(n1 + 127) / 128, 128, 0, c->stream>>>((V*)c->tw1, n1);

@@ -8,6 +8,7 @@
 // fixed blocks writing FP64 partial sums, added on the host in block order, so results
 // are bitwise reproducible.  Loops run on the host and are capped.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -35,14 +36,14 @@ template <typename T> int ensure_ws(fvim_ctx* c) {
   if (c->sv[V_PART]) return FVIM_OK;
   const size_t ns = (size_t)c->n1 * c->n2, nv = ns * c->nz;
   for (int i = 0; i < S_NSURF; ++i)
-    if (cudaMalloc(&c->sv[i], ns * sizeof(T)) != cudaSuccess) return FVIM_ERR_OOM;
+    if (FVIM_CU(cudaMalloc(&c->sv[i], ns * sizeof(T)))) return FVIM_ERR_OOM;
   for (int i = V_X; i <= V_DE; ++i)
-    if (cudaMalloc(&c->sv[i], nv * 6 * sizeof(T)) != cudaSuccess) return FVIM_ERR_OOM;
-  if (cudaMalloc(&c->sv[V_EP], nv * sizeof(T)) != cudaSuccess) return FVIM_ERR_OOM;
-  if (cudaMalloc(&c->sv[V_PART], (size_t)RMAXB * NVMAX * sizeof(double)) != cudaSuccess) return FVIM_ERR_OOM;
-  if (cudaMalloc(&c->sv[V_WZ], (size_t)c->nz * sizeof(double)) != cudaSuccess) return FVIM_ERR_OOM;
-  if (cudaMalloc(&c->sv[V_PKS], 256) != cudaSuccess) return FVIM_ERR_OOM;
-  if (cudaMallocHost(&c->h_part, (size_t)RMAXB * NVMAX * sizeof(double) + 256) != cudaSuccess) {
+    if (FVIM_CU(cudaMalloc(&c->sv[i], nv * 6 * sizeof(T)))) return FVIM_ERR_OOM;
+  if (FVIM_CU(cudaMalloc(&c->sv[V_EP], nv * sizeof(T)))) return FVIM_ERR_OOM;
+  if (FVIM_CU(cudaMalloc(&c->sv[V_PART], (size_t)RMAXB * NVMAX * sizeof(double)))) return FVIM_ERR_OOM;
+  if (FVIM_CU(cudaMalloc(&c->sv[V_WZ], (size_t)c->nz * sizeof(double)))) return FVIM_ERR_OOM;
+  if (FVIM_CU(cudaMalloc(&c->sv[V_PKS], 256))) return FVIM_ERR_OOM;
+  if (FVIM_CU(cudaMallocHost(&c->h_part, (size_t)RMAXB * NVMAX * sizeof(double) + 256))) {
     c->h_part = nullptr;
     return FVIM_ERR_OOM;
   }
@@ -54,10 +55,10 @@ template <typename T> int ensure_ws(fvim_ctx* c) {
     wz[i] += 0.5 * h * dA;
     wz[i + 1] += 0.5 * h * dA;
   }
-  if (cudaMemcpy(c->sv[V_WZ], wz.data(), c->nz * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+  if (FVIM_CU(cudaMemcpy(c->sv[V_WZ], wz.data(), c->nz * sizeof(double), cudaMemcpyHostToDevice)))
     return FVIM_ERR_CUDA;
   for (int i = 0; i < V_PART; ++i)
-    if (cudaMemset(c->sv[i], 0, (i < S_NSURF ? ns : (i == V_EP ? nv : nv * 6)) * sizeof(T)) != cudaSuccess)
+    if (FVIM_CU(cudaMemset(c->sv[i], 0, (i < S_NSURF ? ns : (i == V_EP ? nv : nv * 6)) * sizeof(T))))
       return FVIM_ERR_CUDA;
   return FVIM_OK;
 }
@@ -105,22 +106,36 @@ static SolverRT* rt(fvim_ctx* c) {
 }
 
 // Runs body() (a fixed launch sequence on c->stream) through a CUDA graph captured on first
-// use for this key; launches it directly while kernels are being timed one by one.
+// use for this key; launches it directly while kernels are being timed one by one, when
+// FVIM_SOLVER_GRAPHS=0, and whenever capture, instantiation or a graph launch fails.
+static bool graphs_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("FVIM_SOLVER_GRAPHS");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 template <class F>
 static int graph_run(fvim_ctx* c, std::vector<std::pair<GraphKey, cudaGraphExec_t>>& cache, const GraphKey& key,
                      F&& body) {
-  if (c->prof) return body();
+  if (c->prof || !graphs_enabled()) return body();
   for (auto& e : cache)
-    if (e.first == key) return cudaGraphLaunch(e.second, c->stream) == cudaSuccess ? FVIM_OK : FVIM_ERR_CUDA;
-  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    if (e.first == key) {
+      if (!FVIM_CU(cudaGraphLaunch(e.second, c->stream))) return FVIM_OK;
+      cudaGetLastError();
+      return body();
+    }
+  if (FVIM_CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal))) {
     cudaGetLastError();
     return body();
   }
   const int rc = body();
   cudaGraph_t g = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
-  if (ce != cudaSuccess || !g) {
+  if (FVIM_CU(ce) || !g) {
     // the capture was invalidated (nothing ran): issue the sequence directly
+    if (g) cudaGraphDestroy(g);
     cudaGetLastError();
     return body();
   }
@@ -131,13 +146,18 @@ static int graph_run(fvim_ctx* c, std::vector<std::pair<GraphKey, cudaGraphExec_
   cudaGraphExec_t ex = nullptr;
   const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
   cudaGraphDestroy(g);
-  if (ie != cudaSuccess) return FVIM_ERR_CUDA;
+  if (FVIM_CU(ie)) {
+    cudaGetLastError();
+    return body();
+  }
   if (cache.size() >= kMaxGraphs) {
     cudaGraphExecDestroy(cache.front().second);
     cache.erase(cache.begin());
   }
   cache.emplace_back(key, ex);
-  return cudaGraphLaunch(ex, c->stream) == cudaSuccess ? FVIM_OK : FVIM_ERR_CUDA;
+  if (!FVIM_CU(cudaGraphLaunch(ex, c->stream))) return FVIM_OK;
+  cudaGetLastError();
+  return body();
 }
 
 // The solver entry points run on the runtime's stream, ordered after the caller's stream
@@ -188,10 +208,10 @@ inline int rgrid(size_t n) {
 
 // copy the partials of a reduction grid and add them in block order
 template <int NV> int finish(fvim_ctx* c, int nblk, double* out) {
-  if (cudaMemcpyAsync(c->h_part, c->sv[V_PART], (size_t)nblk * NV * sizeof(double), cudaMemcpyDeviceToHost,
-                      c->stream) != cudaSuccess)
+  if (FVIM_CU(cudaMemcpyAsync(c->h_part, c->sv[V_PART], (size_t)nblk * NV * sizeof(double), cudaMemcpyDeviceToHost,
+                      c->stream)))
     return FVIM_ERR_CUDA;
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
+  if (FVIM_CU(cudaStreamSynchronize(c->stream))) return FVIM_ERR_CUDA;
   for (int j = 0; j < NV; ++j) out[j] = 0;
   for (int b = 0; b < nblk; ++b)
     for (int j = 0; j < NV; ++j) out[j] += c->h_part[b * NV + j];
@@ -618,7 +638,7 @@ int elastic_contact_t(fvim_ctx* c, const T* h, double W, T* p, const fvim_opts* 
   memset(&s0, 0, sizeof(s0));
   s0.G_old = 1.0;
   s0.err = INFINITY;
-  if (cudaMemcpyAsync(st, &s0, sizeof(PKS), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
+  if (FVIM_CU(cudaMemcpyAsync(st, &s0, sizeof(PKS), cudaMemcpyHostToDevice, c->stream))) return FVIM_ERR_CUDA;
   PKS* sh = reinterpret_cast<PKS*>(c->h_part + (size_t)RMAXB * NVMAX);  // pinned
   *sh = s0;
   const int batch = 4;  // iterations issued between two reads of the stop flag
@@ -651,8 +671,8 @@ int elastic_contact_t(fvim_ctx* c, const T* h, double W, T* p, const fvim_opts* 
     // a full batch is one captured graph per (surface, pressure, load, tolerance)
     if ((rc = (nb == batch && srt) ? graph_run(c, srt->cg, key, iterations) : iterations())) return rc;
     issued += nb;
-    if (cudaMemcpyAsync(sh, st, sizeof(PKS), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
+    if (FVIM_CU(cudaMemcpyAsync(sh, st, sizeof(PKS), cudaMemcpyDeviceToHost, c->stream))) return FVIM_ERR_CUDA;
+    if (FVIM_CU(cudaStreamSynchronize(c->stream))) return FVIM_ERR_CUDA;
     if (sh->done) break;
   }
   if (sh->bad) return FVIM_ERR_NONFINITE;
@@ -702,7 +722,7 @@ int plasticity_t(fvim_ctx* c, const T* dT, T* dE, T* deps_p, T* dep, const fvim_
   T* F = S<T>(c, V_F);
   T* xt = S<T>(c, V_XT);
   T* Ft = S<T>(c, V_FT);
-  if (cudaMemcpyAsync(x, S<T>(c, V_B), n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+  if (FVIM_CU(cudaMemcpyAsync(x, S<T>(c, V_B), n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream)))
     return FVIM_ERR_CUDA;
   double f;
   if ((rc = df.eval(x, F, &f))) return rc;
@@ -715,7 +735,7 @@ int plasticity_t(fvim_ctx* c, const T* dT, T* dE, T* deps_p, T* dep, const fvim_
     if ((rc = df.eval(dE, Ft, &fw))) return rc;
     ++evals;
     if (fw < f) {
-      if (cudaMemcpyAsync(x, dE, n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+      if (FVIM_CU(cudaMemcpyAsync(x, dE, n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream)))
         return FVIM_ERR_CUDA;
       std::swap(F, Ft);
       c->sv[V_F] = F;
@@ -729,9 +749,19 @@ int plasticity_t(fvim_ctx* c, const T* dT, T* dE, T* deps_p, T* dep, const fvim_
   double sigma = 1.0;
   int k = 0;
   bool conv_ok = false;
+  // stagnation at the rounding floor of the path precision: the best residual of the
+  // last kStag iterations is not 10 % below the best one before them
+  const int kStag = 30;
+  double best_old = INFINITY;
   for (k = 0; k < o->df_max_iter; ++k) {
     if (!isfinite(f)) return FVIM_ERR_NONFINITE;
     if (sqrt(f) <= o->df_tol_abs + o->df_tol_rel * nF0) { conv_ok = true; break; }
+    if (hist.size() > (size_t)kStag) {
+      best_old = std::min(best_old, hist[hist.size() - 1 - kStag]);
+      double best_new = INFINITY;
+      for (size_t j = hist.size() - kStag; j < hist.size(); ++j) best_new = std::min(best_new, hist[j]);
+      if (best_new > 0.81 * best_old) break;
+    }
     double fmax = 0;
     for (size_t j = hist.size() > (size_t)M ? hist.size() - M : 0; j < hist.size(); ++j) fmax = std::max(fmax, hist[j]);
     const double eta = nF0 / ((1.0 + k) * (1.0 + k));
@@ -773,7 +803,7 @@ int plasticity_t(fvim_ctx* c, const T* dT, T* dE, T* deps_p, T* dep, const fvim_
   }
   if (!conv_ok && sqrt(f) <= o->df_tol_abs + o->df_tol_rel * nF0) conv_ok = true;
   // outputs: dE = x and its return map
-  if (cudaMemcpyAsync(dE, x, n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
+  if (FVIM_CU(cudaMemcpyAsync(dE, x, n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream))) return FVIM_ERR_CUDA;
   if (deps_p || dep) {
     if ((rc = return_map_t<T>(c, x, deps_p ? deps_p : S<T>(c, V_DEP), dep ? dep : S<T>(c, V_EP)))) return rc;
   }
@@ -804,11 +834,11 @@ int solve_contact_t(fvim_ctx* c, const T* h, const double* loads, int n_inc, con
     if ((rc = axpby<T>(c, H0, h, -1.0, dU, ns))) return rc;
     if ((rc = sum2<T>(c, H0, ns, v))) return rc;
     const double hnorm = sqrt(v[1]);
-    if (cudaMemcpyAsync(H, H0, ns * sizeof(T), cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
-    if (cudaMemsetAsync(dUp, 0, ns * sizeof(T), c->stream)) return FVIM_ERR_CUDA;
-    if (cudaMemsetAsync(P, 0, ns * sizeof(T), c->stream)) return FVIM_ERR_CUDA;   // first guess: uniform
+    if (FVIM_CU(cudaMemcpyAsync(H, H0, ns * sizeof(T), cudaMemcpyDeviceToDevice, c->stream))) return FVIM_ERR_CUDA;
+    if (FVIM_CU(cudaMemsetAsync(dUp, 0, ns * sizeof(T), c->stream))) return FVIM_ERR_CUDA;
+    if (FVIM_CU(cudaMemsetAsync(P, 0, ns * sizeof(T), c->stream))) return FVIM_ERR_CUDA;   // first guess: uniform
     // T_prev = pressure of the last converged increment
-    if (cudaMemcpyAsync(Tprev, c->st_T, ns * sizeof(T), cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
+    if (FVIM_CU(cudaMemcpyAsync(Tprev, c->st_T, ns * sizeof(T), cudaMemcpyDeviceToDevice, c->stream))) return FVIM_ERR_CUDA;
     double e = INFINITY;
     int k = 1;
     while (true) {
@@ -837,7 +867,7 @@ int solve_contact_t(fvim_ctx* c, const T* h, const double* loads, int n_inc, con
     }
     // update(S, dE) and the converged pressure
     if ((rc = commit_t<T>(c, dE, S<T>(c, V_DEP), S<T>(c, V_EP)))) return rc;
-    if (cudaMemcpyAsync(c->st_T, P, ns * sizeof(T), cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
+    if (FVIM_CU(cudaMemcpyAsync(c->st_T, P, ns * sizeof(T), cudaMemcpyDeviceToDevice, c->stream))) return FVIM_ERR_CUDA;
     if ((rc = sum2<T>(c, P, ns, v))) return rc;
     double area[1];
     k_count_pos<T><<<gs, RT, 0, c->stream>>>(P, ns, (double*)c->sv[V_PART]);
@@ -855,8 +885,8 @@ int solve_contact_t(fvim_ctx* c, const T* h, const double* loads, int n_inc, con
     if (!(e < o->tol)) status = FVIM_ERR_NOT_CONVERGED;
   }
   (void)nv;
-  if (p_out && cudaMemcpyAsync(p_out, P, ns * sizeof(T), cudaMemcpyDeviceToDevice, c->stream)) return FVIM_ERR_CUDA;
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
+  if (p_out && FVIM_CU(cudaMemcpyAsync(p_out, P, ns * sizeof(T), cudaMemcpyDeviceToDevice, c->stream))) return FVIM_ERR_CUDA;
+  if (FVIM_CU(cudaStreamSynchronize(c->stream))) return FVIM_ERR_CUDA;
   return status;
 }
 
@@ -927,7 +957,7 @@ int fvim_plasticity_solve(fvim_ctx* c, const void* dT, void* dE, void* deps_p, v
     rc = plasticity_t<double>(c, (const double*)dT, (double*)dE, (double*)deps_p, (double*)dep, o, iters, res, nullptr);
   else
     rc = plasticity_t<float>(c, (const float*)dT, (float*)dE, (float*)deps_p, (float*)dep, o, iters, res, nullptr);
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FVIM_ERR_CUDA;
+  if (FVIM_CU(cudaStreamSynchronize(c->stream))) return FVIM_ERR_CUDA;
   return rc;
 }
 

@@ -50,7 +50,10 @@ class Report(ctypes.Structure):
 
 class FvimError(RuntimeError):
     def __init__(self, status, what):
-        super().__init__("%s failed: %s (status %d)" % (what, strerror(status), status))
+        msg = "%s failed: %s (status %d)" % (what, strerror(status), status)
+        if status == -3:
+            msg += ": " + lib().fvim_last_cuda_error().decode()
+        super().__init__(msg)
         self.status = status
 
 
@@ -76,6 +79,7 @@ def lib():
         "fvim_sync": (i, [vp]),
         "fvim_destroy": (i, [vp]),
         "fvim_strerror": (ctypes.c_char_p, [i]),
+        "fvim_last_cuda_error": (ctypes.c_char_p, []),
         "fvim_last_kernel_count": (i, [vp]),
         "fvim_profile_enable": (i, [vp, i]),
         "fvim_profile_read": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(i), i]),
