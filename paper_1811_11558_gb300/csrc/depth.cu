@@ -862,23 +862,29 @@ __global__ void k_boussinesq(typename Cx<T>::t* __restrict__ spec, typename Cx<T
 template <typename T> int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps_in) {
   typedef typename Cx<T>::t V;
   const int nz = c->nz, h1 = c->h1, n2 = c->n2;
-  const int KT = h1 < KT_MAX ? h1 : KT_MAX;  // h1 is a power of two
   int C = (nz + 15) / 16;
   if (C < 2) C = 2;
   const int nch = (nz + C - 1) / C;
-  const int threads = KT * nch;
   const int prow = nz > 2 * nch + 1 ? nz : 2 * nch + 1;
-  const size_t smem = (size_t)nz * 6 * KT * sizeof(V) + (size_t)prow * KT * sizeof(Mom<V>) + (size_t)nz * sizeof(T);
+  // tile width: 16 k1 columns (128-byte rows in FP32), narrower where the depth column of
+  // the tile does not fit in shared memory (deep grids, FP64)
+  int KT = h1 < KT_MAX ? h1 : KT_MAX;  // h1 is a power of two
+  auto smem_of = [&](int kt) {
+    return (size_t)nz * 6 * kt * sizeof(V) + (size_t)prow * kt * sizeof(Mom<V>) + (size_t)nz * sizeof(T);
+  };
+  while (KT > 2 && smem_of(KT) > 227 * 1024) KT >>= 1;
+  const size_t smem = smem_of(KT);
   if (smem > 227 * 1024) return FVIM_ERR_UNSUPPORTED;
+  const int threads = KT * nch;
   dim3 grid(h1 / KT, n2);
   const T w1 = (T)(kTwoPi / c->L1), w2 = (T)(kTwoPi / c->L2);
   // FP32, 16-column tiles, at most 8 nodes per chunk: the register variant (C rounded up
   // to an instantiated chunk length; any C >= 2 is exact)
-  if constexpr (sizeof(T) == 4) if (KT == 16 && C <= 8) {
-    const int CR = C <= 2 ? 2 : (C <= 3 ? 3 : (C <= 4 ? 4 : (C <= 6 ? 6 : 8)));
-    const int nchr = (nz + CR - 1) / CR;
-    const size_t smr = (size_t)nz * 6 * 16 * sizeof(V) + (size_t)(2 * nchr) * 16 * sizeof(Mom<V>) +
-                       (size_t)3 * 16 * sizeof(V) + (size_t)nz * sizeof(T);
+  const int CR = C <= 2 ? 2 : (C <= 3 ? 3 : (C <= 4 ? 4 : (C <= 6 ? 6 : 8)));
+  const int nchr = (nz + CR - 1) / CR;
+  const size_t smr = (size_t)nz * 6 * 16 * sizeof(V) + (size_t)(2 * nchr) * 16 * sizeof(Mom<V>) +
+                     (size_t)3 * 16 * sizeof(V) + (size_t)nz * sizeof(T);
+  if constexpr (sizeof(T) == 4) if (KT == 16 && C <= 8 && smr <= 227 * 1024) {
 #define DEPTHR(CV, EI)                                                                                          \
   if (CR == CV && eps_in == EI) {                                                                               \
     cudaFuncSetAttribute(k_mindlin_depth_r<T, 16, CV, EI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr); \

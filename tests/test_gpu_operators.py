@@ -34,6 +34,9 @@ MINDLIN_CASES = [
     (64, 64, inputs.uniform_depth(16, 0.4), 1.0, 1.0, "fp32"),
     (128, 64, inputs.uniform_depth(33, 0.4), 1.0, 0.5, "fp32"),         # ragged depth chunks
     (256, 32, inputs.uniform_depth(64, 0.4), 1.0, 1.0, "fp32"),         # config-[1] depth, several tiles
+    # deep grids: the depth tile narrows to fit shared memory
+    (32, 16, inputs.uniform_depth(130, 0.3), 1.0, 1.0, "fp64"),
+    (32, 16, inputs.uniform_depth(300, 0.5), 1.0, 1.0, "fp32"),
     # plane sizes of the whole-plane cluster FFTs (FP32); depth steps keep q h within the
     # range where the oracle's element quadrature is exact
     (256, 256, inputs.uniform_depth(4, 0.06), 1.0, 1.0, "fp32"),
