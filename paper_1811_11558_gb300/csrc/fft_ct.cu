@@ -1,6 +1,8 @@
 // Compile-time-length variants of the register-resident in-plane FFT kernels (fft.cu has
 // the runtime-length ones).  Same data layouts, same arithmetic, same results up to the
 // order of operations inside the butterflies; chosen by the launchers for 16 <= N <= 1024.
+#include <algorithm>
+
 #include "fvim_internal.cuh"
 
 namespace {
@@ -46,6 +48,38 @@ __global__ void __launch_bounds__(512) k_cols_ct(typename Cx<T>::t* __restrict__
   fft_ct<V, INV, N, 1, 1>(v, t, sm, tw);
 #pragma unroll
   for (int m = 0; m < 8; ++m) col[(size_t)(t + m * T8) * h1] = v[0][m];
+}
+
+// FP32 column FFTs with 16-byte global accesses: a thread owns two adjacent columns (one
+// float4 per row holds both), so every load and store moves 16 bytes; 8 columns per CTA.
+// Interleaved exchange: entry p of column c at buf[p * 8 + c].
+struct ColPairSm {
+  float2* buf;
+  int f2;  // column pair
+  __device__ __forceinline__ void put(int g, int p, float2 x) const { buf[p * 8 + 2 * f2 + g] = x; }
+  __device__ __forceinline__ float2 get(int g, int p) const { return buf[p * 8 + 2 * f2 + g]; }
+};
+
+template <bool INV, int N>
+__global__ void __launch_bounds__(N / 2) k_cols_v(float2* __restrict__ planes, const float2* __restrict__ tw,
+                                                  int h1) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);  // [N][8]
+  constexpr int T8 = N / 8;
+  const int f2 = threadIdx.x & 3, t = threadIdx.x >> 2;
+  float4* col = reinterpret_cast<float4*>(planes + (size_t)blockIdx.y * N * h1 + (size_t)blockIdx.x * 8 + 2 * f2);
+  const size_t rs = (size_t)h1 / 2;  // row stride in float4
+  float2 v[2][8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const float4 a = col[(size_t)(t + m * T8) * rs];
+    v[0][m] = make_float2(a.x, a.y);
+    v[1][m] = make_float2(a.z, a.w);
+  }
+  ColPairSm x{sm, f2};
+  fft_ct<float2, INV, N, 2, 1>(v, t, x, tw);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) col[(size_t)(t + m * T8) * rs] = make_float4(v[0][m].x, v[0][m].y, v[1][m].x, v[1][m].y);
 }
 
 template <typename V>
@@ -149,6 +183,128 @@ __global__ void __launch_bounds__(256) k_rows_inv6_ct(const typename Cx<T>::t* _
     }
 }
 
+// FP32 row passes with 16-byte global accesses.  The CTA's rows are staged in shared memory
+// with 16-byte cp.async copies (forward: the six eps_p rows; inverse: the six half-spectrum
+// rows), read from there in the FFT's strided order, and the staging area then serves as the
+// FFT exchange area.  Results leave as float4: two spectrum entries (forward) or four real
+// values staged back through shared memory (inverse).
+template <int N>
+__global__ void __launch_bounds__(256) k_rows_fwd6_v(const float* __restrict__ eps_p, float2* __restrict__ spec,
+                                                     float* __restrict__ nq, const float2* __restrict__ tw, int n2,
+                                                     int rb, int z0, float lam, float mu) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int T8 = N / 8, LD = N + N / 8, H1 = N / 2;
+  const int r = threadIdx.x / T8, t = threadIdx.x % T8;
+  const int z = z0 + blockIdx.y;
+  const int x2b = blockIdx.x * rb, x2 = x2b + r;
+  float* stg = reinterpret_cast<float*>(smraw);  // [6][rb][N]
+  const int per_c = rb * N / 4;
+  for (int i = threadIdx.x; i < 6 * per_c; i += blockDim.x) {
+    const int c = i / per_c, j = i - c * per_c;
+    cp_async_16(stg + (size_t)c * rb * N + 4 * j, eps_p + (((size_t)z * 6 + c) * n2 + x2b) * N + 4 * j);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  float2 v[3][8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int x1 = t + m * T8;
+    float e[6], w[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) e[c] = stg[((size_t)c * rb + r) * N + x1];
+    hooke6_ct(e, w, lam, mu);
+    v[0][m] = make_float2(w[0], w[1]);
+    v[1][m] = make_float2(w[2], w[3]);
+    v[2][m] = make_float2(w[4], w[5]);
+  }
+  __syncthreads();  // staging is dead: the exchange area takes its place
+  RowSm<float2> sm{reinterpret_cast<float2*>(smraw) + (size_t)r * 3 * LD, LD};
+  fft_ct<float2, false, N, 3, 1>(v, t, sm, tw);
+#pragma unroll
+  for (int g = 0; g < 3; ++g)
+#pragma unroll
+    for (int m = 0; m < 8; ++m) sm.put(g, t + m * T8, v[g][m]);
+  __syncthreads();
+  for (int idx = t; idx < 3 * (H1 / 2); idx += T8) {
+    const int g = idx / (H1 / 2), k = 2 * (idx - g * (H1 / 2));
+    float2 A0, B0, A1, B1;
+    split_pair_ct(sm.get(g, k), sm.get(g, (N - k) & (N - 1)), A0, B0);
+    split_pair_ct(sm.get(g, k + 1), sm.get(g, N - k - 1), A1, B1);
+    float4* ra = reinterpret_cast<float4*>(spec + (((size_t)z * 6 + 2 * g) * n2 + x2) * H1 + k);
+    float4* rbp = reinterpret_cast<float4*>(spec + (((size_t)z * 6 + 2 * g + 1) * n2 + x2) * H1 + k);
+    *ra = make_float4(A0.x, A0.y, A1.x, A1.y);
+    *rbp = make_float4(B0.x, B0.y, B1.x, B1.y);
+  }
+  if (t < 3) {
+    float2 A, B;
+    split_pair_ct(sm.get(t, H1), sm.get(t, H1), A, B);
+    nq[((size_t)z * 6 + 2 * t) * n2 + x2] = A.x;
+    nq[((size_t)z * 6 + 2 * t + 1) * n2 + x2] = B.x;
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) k_rows_inv6_v(const float2* __restrict__ spec, const float* __restrict__ nq,
+                                                     float* __restrict__ out, const float2* __restrict__ tw, int n2,
+                                                     int rb, int z0, float nq_scale, float scale) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int T8 = N / 8, LD = N + N / 8, H1 = N / 2;
+  const int r = threadIdx.x / T8, t = threadIdx.x % T8;
+  const int z = z0 + blockIdx.y;
+  const int x2b = blockIdx.x * rb, x2 = x2b + r;
+  float2* stg = reinterpret_cast<float2*>(smraw);  // [6][rb][H1]
+  const int per_row = H1 / 2;                      // 16-byte pieces of a half-spectrum row
+  for (int i = threadIdx.x; i < 6 * rb * per_row; i += blockDim.x) {
+    const int cr = i / per_row, j = 2 * (i - cr * per_row);
+    const int c = cr / rb, rr = cr - c * rb;
+    cp_async_16(stg + (size_t)cr * H1 + j, spec + (((size_t)z * 6 + c) * n2 + x2b + rr) * H1 + j);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  float2 v[3][8];
+#pragma unroll
+  for (int g = 0; g < 3; ++g) {
+    const float2* sa = stg + ((size_t)(2 * g) * rb + r) * H1;
+    const float2* sb = stg + ((size_t)(2 * g + 1) * rb + r) * H1;
+    const float na = nq_scale == 0.f ? 0.f : nq_scale * nq[((size_t)z * 6 + 2 * g) * n2 + x2];
+    const float nb = nq_scale == 0.f ? 0.f : nq_scale * nq[((size_t)z * 6 + 2 * g + 1) * n2 + x2];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int k = t + m * T8;
+      const int kk = k < H1 ? k : (k > H1 ? N - k : 0);
+      float2 A = sa[kk], B = sb[kk];
+      if (k > H1) {
+        A = cconj(A);
+        B = cconj(B);
+      }
+      if (k == H1) {
+        A = make_float2(na, 0.f);
+        B = make_float2(nb, 0.f);
+      }
+      v[g][m] = cadd(A, cmuli(B));
+    }
+  }
+  __syncthreads();  // staging is dead: the exchange area takes its place
+  RowSm<float2> sm{reinterpret_cast<float2*>(smraw) + (size_t)r * 3 * LD, LD};
+  fft_ct<float2, true, N, 3, 1>(v, t, sm, tw);
+  float* ostg = reinterpret_cast<float*>(smraw);  // [6][rb][N]; every exchange read is done
+#pragma unroll
+  for (int g = 0; g < 3; ++g)
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int x1 = t + m * T8;
+      ostg[((size_t)(2 * g) * rb + r) * N + x1] = v[g][m].x * scale;
+      ostg[((size_t)(2 * g + 1) * rb + r) * N + x1] = v[g][m].y * scale;
+    }
+  __syncthreads();
+  const int per_c = rb * N / 4;
+  for (int i = threadIdx.x; i < 6 * per_c; i += blockDim.x) {
+    const int c = i / per_c, j = i - c * per_c;
+    reinterpret_cast<float4*>(out + (((size_t)z * 6 + c) * n2 + x2b) * N)[j] =
+        reinterpret_cast<const float4*>(ostg + (size_t)c * rb * N)[j];
+  }
+}
+
 template <typename K> void smem_attr(K kern, size_t smem) {
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
@@ -162,6 +318,20 @@ inline int ct_rows(int n1, int n2) {
 
 template <typename T, int N> void cols_n(const fvim_ctx* c, bool inverse, void* planes, int nplanes) {
   typedef typename Cx<T>::t V;
+  if constexpr (sizeof(T) == 4 && N >= 64) {
+    if (c->h1 % 8 == 0) {
+      dim3 grid(c->h1 / 8, nplanes);
+      const size_t sm = (size_t)N * 8 * sizeof(float2);
+      if (inverse) {
+        smem_attr(k_cols_v<true, N>, sm);
+        k_cols_v<true, N><<<grid, N / 2, sm, c->stream>>>((float2*)planes, (const float2*)c->tw2, c->h1);
+      } else {
+        smem_attr(k_cols_v<false, N>, sm);
+        k_cols_v<false, N><<<grid, N / 2, sm, c->stream>>>((float2*)planes, (const float2*)c->tw2, c->h1);
+      }
+      return;
+    }
+  }
   int kc = (int)(64 / sizeof(V));
   while (kc > 1 && kc * (N / 8) > 512) kc >>= 1;
   if (kc > c->h1) kc = c->h1;
@@ -180,6 +350,15 @@ template <typename T, int N> void cols_n(const fvim_ctx* c, bool inverse, void* 
 template <typename T, int N> void rows_fwd_n(const fvim_ctx* c, const T* eps_p, int z0, int nzs) {
   typedef typename Cx<T>::t V;
   const int rb = ct_rows(N, c->n2);
+  if constexpr (sizeof(T) == 4 && N >= 64) {
+    const size_t sm = std::max((size_t)rb * 3 * (N + N / 8) * sizeof(V), (size_t)6 * rb * N * sizeof(T));
+    dim3 grid(c->n2 / rb, nzs);
+    smem_attr(k_rows_fwd6_v<N>, sm);
+    k_rows_fwd6_v<N><<<grid, rb * (N / 8), sm, c->stream>>>((const float*)eps_p, (float2*)c->spec, (float*)c->nq,
+                                                            (const float2*)c->tw1, c->n2, rb, z0, (float)c->lam,
+                                                            (float)c->mu);
+    return;
+  }
   const size_t smem = (size_t)rb * 3 * (N + N / 8) * sizeof(V);
   dim3 grid(c->n2 / rb, nzs);
   smem_attr(k_rows_fwd6_ct<T, N>, smem);
@@ -190,6 +369,16 @@ template <typename T, int N> void rows_fwd_n(const fvim_ctx* c, const T* eps_p, 
 template <typename T, int N> void rows_inv_n(const fvim_ctx* c, T* out, T nq_scale, int z0, int nzs) {
   typedef typename Cx<T>::t V;
   const int rb = ct_rows(N, c->n2);
+  if constexpr (sizeof(T) == 4 && N >= 64) {
+    const size_t sm = std::max((size_t)rb * 3 * (N + N / 8) * sizeof(V), (size_t)6 * rb * N * sizeof(T));
+    dim3 grid(c->n2 / rb, nzs);
+    const float scale = (float)(1.0 / ((double)N * (double)c->n2));
+    smem_attr(k_rows_inv6_v<N>, sm);
+    k_rows_inv6_v<N><<<grid, rb * (N / 8), sm, c->stream>>>((const float2*)c->spec, (const float*)c->nq,
+                                                            (float*)out, (const float2*)c->tw1, c->n2, rb, z0,
+                                                            (float)nq_scale, scale);
+    return;
+  }
   const size_t smem = (size_t)rb * 3 * (N + N / 8) * sizeof(V);
   dim3 grid(c->n2 / rb, nzs);
   const T scale = (T)(1.0 / ((double)N * (double)c->n2));
