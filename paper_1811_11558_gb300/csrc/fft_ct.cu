@@ -183,11 +183,11 @@ __global__ void __launch_bounds__(256) k_rows_inv6_ct(const typename Cx<T>::t* _
     }
 }
 
-// FP32 row passes with 16-byte global accesses.  The CTA's rows are staged in shared memory
-// with 16-byte cp.async copies (forward: the six eps_p rows; inverse: the six half-spectrum
-// rows), read from there in the FFT's strided order, and the staging area then serves as the
-// FFT exchange area.  Results leave as float4: two spectrum entries (forward) or four real
-// values staged back through shared memory (inverse).
+// FP32 forward row pass with 16-byte global accesses: the CTA's six eps_p rows are staged in
+// shared memory with 16-byte cp.async copies and read from there in the FFT's strided order;
+// the staging area then serves as the FFT exchange area, and the half spectrum leaves as
+// float4 pairs of entries.  (Staging the inverse pass the same way made it slower: 0.254
+// against 0.183 ms at 512 x 512 x 64, from the extra shared-memory traffic and registers.)
 template <int N>
 __global__ void __launch_bounds__(256) k_rows_fwd6_v(const float* __restrict__ eps_p, float2* __restrict__ spec,
                                                      float* __restrict__ nq, const float2* __restrict__ tw, int n2,
@@ -240,68 +240,6 @@ __global__ void __launch_bounds__(256) k_rows_fwd6_v(const float* __restrict__ e
     split_pair_ct(sm.get(t, H1), sm.get(t, H1), A, B);
     nq[((size_t)z * 6 + 2 * t) * n2 + x2] = A.x;
     nq[((size_t)z * 6 + 2 * t + 1) * n2 + x2] = B.x;
-  }
-}
-
-template <int N>
-__global__ void __launch_bounds__(256) k_rows_inv6_v(const float2* __restrict__ spec, const float* __restrict__ nq,
-                                                     float* __restrict__ out, const float2* __restrict__ tw, int n2,
-                                                     int rb, int z0, float nq_scale, float scale) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  constexpr int T8 = N / 8, LD = N + N / 8, H1 = N / 2;
-  const int r = threadIdx.x / T8, t = threadIdx.x % T8;
-  const int z = z0 + blockIdx.y;
-  const int x2b = blockIdx.x * rb, x2 = x2b + r;
-  float2* stg = reinterpret_cast<float2*>(smraw);  // [6][rb][H1]
-  const int per_row = H1 / 2;                      // 16-byte pieces of a half-spectrum row
-  for (int i = threadIdx.x; i < 6 * rb * per_row; i += blockDim.x) {
-    const int cr = i / per_row, j = 2 * (i - cr * per_row);
-    const int c = cr / rb, rr = cr - c * rb;
-    cp_async_16(stg + (size_t)cr * H1 + j, spec + (((size_t)z * 6 + c) * n2 + x2b + rr) * H1 + j);
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  float2 v[3][8];
-#pragma unroll
-  for (int g = 0; g < 3; ++g) {
-    const float2* sa = stg + ((size_t)(2 * g) * rb + r) * H1;
-    const float2* sb = stg + ((size_t)(2 * g + 1) * rb + r) * H1;
-    const float na = nq_scale == 0.f ? 0.f : nq_scale * nq[((size_t)z * 6 + 2 * g) * n2 + x2];
-    const float nb = nq_scale == 0.f ? 0.f : nq_scale * nq[((size_t)z * 6 + 2 * g + 1) * n2 + x2];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int k = t + m * T8;
-      const int kk = k < H1 ? k : (k > H1 ? N - k : 0);
-      float2 A = sa[kk], B = sb[kk];
-      if (k > H1) {
-        A = cconj(A);
-        B = cconj(B);
-      }
-      if (k == H1) {
-        A = make_float2(na, 0.f);
-        B = make_float2(nb, 0.f);
-      }
-      v[g][m] = cadd(A, cmuli(B));
-    }
-  }
-  __syncthreads();  // staging is dead: the exchange area takes its place
-  RowSm<float2> sm{reinterpret_cast<float2*>(smraw) + (size_t)r * 3 * LD, LD};
-  fft_ct<float2, true, N, 3, 1>(v, t, sm, tw);
-  float* ostg = reinterpret_cast<float*>(smraw);  // [6][rb][N]; every exchange read is done
-#pragma unroll
-  for (int g = 0; g < 3; ++g)
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int x1 = t + m * T8;
-      ostg[((size_t)(2 * g) * rb + r) * N + x1] = v[g][m].x * scale;
-      ostg[((size_t)(2 * g + 1) * rb + r) * N + x1] = v[g][m].y * scale;
-    }
-  __syncthreads();
-  const int per_c = rb * N / 4;
-  for (int i = threadIdx.x; i < 6 * per_c; i += blockDim.x) {
-    const int c = i / per_c, j = i - c * per_c;
-    reinterpret_cast<float4*>(out + (((size_t)z * 6 + c) * n2 + x2b) * N)[j] =
-        reinterpret_cast<const float4*>(ostg + (size_t)c * rb * N)[j];
   }
 }
 
@@ -369,16 +307,6 @@ template <typename T, int N> void rows_fwd_n(const fvim_ctx* c, const T* eps_p, 
 template <typename T, int N> void rows_inv_n(const fvim_ctx* c, T* out, T nq_scale, int z0, int nzs) {
   typedef typename Cx<T>::t V;
   const int rb = ct_rows(N, c->n2);
-  if constexpr (sizeof(T) == 4 && N >= 64) {
-    const size_t sm = std::max((size_t)rb * 3 * (N + N / 8) * sizeof(V), (size_t)6 * rb * N * sizeof(T));
-    dim3 grid(c->n2 / rb, nzs);
-    const float scale = (float)(1.0 / ((double)N * (double)c->n2));
-    smem_attr(k_rows_inv6_v<N>, sm);
-    k_rows_inv6_v<N><<<grid, rb * (N / 8), sm, c->stream>>>((const float2*)c->spec, (const float*)c->nq,
-                                                            (float*)out, (const float2*)c->tw1, c->n2, rb, z0,
-                                                            (float)nq_scale, scale);
-    return;
-  }
   const size_t smem = (size_t)rb * 3 * (N + N / 8) * sizeof(V);
   dim3 grid(c->n2 / rb, nzs);
   const T scale = (T)(1.0 / ((double)N * (double)c->n2));
