@@ -60,3 +60,24 @@ def test_budget_refuses_oversized_request():
     r = _requests("fp32")[0]
     with pytest.raises(ValueError):
         Server(slots=2, hbm_budget=1024).solve(r)
+
+
+def test_new_shapes_arriving_while_others_capture_graphs():
+    """Twelve requests of twelve different shapes on eight slots: contexts are created (device
+    allocations, fills on the legacy stream) while other requests capture and replay their
+    solver graphs.  Every request completes and gives the bits it gives alone."""
+    require_gpu()
+    from paper_1811_11558_gb300.serve import Request, Server
+
+    reqs = []
+    for i in range(12):
+        n = (16, 32)[i % 2]
+        z = inputs.uniform_depth(6 + i, 0.3)
+        h = inputs.self_affine_surface(n, 1.0, 0.8, 2, 4, n // 4, 0.1, seed=1900 + i)
+        reqs.append(Request(i, n, z, h, [1e-3, 2e-3], precision="fp32", sigma_y=0.05 * ES, E_h=0.1,
+                            opts={"max_iter": 60, "relax": 0.3}))
+    mix, _ = Server(slots=8).run(reqs)
+    alone = [Server(slots=1).solve(r) for r in reqs]
+    for a, m in zip(alone, mix):
+        assert m is not None and m.report["n_increments"] == 2
+        assert np.array_equal(a.pressure, m.pressure)
