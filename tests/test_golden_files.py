@@ -1,0 +1,46 @@
+"""The stored Algorithm-1 solutions satisfy the equations that define them.
+
+The golden files are written by the oracle (tests/golden/make_*_golden.py); these checks do
+not call the oracle: they restate, on the stored arrays, the total-load constraint and the
+positivity of the pressure (Sec. 5.1), the plastic incompressibility of eps_p and the yield
+admissibility of the stress state (Sec. 4.1), in a few lines of numpy.
+"""
+import os
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+E, NU = 1.0, 0.3
+
+
+def _von_mises(sig):
+    s = np.array(sig, dtype=np.float64)
+    m = (s[:, 0] + s[:, 1] + s[:, 2]) / 3.0
+    for k in range(3):
+        s[:, k] -= m
+    return np.sqrt(1.5 * (s[:, 0] ** 2 + s[:, 1] ** 2 + s[:, 2] ** 2 + 2 * (s[:, 3] ** 2 + s[:, 4] ** 2 + s[:, 5] ** 2)))
+
+
+@pytest.mark.parametrize("name", ["hertz_32x32x16.npz", "rough_32x32x8.npz"])
+def test_golden_solution_is_admissible(name):
+    g = np.load(os.path.join(GOLDEN, name))
+    p, ep, epp, sig = g["p"], g["e_p"], g["eps_p"], g["sigma"]
+    n2, n1 = p.shape
+    dA = 1.0 / (n1 * n2)
+    W = float(g["loads"][-1])
+    # total load and unilateral contact
+    assert abs(p.sum() * dA - W) < 1e-10 * W
+    assert (p >= 0).all()
+    assert abs((p > 0).mean() - g["areas"][-1]) == 0
+    # plastic flow is isochoric, cumulated plastic strain is non-negative
+    assert np.abs(epp[:, 0] + epp[:, 1] + epp[:, 2]).max() < 1e-12
+    assert (ep >= -1e-15).all() and ep.max() > 0
+    # the stress state lies inside the current yield surface (to the solver tolerance)
+    fy = float(g["sigma_y"]) + float(g["E_h"]) * ep
+    assert (_von_mises(sig) <= fy * (1 + 1e-6)).all()
+    # where plastic strain accumulated, the state is on the yield surface (it was at the last
+    # increment that loaded it; check that at least the most strained point is)
+    i = np.unravel_index(np.argmax(ep), ep.shape)
+    vm = _von_mises(sig)
+    assert abs(vm[i] - fy[i]) < 1e-6 * fy[i]

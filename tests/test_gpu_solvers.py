@@ -117,6 +117,51 @@ def test_solve_contact_fp32_matches_oracle_hertz():
     assert np.abs(np.array(rep["contact_area"]) - g["areas"]).max() <= 1e-4 + 1.0 / 1024
 
 
+ROUGH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rough_32x32x8.npz")
+
+
+def _rough_run(prec, **opt_kw):
+    """The small elastic-plastic rough-surface case (self-affine 32 x 32, 8 nodes to z = 0.1,
+    two increments to W = 5e-3, relaxation 0.3) through Algorithm 1 on the GPU."""
+    torch = require_gpu()
+    g = np.load(ROUGH)
+    n, nz = 32, 8
+    z = inputs.uniform_depth(nz, float(g["depth"]))
+    # the stored surface is the oracle's input (the generator's FFT may round differently on
+    # another machine)
+    h = np.array(g["h"])
+    assert np.allclose(h, inputs.self_affine_surface(n, 1.0, 0.8, 2, 4, 8, 0.1, seed=1813), rtol=0, atol=1e-12)
+    ctx = _ctx(n, z, prec, sigma_y=float(g["sigma_y"]), E_h=float(g["E_h"]))
+    dt = ctx.dtype
+    p = torch.empty(ctx.surf_shape, dtype=dt, device="cuda")
+    rep = ctx.solve_contact(to_dev(torch, h, dt), list(g["loads"]), p,
+                            ctx.default_opts(relax=float(g["relax"]), **opt_kw))
+    epp = torch.empty(ctx.vol_shape, dtype=dt, device="cuda")
+    ep = torch.empty(ctx.scal_shape, dtype=dt, device="cuda")
+    ctx.get_state(epp, ep, None)
+    torch.cuda.synchronize()
+    return g, rep, p.cpu().numpy(), epp.cpu().numpy(), ep.cpu().numpy()
+
+
+def test_rough_solve_fp64_matches_oracle():
+    g, rep, p, epp, ep = _rough_run("fp64", cg_tol=1e-13, df_tol_rel=1e-11, max_iter=200)
+    assert rep["status"] == 0 and rep["n_increments"] == 2
+    assert rel_l2(p, g["p"]) < 1e-7
+    assert rel_l2(ep, g["e_p"]) < 1e-6
+    assert rel_l2(epp, g["eps_p"]) < 1e-6
+    assert np.array_equal(np.array(rep["contact_area"]), g["areas"])
+
+
+def test_rough_solve_fp32_matches_oracle():
+    g, rep, p, epp, ep = _rough_run("fp32", max_iter=200)
+    print("rough FP32 vs oracle: p %.2e e_p %.2e eps_p %.2e areas %s vs %s" % (
+        rel_l2(p, g["p"]), rel_l2(ep, g["e_p"]), rel_l2(epp, g["eps_p"]), rep["contact_area"], list(g["areas"])))
+    assert rep["status"] == 0
+    assert rel_l2(p, g["p"]) < 2e-5
+    assert rel_l2(ep, g["e_p"]) < 2e-5
+    assert np.abs(np.array(rep["contact_area"]) - g["areas"]).max() <= 1e-4 + 1.0 / 1024
+
+
 def test_solve_contact_deterministic_and_caps():
     torch = require_gpu()
     n, nz = 16, 8
