@@ -31,6 +31,41 @@ template <typename V> __device__ __forceinline__ V caxpy(V a, decltype(V::x) s, 
   return mk<V>(a.x + s * b.x, a.y + s * b.y);
 }
 
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000) && !defined(FVIM_NO_F32X2)
+// Blackwell packed FP32 pairs (add/sub/mul/fma .f32x2): one instruction per FP32 complex
+// add, subtract, real scale or real axpy, each lane rounded as its scalar counterpart.
+__device__ __forceinline__ unsigned long long f2pack(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 f2unpack(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2pack(a)), "l"(f2pack(b)));
+  return f2unpack(d);
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2pack(a)), "l"(f2pack(b)));
+  return f2unpack(d);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2pack(a)), "l"(f2pack(make_float2(s, s))));
+  return f2unpack(d);
+}
+__device__ __forceinline__ float2 caxpy(float2 a, float s, float2 b) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2pack(make_float2(s, s))), "l"(f2pack(b)), "l"(f2pack(a)));
+  return f2unpack(d);
+}
+#endif
+
 // ---------------------------------------------------------------------------
 // Shared-memory FFT: batched, in place, Stockham autosort with radix 8/4/2
 // stages.  Every thread of the block takes part; at most MAXI work items (one
