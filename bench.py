@@ -305,7 +305,7 @@ def hertz_case():
                 loads=[wmax * (k + 1) / 5 for k in range(5)], sigma_y=sy, E_h=0.1 * E)
 
 
-def solve_metrics(repeats=3, served=16, slots=8):
+def solve_metrics(repeats=3, served=32, slots=16):
     """Contact solves/s of Algorithm 1 (relaxation 0.5) on the Hertz case: FP64 and FP32 one
     solve at a time, and FP32 served (requests admitted as slots free up, solves overlapping on
     the device), with p50/p99 latency and the FP32 error against the FP64 solution."""

@@ -410,8 +410,9 @@ __global__ void k_df_sy(const T* __restrict__ x, const T* __restrict__ xn, const
 }
 // dst = a + s b over a volume vector (FP32: four values at a time, FP32 arithmetic)
 template <typename T>
-__global__ void k_axpby_vol(T* __restrict__ dst, const T* __restrict__ a, double s, const T* __restrict__ b,
-                            size_t n) {
+__global__ void k_axpby_vol(T* __restrict__ dst, const T* __restrict__ a, double s, const double* __restrict__ sdev,
+                            const T* __restrict__ b, size_t n) {
+  if (sdev) s *= *sdev;
   if constexpr (sizeof(T) == 4) {
     const float sf = (float)s;
     for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < (n >> 2); i += (size_t)gridDim.x * RT) {
@@ -437,8 +438,10 @@ template <typename T> int axpby(fvim_ctx* c, T* dst, const T* a, double s, const
   FVIM_CUDA_CHECK_LAUNCH();
   return FVIM_OK;
 }
-template <typename T> int axpby_vol(fvim_ctx* c, T* dst, const T* a, double s, const T* b, size_t n) {
-  k_axpby_vol<T><<<rgrid(sizeof(T) == 4 ? n / 4 : n), RT, 0, c->stream>>>(dst, a, s, b, n);
+// dst = a + s (*sdev) b (sdev: a device scalar, or NULL for 1)
+template <typename T>
+int axpby_vol(fvim_ctx* c, T* dst, const T* a, double s, const double* sdev, const T* b, size_t n) {
+  k_axpby_vol<T><<<rgrid(sizeof(T) == 4 ? n / 4 : n), RT, 0, c->stream>>>(dst, a, s, sdev, b, n);
   FVIM_CUDA_CHECK_LAUNCH();
   return FVIM_OK;
 }
@@ -456,6 +459,7 @@ struct PKS {
   double nIc, gbar, G_old, beta, delta, rbar, tau, s, err;
   int done, it, bad, pad;
 };
+static_assert(sizeof(PKS) <= 128, "the DF-SANE step is kept at byte 128 of the scalar block");
 
 // sum the partials [nblk][NV] of a reduction grid in a fixed order (one block)
 template <int NV> __device__ __forceinline__ void fin_sum(const double* part, int nblk, double (&out)[NV]) {
@@ -465,7 +469,7 @@ template <int NV> __device__ __forceinline__ void fin_sum(const double* part, in
   for (int j = 0; j < NV; ++j) v[j] = 0;
   for (int b = threadIdx.x; b < nblk; b += RT)
 #pragma unroll
-    for (int j = 0; j < NV; ++j) v[j] += part[b * NV + j];
+    for (int j = 0; j < NV; ++j) v[j] += __ldcg(part + b * NV + j);
 #pragma unroll
   for (int j = 0; j < NV; ++j) sh[j][threadIdx.x] = v[j];
   __syncthreads();
@@ -479,7 +483,7 @@ template <int NV> __device__ __forceinline__ void fin_sum(const double* part, in
   for (int j = 0; j < NV; ++j) out[j] = sh[j][0];
 }
 
-__global__ void k_fin_stats(const double* part, int nblk, PKS* S) {
+__device__ __forceinline__ void fin_stats(const double* part, int nblk, PKS* S) {
   if (S->done) return;
   double v[2];
   fin_sum<2>(part, nblk, v);
@@ -489,7 +493,7 @@ __global__ void k_fin_stats(const double* part, int nblk, PKS* S) {
     else S->gbar = v[0] / v[1];
   }
 }
-__global__ void k_fin_G(const double* part, int nblk, PKS* S) {
+__device__ __forceinline__ void fin_G(const double* part, int nblk, PKS* S) {
   if (S->done) return;
   double v[1];
   fin_sum<1>(part, nblk, v);
@@ -498,19 +502,19 @@ __global__ void k_fin_G(const double* part, int nblk, PKS* S) {
     S->G_old = v[0];
   }
 }
-__global__ void k_fin_rbar(const double* part, int nblk, PKS* S) {
+__device__ __forceinline__ void fin_rbar(const double* part, int nblk, PKS* S) {
   if (S->done) return;
   double v[1];
   fin_sum<1>(part, nblk, v);
   if (threadIdx.x == 0) S->rbar = v[0] / S->nIc;
 }
-__global__ void k_fin_tau(const double* part, int nblk, PKS* S) {
+__device__ __forceinline__ void fin_tau(const double* part, int nblk, PKS* S) {
   if (S->done) return;
   double v[2];
   fin_sum<2>(part, nblk, v);
   if (threadIdx.x == 0) S->tau = v[1] != 0 ? v[0] / v[1] : 0.0;
 }
-__global__ void k_fin_scale(const double* part, int nblk, PKS* S, double W, double dA) {
+__device__ __forceinline__ void fin_scale(const double* part, int nblk, PKS* S, double W, double dA) {
   if (S->done) return;
   double v[2];
   fin_sum<2>(part, nblk, v);
@@ -520,7 +524,7 @@ __global__ void k_fin_scale(const double* part, int nblk, PKS* S, double W, doub
     else S->s = W / (dA * v[0]);
   }
 }
-__global__ void k_fin_err(const double* part, int nblk, PKS* S, double W, double dA, double tol, int max_it) {
+__device__ __forceinline__ void fin_err(const double* part, int nblk, PKS* S, double W, double dA, double tol, int max_it) {
   if (S->done) return;
   double v[2];
   fin_sum<2>(part, nblk, v);
@@ -532,18 +536,37 @@ __global__ void k_fin_err(const double* part, int nblk, PKS* S, double W, double
   }
 }
 
+// The reduction kernels below finish their own sums: the last block to arrive (counted
+// with an atomic, after a fence) adds the partials in block order and applies the scalar
+// logic, then re-arms the counter for the next kernel.
+__device__ __forceinline__ bool last_block(unsigned* cnt) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+  __syncthreads();
+  return last;
+}
+__device__ __forceinline__ void rearm(unsigned* cnt) {
+  if (threadIdx.x == 0) *cnt = 0u;
+}
+
 template <typename T>
 __global__ void k_pkd_stats(const T* __restrict__ u, const T* __restrict__ h, const T* __restrict__ p, size_t n,
-                            double* part, const PKS* S) {
+                            double* part, PKS* S, unsigned* cnt) {
   if (S->done) return;
   double v[2] = {0, 0};
   for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT)
     if (p[i] > 0) { v[0] += (double)u[i] - (double)h[i]; v[1] += 1; }
   block_reduce<2>(v, part);
+  if (last_block(cnt)) {
+    fin_stats(part, gridDim.x, S);
+    rearm(cnt);
+  }
 }
 template <typename T>
 __global__ void k_pkd_g(const T* __restrict__ u, const T* __restrict__ h, const T* __restrict__ p, T* __restrict__ g,
-                        size_t n, double* part, const PKS* S) {
+                        size_t n, double* part, PKS* S, unsigned* cnt) {
   if (S->done) return;
   const double gbar = S->gbar;
   double v[1] = {0};
@@ -553,6 +576,10 @@ __global__ void k_pkd_g(const T* __restrict__ u, const T* __restrict__ h, const 
     if (p[i] > 0) v[0] += (double)gi * (double)gi;
   }
   block_reduce<1>(v, part);
+  if (last_block(cnt)) {
+    fin_G(part, gridDim.x, S);
+    rearm(cnt);
+  }
 }
 template <typename T>
 __global__ void k_pkd_dir(const T* __restrict__ g, const T* __restrict__ p, T* __restrict__ t, size_t n,
@@ -563,16 +590,21 @@ __global__ void k_pkd_dir(const T* __restrict__ g, const T* __restrict__ p, T* _
     t[i] = p[i] > 0 ? (T)((double)g[i] + beta * (double)t[i]) : (T)0;
 }
 template <typename T>
-__global__ void k_pkd_rsum(const T* __restrict__ r, const T* __restrict__ p, size_t n, double* part, const PKS* S) {
+__global__ void k_pkd_rsum(const T* __restrict__ r, const T* __restrict__ p, size_t n, double* part, PKS* S,
+                           unsigned* cnt) {
   if (S->done) return;
   double v[1] = {0};
   for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT)
     if (p[i] > 0) v[0] += (double)r[i];
   block_reduce<1>(v, part);
+  if (last_block(cnt)) {
+    fin_rbar(part, gridDim.x, S);
+    rearm(cnt);
+  }
 }
 template <typename T>
 __global__ void k_pkd_dots(const T* __restrict__ g, const T* __restrict__ t, const T* __restrict__ r,
-                           const T* __restrict__ p, size_t n, double* part, const PKS* S) {
+                           const T* __restrict__ p, size_t n, double* part, PKS* S, unsigned* cnt) {
   if (S->done) return;
   const double rbar = S->rbar;
   double v[2] = {0, 0};
@@ -582,10 +614,15 @@ __global__ void k_pkd_dots(const T* __restrict__ g, const T* __restrict__ t, con
       v[1] += ((double)r[i] - rbar) * (double)t[i];
     }
   block_reduce<2>(v, part);
+  if (last_block(cnt)) {
+    fin_tau(part, gridDim.x, S);
+    rearm(cnt);
+  }
 }
 template <typename T>
 __global__ void k_pkd_update(T* __restrict__ p, T* __restrict__ pold, const T* __restrict__ t,
-                             const T* __restrict__ g, size_t n, double* part, const PKS* S) {
+                             const T* __restrict__ g, size_t n, double* part, PKS* S, unsigned* cnt, double W,
+                             double dA) {
   if (S->done) return;
   const double tau = S->tau;
   double v[2] = {0, 0};
@@ -600,9 +637,14 @@ __global__ void k_pkd_update(T* __restrict__ p, T* __restrict__ pold, const T* _
     v[1] += ol ? 1.0 : 0.0;
   }
   block_reduce<2>(v, part);
+  if (last_block(cnt)) {
+    fin_scale(part, gridDim.x, S, W, dA);
+    rearm(cnt);
+  }
 }
 template <typename T>
-__global__ void k_pkd_scale(T* __restrict__ p, const T* __restrict__ pold, size_t n, double* part, const PKS* S) {
+__global__ void k_pkd_scale(T* __restrict__ p, const T* __restrict__ pold, size_t n, double* part, PKS* S,
+                            unsigned* cnt, double W, double dA, double tol, int max_it) {
   if (S->done) return;
   const double s = S->s;
   double v[2] = {0, 0};
@@ -613,6 +655,10 @@ __global__ void k_pkd_scale(T* __restrict__ p, const T* __restrict__ pold, size_
     v[1] += pn > (T)0 ? 1.0 : 0.0;
   }
   block_reduce<2>(v, part);
+  if (last_block(cnt)) {
+    fin_err(part, gridDim.x, S, W, dA, tol, max_it);
+    rearm(cnt);
+  }
 }
 
 template <typename T>
@@ -639,6 +685,9 @@ int elastic_contact_t(fvim_ctx* c, const T* h, double W, T* p, const fvim_opts* 
   s0.G_old = 1.0;
   s0.err = INFINITY;
   if (FVIM_CU(cudaMemcpyAsync(st, &s0, sizeof(PKS), cudaMemcpyHostToDevice, c->stream))) return FVIM_ERR_CUDA;
+  // arrival counter of the self-finishing reductions (byte 192 of the scalar block)
+  unsigned* cnt = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(st) + 192);
+  if (FVIM_CU(cudaMemsetAsync(cnt, 0, sizeof(unsigned), c->stream))) return FVIM_ERR_CUDA;
   PKS* sh = reinterpret_cast<PKS*>(c->h_part + (size_t)RMAXB * NVMAX);  // pinned
   *sh = s0;
   const int batch = 4;  // iterations issued between two reads of the stop flag
@@ -650,20 +699,14 @@ int elastic_contact_t(fvim_ctx* c, const T* h, double W, T* p, const fvim_opts* 
       int r;
       for (int b = 0; b < nb; ++b) {
         if ((r = conv<T>(c, p, u))) return r;
-        k_pkd_stats<T><<<grd, RT, 0, c->stream>>>(u, h, p, n, part, st);
-        k_fin_stats<<<1, RT, 0, c->stream>>>(part, grd, st);
-        k_pkd_g<T><<<grd, RT, 0, c->stream>>>(u, h, p, g, n, part, st);
-        k_fin_G<<<1, RT, 0, c->stream>>>(part, grd, st);
+        k_pkd_stats<T><<<grd, RT, 0, c->stream>>>(u, h, p, n, part, st, cnt);
+        k_pkd_g<T><<<grd, RT, 0, c->stream>>>(u, h, p, g, n, part, st, cnt);
         k_pkd_dir<T><<<grd, RT, 0, c->stream>>>(g, p, t, n, st);
         if ((r = conv<T>(c, t, r_))) return r;
-        k_pkd_rsum<T><<<grd, RT, 0, c->stream>>>(r_, p, n, part, st);
-        k_fin_rbar<<<1, RT, 0, c->stream>>>(part, grd, st);
-        k_pkd_dots<T><<<grd, RT, 0, c->stream>>>(g, t, r_, p, n, part, st);
-        k_fin_tau<<<1, RT, 0, c->stream>>>(part, grd, st);
-        k_pkd_update<T><<<grd, RT, 0, c->stream>>>(p, pold, t, g, n, part, st);
-        k_fin_scale<<<1, RT, 0, c->stream>>>(part, grd, st, W, dA);
-        k_pkd_scale<T><<<grd, RT, 0, c->stream>>>(p, pold, n, part, st);
-        k_fin_err<<<1, RT, 0, c->stream>>>(part, grd, st, W, dA, o->cg_tol, o->cg_max_iter);
+        k_pkd_rsum<T><<<grd, RT, 0, c->stream>>>(r_, p, n, part, st, cnt);
+        k_pkd_dots<T><<<grd, RT, 0, c->stream>>>(g, t, r_, p, n, part, st, cnt);
+        k_pkd_update<T><<<grd, RT, 0, c->stream>>>(p, pold, t, g, n, part, st, cnt, W, dA);
+        k_pkd_scale<T><<<grd, RT, 0, c->stream>>>(p, pold, n, part, st, cnt, W, dA, o->cg_tol, o->cg_max_iter);
         FVIM_CUDA_CHECK_LAUNCH();
       }
       return FVIM_OK;
@@ -682,6 +725,22 @@ int elastic_contact_t(fvim_ctx* c, const T* h, double W, T* p, const fvim_opts* 
 }
 
 // ---- DF-SANE on R[x] = x - b - grad^sym N[C:deps_p(x; S)] --------------------------
+// spectral step sigma = <s, s> / <s, y> with its safeguard, finished on the device so the
+// next trial point needs no host round trip
+__global__ void k_df_sigma(const double* part, int nblk, double fn, double smin, double smax, double* sig) {
+  double v[2];
+  fin_sum<2>(part, nblk, v);
+  if (threadIdx.x == 0) {
+    double sigma = v[1] != 0 ? v[0] / v[1] : INFINITY;
+    if (!(fabs(sigma) >= smin && fabs(sigma) <= smax)) {
+      const double nf = sqrt(fn);
+      sigma = nf > 1 ? 1.0 : (nf >= 1e-5 ? 1.0 / nf : 1e5);
+    }
+    *sig = sigma;
+  }
+}
+__global__ void k_set_double(double* d, double v) { *d = v; }
+
 template <typename T> struct DF {
   fvim_ctx* c;
   size_t n, nxy;
@@ -746,7 +805,10 @@ int plasticity_t(fvim_ctx* c, const T* dT, T* dE, T* deps_p, T* dep, const fvim_
   const int M = 10;
   const double gamma = 1e-4, smin = 1e-10, smax = 1e10, tmin = 0.1, tmax = 0.5;
   std::vector<double> hist(1, f);
-  double sigma = 1.0;
+  // the spectral step lives on the device (after the plasticity state block)
+  double* dsig = reinterpret_cast<double*>(static_cast<char*>(c->sv[V_PKS]) + 128);
+  k_set_double<<<1, 1, 0, c->stream>>>(dsig, 1.0);
+  FVIM_CUDA_CHECK_LAUNCH();
   int k = 0;
   bool conv_ok = false;
   // stagnation at the rounding floor of the path precision: the best residual of the
@@ -770,11 +832,11 @@ int plasticity_t(fvim_ctx* c, const T* dT, T* dE, T* deps_p, T* dep, const fvim_
     for (int bt = 0; bt < 60 && !ok; ++bt) {
       double fp, fm;
       // x + ap d with d = -sigma F
-      if ((rc = axpby_vol<T>(c, xt, x, -ap * sigma, F, n))) return rc;
+      if ((rc = axpby_vol<T>(c, xt, x, -ap, dsig, F, n))) return rc;
       if ((rc = df.eval(xt, Ft, &fp))) return rc;
       ++evals;
       if (fp <= fmax + eta - gamma * ap * ap * f) { fn = fp; ok = true; break; }
-      if ((rc = axpby_vol<T>(c, xt, x, am * sigma, F, n))) return rc;
+      if ((rc = axpby_vol<T>(c, xt, x, am, dsig, F, n))) return rc;
       if ((rc = df.eval(xt, Ft, &fm))) return rc;
       ++evals;
       if (fm <= fmax + eta - gamma * am * am * f) { fn = fm; ok = true; break; }
@@ -782,16 +844,10 @@ int plasticity_t(fvim_ctx* c, const T* dT, T* dE, T* deps_p, T* dep, const fvim_
       am = std::min(std::max(am * am * f / (fm + (2 * am - 1) * f), tmin * am), tmax * am);
     }
     if (!ok) break;
-    double sv[2];
     k_df_sy<T><<<df.grd, RT, 0, c->stream>>>(x, xt, F, Ft, (const double*)c->sv[V_WZ], df.lgxy, n,
                                              (double*)c->sv[V_PART]);
+    k_df_sigma<<<1, RT, 0, c->stream>>>((const double*)c->sv[V_PART], df.grd, fn, smin, smax, dsig);
     FVIM_CUDA_CHECK_LAUNCH();
-    if ((rc = finish<2>(c, df.grd, sv))) return rc;
-    sigma = sv[1] != 0 ? sv[0] / sv[1] : INFINITY;
-    if (!(fabs(sigma) >= smin && fabs(sigma) <= smax)) {
-      const double nf = sqrt(fn);
-      sigma = nf > 1 ? 1.0 : (nf >= 1e-5 ? 1.0 / nf : 1e5);
-    }
     std::swap(x, xt);
     std::swap(F, Ft);
     c->sv[V_X] = x;
