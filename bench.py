@@ -154,13 +154,10 @@ def run_gpu(args):
             pg.barrier()
         torch.cuda.synchronize()
 
-    # --- device-resident timing (per-kernel events recorded live by the library) ---
+    # --- device-resident timing -------------------------------------------------------
     for _ in range(args.warmup):
         ctx.apply_mindlin(d_in, d_out)
     kernels_per_step = ctx.last_kernel_count()
-    ctx.profile_read()
-    ctx.profile(True)
-    ctx.profile_read()
     barrier()
     clk = ClockSampler(local)
     clk.start()
@@ -173,10 +170,20 @@ def run_gpu(args):
     barrier()
     clocks = clk.stop()
     ms = t0.elapsed_time(t1)
-    prof = ctx.profile_read()
-    ctx.profile(False)
     ms_max = max_over_ranks(ms, pg, "cuda")
     value = replica_throughput(vox, args.steps, ms_max, ws)
+
+    # --- the same K steps again with every kernel bracketed by CUDA events on the
+    # launching stream (recorded live by the library): per-kernel durations for the roofline
+    ctx.profile_read()
+    ctx.profile(True)
+    ctx.profile_read()
+    barrier()
+    for _ in range(args.steps):
+        ctx.apply_mindlin(d_in, d_out)
+    barrier()
+    prof = ctx.profile_read()
+    ctx.profile(False)
 
     # --- end to end through the same C-ABI call with host buffers -------------------
     # every step copies its input from pinned host memory, applies the operator and copies
