@@ -98,9 +98,8 @@ template <typename V> __device__ __forceinline__ void mom_zero(Mom<V>& M) {
 // scalar Delta^-.X.Delta^- (A branch, sgn = -1) or Delta^+.X.Delta^+ (P branch, sgn = +1)
 // for the rotated components qq, 33, q3:  -X_qq + X_33 + sgn 2i X_q3
 template <typename V> __device__ __forceinline__ V nscal(V qq, V z33, V q3, int sgn) {
-  V r = csub(z33, qq);
-  V t = cmuli(q3);
-  return sgn > 0 ? caxpy(r, (decltype(V::x))2, t) : caxpy(r, (decltype(V::x))-2, t);
+  const V r = csub(z33, qq);
+  return caxpy_i(r, sgn > 0 ? (decltype(V::x))2 : (decltype(V::x))-2, q3);
 }
 
 // forward step of the g^- moments from node i to node i+1 over element [i, i+1]
@@ -180,19 +179,19 @@ __device__ __forceinline__ void kelvin_strain(const Mom<V>& A, const Mom<V>& P, 
   // eps_qq = q K [(4nu-3) S0 + S2 + 4i(nu-1) D4 + An - Pn]
   V t = cscale(S0, (T)4 * nu - (T)3);
   t = cadd(t, S2);
-  t = caxpy(t, (T)4 * (nu - (T)1), cmuli(D4));
+  t = caxpy_i(t, (T)4 * (nu - (T)1), D4);
   t = cadd(t, csub(An, Pn));
   e[0] = cscale(t, q * K);
   e[1] = mk<V>(0, 0);
   // eps_33 = K [q (S0 - (4nu-1) S2 + 4i nu D4 - An + Pn) + 4(2nu-1) w33]
   t = caxpy(S0, -((T)4 * nu - (T)1), S2);
-  t = caxpy(t, (T)4 * nu, cmuli(D4));
+  t = caxpy_i(t, (T)4 * nu, D4);
   t = cadd(t, csub(Pn, An));
   t = cscale(t, q);
   t = caxpy(t, (T)4 * ((T)2 * nu - (T)1), w[2]);
   e[2] = cscale(t, K);
   // eps_p3 = (q(-S3 + i D5) + 2 w_p3) / (4 mu)
-  t = csub(cmuli(D5), S3);
+  t = caxpy_i(cscale(S3, (T)-1), (T)1, D5);
   t = cscale(t, q);
   t = caxpy(t, (T)2, w[3]);
   e[3] = cscale(t, (T)1 / ((T)4 * mu));
@@ -200,12 +199,12 @@ __device__ __forceinline__ void kelvin_strain(const Mom<V>& A, const Mom<V>& P, 
   V u = cscale(D0, (T)2 * (nu - (T)1));
   u = caxpy(u, (T)2 * nu, D2);
   u = cadd(u, cadd(An, Pn));
-  t = caxpy(cmuli(u), (T)2, S4);
+  t = caxpy_i(cscale(S4, (T)2), (T)1, u);
   t = cscale(t, q);
   t = caxpy(t, (T)4 * (nu - (T)1), w[4]);
   e[4] = cscale(t, K);
   // eps_qp = q (i D3 + S5) / (4 mu)
-  t = cadd(cmuli(D3), S5);
+  t = caxpy_i(S5, (T)1, D3);
   e[5] = cscale(t, q / ((T)4 * mu));
 }
 
@@ -216,23 +215,19 @@ __device__ __forceinline__ void bous_strain_add(const V* tr, T zeta, T ex, T nu,
   // ex = exp(-zeta), imu = 1 / mu
   const T c1 = ex * imu, c2 = (T)0.5 * ex * imu;
   const V t0 = tr[0], t1 = tr[1], t2 = tr[2];
-  const V it0 = cmuli(t0), it1 = cmuli(t1), it2 = cmuli(t2);
   // qq: ((1-nu) i t0 + (nu - 1/2) t2 + zeta(-i t0/2 + t2/2)) / mu
-  V v = cscale(it0, (T)1 - nu);
-  v = caxpy(v, nu - (T)0.5, t2);
-  v = caxpy(v, (T)-0.5 * zeta, it0);
-  v = caxpy(v, (T)0.5 * zeta, t2);
+  //   = ((1 - nu) - zeta/2) i t0 + ((nu - 1/2) + zeta/2) t2
+  V v = caxpy_i(cscale(t2, nu - (T)0.5 + (T)0.5 * zeta), (T)1 - nu - (T)0.5 * zeta, t0);
   e[0] = caxpy(e[0], c1, v);
   // 33: (-2 i nu t0 + (2nu-1) t2 + zeta (i t0 - t2)) / (2 mu)
-  v = cscale(it0, (T)-2 * nu);
-  v = caxpy(v, (T)2 * nu - (T)1, t2);
-  v = caxpy(v, zeta, csub(it0, t2));
+  //   = (zeta - 2 nu) i t0 + ((2 nu - 1) - zeta) t2
+  v = caxpy_i(cscale(t2, (T)2 * nu - (T)1 - zeta), zeta - (T)2 * nu, t0);
   e[2] = caxpy(e[2], c2, v);
   // p3: -t1 / (2 mu) ; qp: i t1 / (2 mu)
   e[3] = caxpy(e[3], -c2, t1);
-  e[5] = caxpy(e[5], c2, it1);
-  // q3: (-t0 + zeta (t0 + i t2)) / (2 mu)
-  v = caxpy(cscale(t0, (T)-1), zeta, cadd(t0, it2));
+  e[5] = caxpy_i(e[5], c2, t1);
+  // q3: (-t0 + zeta (t0 + i t2)) / (2 mu) = (zeta - 1) t0 + zeta i t2
+  v = caxpy_i(cscale(t0, zeta - (T)1), zeta, t2);
   e[4] = caxpy(e[4], c2, v);
 }
 

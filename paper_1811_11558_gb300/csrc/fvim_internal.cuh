@@ -30,6 +30,10 @@ template <typename V> __device__ __forceinline__ V cmuli(V a) { return mk<V>(-a.
 template <typename V> __device__ __forceinline__ V caxpy(V a, decltype(V::x) s, V b) {
   return mk<V>(a.x + s * b.x, a.y + s * b.y);
 }
+// a + s*i*b (s real): two scalar multiply-adds, the swap and the sign folded into them
+template <typename V> __device__ __forceinline__ V caxpy_i(V a, decltype(V::x) s, V b) {
+  return mk<V>(a.x - s * b.y, a.y + s * b.x);
+}
 
 #if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000) && !defined(FVIM_NO_F32X2)
 // Blackwell packed FP32 pairs (add/sub/mul/fma .f32x2): one instruction per FP32 complex
