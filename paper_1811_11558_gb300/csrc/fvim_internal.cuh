@@ -104,12 +104,16 @@ template <typename V, bool INV>
 __device__ __forceinline__ void dft4(V* v) {
   V a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
   V b0 = cadd(v[1], v[3]), b1 = csub(v[1], v[3]);
-  // forward: W4 = -i ; inverse: +i
-  V b1r = INV ? cmuli(b1) : cscale(cmuli(b1), (decltype(V::x))-1);
   v[0] = cadd(a0, b0);
   v[2] = csub(a0, b0);
-  v[1] = cadd(a1, b1r);
-  v[3] = csub(a1, b1r);
+  // a1 -/+ i b1 (forward W4 = -i, inverse +i), the swap folded into the adds
+  if (INV) {
+    v[1] = mk<V>(a1.x - b1.y, a1.y + b1.x);
+    v[3] = mk<V>(a1.x + b1.y, a1.y - b1.x);
+  } else {
+    v[1] = mk<V>(a1.x + b1.y, a1.y - b1.x);
+    v[3] = mk<V>(a1.x - b1.y, a1.y + b1.x);
+  }
 }
 
 template <typename V, bool INV>
@@ -120,13 +124,18 @@ __device__ __forceinline__ void dft8(V* v) {
   V o[4] = {v[1], v[3], v[5], v[7]};
   dft4<V, INV>(e);
   dft4<V, INV>(o);
-  // twiddles W8^m, m = 0..3 (forward exp(-i pi m/4))
-  V w1 = INV ? mk<V>(r, r) : mk<V>(r, -r);
-  V w2 = INV ? mk<V>(0, 1) : mk<V>(0, -1);
-  V w3 = INV ? mk<V>(-r, r) : mk<V>(-r, -r);
-  o[1] = cmul(o[1], w1);
-  o[2] = cmul(o[2], w2);
-  o[3] = cmul(o[3], w3);
+  // twiddles W8^m, m = 0..3 (forward exp(-i pi m/4)): products by r(1 -/+ i), -/+ i and
+  // r(-1 -/+ i) written out (the zero parts of the twiddles cost nothing)
+  const V o1 = o[1], o2 = o[2], o3 = o[3];
+  if (INV) {
+    o[1] = mk<V>(r * (o1.x - o1.y), r * (o1.x + o1.y));
+    o[2] = mk<V>(-o2.y, o2.x);
+    o[3] = mk<V>(-r * (o3.x + o3.y), r * (o3.x - o3.y));
+  } else {
+    o[1] = mk<V>(r * (o1.x + o1.y), r * (o1.y - o1.x));
+    o[2] = mk<V>(o2.y, -o2.x);
+    o[3] = mk<V>(r * (o3.y - o3.x), -r * (o3.x + o3.y));
+  }
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     v[m] = cadd(e[m], o[m]);
