@@ -23,7 +23,7 @@ namespace {
 template <typename T>
 __global__ void k_return_map(const T* __restrict__ d_eps, const T* __restrict__ sig_n, const T* __restrict__ ep,
                              T* __restrict__ d_eps_p, T* __restrict__ d_ep, size_t nxy, size_t nvox, T lam, T mu,
-                             T sy, T Eh) {
+                             T sy, T Eh, int* __restrict__ zr) {
   const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= nvox) return;
   const size_t z = v / nxy, xy = v - z * nxy;
@@ -53,6 +53,17 @@ __global__ void k_return_map(const T* __restrict__ d_eps, const T* __restrict__ 
 #pragma unroll
   for (int c = 0; c < 6; ++c) d_eps_p[base + c * nxy] = k * s[c];
   if (d_ep) d_ep[v] = dEp;
+  // layer range of the flowing voxels (elsewhere d_eps_p is exactly zero): one pair of
+  // atomics per warp, over the lanes that flow
+  if (zr && dEp > 0) {
+    const unsigned am = __activemask();
+    const int zi = (int)z;
+    const int lo = __reduce_min_sync(am, zi), hi = __reduce_max_sync(am, zi);
+    if ((int)(threadIdx.x & 31) == __ffs(am) - 1) {
+      atomicMin(zr, lo);
+      atomicMax(zr + 1, hi + 1);
+    }
+  }
 }
 
 // S_{n+1} = S_n + increment (Sec. 4.2, update(S)).
@@ -177,7 +188,7 @@ template <typename T> int apply_mindlin_cluster(fvim_ctx* c, const T* eps_p, T* 
   }
 }
 
-template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, int kind, T* u3) {
+template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, int kind, T* u3, const int* zr) {
   int rc;
   int nk = 0;
   if (use_fft2_cluster(c)) {
@@ -189,9 +200,14 @@ template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, i
     c->last_kernels = nk;
     return FVIM_OK;
   }
-  if ((rc = timed(c, PROF_ROWS_FWD6, nk, [&] { return launch_rows_fwd6<T>(c, eps_p, 0, c->nz); }))) return rc;
-  if ((rc = timed(c, PROF_COLS_FWD, nk, [&] { return launch_cols<T>(c, false, c->spec, c->nz * 6); }))) return rc;
-  if ((rc = timed(c, PROF_MINDLIN_DEPTH, nk, [&] { return launch_mindlin_depth<T>(c, kind, u3 != nullptr); })))
+  // a known layer range of the input skips the forward passes of the empty layers (the
+  // Nyquist side array of those layers is left stale, so only for strain output)
+  const int* zin = kind == FVIM_STRAIN ? zr : nullptr;
+  if ((rc = timed(c, PROF_ROWS_FWD6, nk, [&] { return launch_rows_fwd6<T>(c, eps_p, 0, c->nz, zin); }))) return rc;
+  if ((rc = timed(c, PROF_COLS_FWD, nk, [&] { return launch_cols<T>(c, false, c->spec, c->nz * 6, zin); })))
+    return rc;
+  if ((rc = timed(c, PROF_MINDLIN_DEPTH, nk,
+                  [&] { return launch_mindlin_depth<T>(c, kind, u3 != nullptr, false, zin); })))
     return rc;
   if ((rc = timed(c, PROF_COLS_INV, nk, [&] { return launch_cols<T>(c, true, c->spec, c->nz * 6); }))) return rc;
   if ((rc = timed(c, PROF_ROWS_INV6, nk, [&] {
@@ -230,7 +246,7 @@ template <typename T> int apply_boussinesq_t(fvim_ctx* c, const T* p, T* u3, T* 
   return FVIM_OK;
 }
 
-template <typename T> int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep) {
+template <typename T> int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep, int* zr) {
   const size_t nv = nvox(c);
   const int threads = 256;
   const unsigned blocks = (unsigned)((nv + threads - 1) / threads);
@@ -238,7 +254,7 @@ template <typename T> int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, 
   const int rc = timed(c, PROF_RETURN_MAP, nk, [&] {
     k_return_map<T><<<blocks, threads, 0, c->stream>>>(d_eps, (const T*)c->st_sig, (const T*)c->st_ep, d_eps_p, d_ep,
                                                        (size_t)c->n1 * c->n2, nv, (T)c->lam, (T)c->mu,
-                                                       (T)c->sigma_y, (T)c->E_h);
+                                                       (T)c->sigma_y, (T)c->E_h, zr);
     FVIM_CUDA_CHECK_LAUNCH();
     return FVIM_OK;
   });
@@ -261,12 +277,12 @@ template <typename T> int commit_t(fvim_ctx* c, const T* d_eps, const T* d_eps_p
   return rc;
 }
 
-template int apply_mindlin_t<float>(fvim_ctx*, const float*, float*, int, float*);
-template int apply_mindlin_t<double>(fvim_ctx*, const double*, double*, int, double*);
+template int apply_mindlin_t<float>(fvim_ctx*, const float*, float*, int, float*, const int*);
+template int apply_mindlin_t<double>(fvim_ctx*, const double*, double*, int, double*, const int*);
 template int apply_boussinesq_t<float>(fvim_ctx*, const float*, float*, float*, int);
 template int apply_boussinesq_t<double>(fvim_ctx*, const double*, double*, double*, int);
-template int return_map_t<float>(fvim_ctx*, const float*, float*, float*);
-template int return_map_t<double>(fvim_ctx*, const double*, double*, double*);
+template int return_map_t<float>(fvim_ctx*, const float*, float*, float*, int*);
+template int return_map_t<double>(fvim_ctx*, const double*, double*, double*, int*);
 template int commit_t<float>(fvim_ctx*, const float*, const float*, const float*);
 template int commit_t<double>(fvim_ctx*, const double*, const double*, const double*);
 

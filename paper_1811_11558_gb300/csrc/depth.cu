@@ -283,7 +283,8 @@ __device__ __forceinline__ ModeGeom<T> mode_geom(int k1, int k2, int n2, T w1, T
 template <typename T, int KT, bool EIN>
 __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __restrict__ spec, typename Cx<T>::t* __restrict__ surf,
                                 const T* __restrict__ zn, int nz, int n2, int h1, int C, int nch, int prow, T w1,
-                                T w2, T lam, T mu, T nu, int out_kind, int want_u3, int uniform, T hz) {
+                                T w2, T lam, T mu, T nu, int out_kind, int want_u3, int uniform, T hz,
+                                const int* __restrict__ zr) {
   typedef typename Cx<T>::t V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* W = reinterpret_cast<V*>(smraw);                 // [nz][6][KT]
@@ -298,9 +299,13 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
 
   // 1. load the tile (coalesced KT-wide rows, every copy in flight before one wait) and
   //    the depth nodes
+  // (layers outside zr hold no input: their spectrum was not computed and reads as zero)
+  const int zlo = zr ? zr[0] : 0, zhi = zr ? zr[1] : nz;
   for (int idx = threadIdx.x; idx < nz * 6 * KT; idx += blockDim.x) {
     const int zc = idx / KT, j = idx & (KT - 1);
-    cp_async_cx(W + idx, spec + (size_t)zc * plane + colofs + j);
+    const int zl = zc / 6;
+    if (zl >= zlo && zl < zhi) cp_async_cx(W + idx, spec + (size_t)zc * plane + colofs + j);
+    else W[idx] = mk<V>(0, 0);
   }
   for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];
   cp_async_wait_all();
@@ -551,7 +556,7 @@ __global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* _
                                                             typename Cx<T>::t* __restrict__ surf,
                                                             const T* __restrict__ zn, int nz, int n2, int h1, int nch,
                                                             T w1, T w2, T lam, T mu, T nu, int out_kind, int want_u3,
-                                                            int uniform, T hz) {
+                                                            int uniform, T hz, const int* __restrict__ zr) {
   typedef typename Cx<T>::t V;
   static_assert(sizeof(V) == 8 && KT % 2 == 0, "FP32 tiles of an even width");
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -568,9 +573,17 @@ __global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* _
   const size_t colofs = (size_t)k2 * h1 + blockIdx.x * KT;
 
   // 1. load the tile (16-byte copies, two FP32 complex values each) and the depth nodes
+  // (layers outside zr hold no input: their spectrum was not computed and reads as zero)
+  const int zlo = zr ? zr[0] : 0, zhi = zr ? zr[1] : nz;
   for (int idx = threadIdx.x; idx < nz * 6 * (KT / 2); idx += blockDim.x) {
     const int zc = idx / (KT / 2), j = 2 * (idx % (KT / 2));
-    cp_async_16(W + zc * KT + j, spec + (size_t)zc * plane + colofs + j);
+    const int zl = zc / 6;
+    if (zl >= zlo && zl < zhi) {
+      cp_async_16(W + zc * KT + j, spec + (size_t)zc * plane + colofs + j);
+    } else {
+      W[zc * KT + j] = mk<V>(0, 0);
+      W[zc * KT + j + 1] = mk<V>(0, 0);
+    }
   }
   for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];
   cp_async_wait_all();
@@ -854,7 +867,8 @@ __global__ void k_boussinesq(typename Cx<T>::t* __restrict__ spec, typename Cx<T
 
 }  // namespace
 
-template <typename T> int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps_in) {
+template <typename T>
+int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps_in, const int* zr) {
   typedef typename Cx<T>::t V;
   const int nz = c->nz, h1 = c->h1, n2 = c->n2;
   int C = (nz + 15) / 16;
@@ -885,7 +899,7 @@ template <typename T> int launch_mindlin_depth(const fvim_ctx* c, int out_kind, 
     cudaFuncSetAttribute(k_mindlin_depth_r<T, 16, CV, EI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr); \
     k_mindlin_depth_r<T, 16, CV, EI><<<grid, 16 * nchr, smr, c->stream>>>(                                       \
         (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, n2, h1, nchr, w1, w2, (T)c->lam, (T)c->mu, (T)c->nu,  \
-        out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz);                                                        \
+        out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz, zr);                                                    \
   }
     DEPTHR(2, false) DEPTHR(3, false) DEPTHR(4, false) DEPTHR(6, false) DEPTHR(8, false)
     DEPTHR(2, true) DEPTHR(3, true) DEPTHR(4, true) DEPTHR(6, true) DEPTHR(8, true)
@@ -898,7 +912,7 @@ template <typename T> int launch_mindlin_depth(const fvim_ctx* c, int out_kind, 
     cudaFuncSetAttribute(k_mindlin_depth<T, KTV, EI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
     k_mindlin_depth<T, KTV, EI><<<grid, threads, smem, c->stream>>>(                                             \
         (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, n2, h1, C, nch, prow, w1, w2, (T)c->lam, (T)c->mu,   \
-        (T)c->nu, out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz);                                           \
+        (T)c->nu, out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz, zr);                                       \
   }
   DEPTH(16, false) DEPTH(8, false) DEPTH(4, false) DEPTH(2, false)
   DEPTH(16, true) DEPTH(8, true) DEPTH(4, true) DEPTH(2, true)
@@ -918,7 +932,7 @@ template <typename T> int launch_boussinesq(const fvim_ctx* c, int out_kind, boo
   return FVIM_OK;
 }
 
-template int launch_mindlin_depth<float>(const fvim_ctx*, int, bool, bool);
-template int launch_mindlin_depth<double>(const fvim_ctx*, int, bool, bool);
+template int launch_mindlin_depth<float>(const fvim_ctx*, int, bool, bool, const int*);
+template int launch_mindlin_depth<double>(const fvim_ctx*, int, bool, bool, const int*);
 template int launch_boussinesq<float>(const fvim_ctx*, int, bool, bool);
 template int launch_boussinesq<double>(const fvim_ctx*, int, bool, bool);

@@ -444,10 +444,10 @@ inline int r8_rows(int n1, int n2) {
   return rb;
 }
 
-template <typename T> int launch_rows_fwd6(const fvim_ctx* c, const T* eps_p, int z0, int nzs) {
+template <typename T> int launch_rows_fwd6(const fvim_ctx* c, const T* eps_p, int z0, int nzs, const int* zr) {
   typedef typename Cx<T>::t V;
   const int n1 = c->n1, n2 = c->n2;
-  if (launch_rows_fwd6_ct<T>(c, eps_p, z0, nzs)) {
+  if (launch_rows_fwd6_ct<T>(c, eps_p, z0, nzs, zr)) {
     FVIM_CUDA_CHECK_LAUNCH();
     return FVIM_OK;
   }
@@ -502,10 +502,10 @@ template <typename T> int launch_rows_fwd1(const fvim_ctx* c, const T* f) {
   return FVIM_OK;
 }
 
-template <typename T> int launch_cols(const fvim_ctx* c, bool inverse, void* planes, int nplanes) {
+template <typename T> int launch_cols(const fvim_ctx* c, bool inverse, void* planes, int nplanes, const int* zr) {
   typedef typename Cx<T>::t V;
   const int n2 = c->n2, h1 = c->h1;
-  if (launch_cols_ct<T>(c, inverse, planes, nplanes)) {
+  if (launch_cols_ct<T>(c, inverse, planes, nplanes, zr)) {
     FVIM_CUDA_CHECK_LAUNCH();
     return FVIM_OK;
   }
@@ -609,12 +609,12 @@ template <typename T> int launch_rows_inv1(const fvim_ctx* c, T* f) {
   return FVIM_OK;
 }
 
-template int launch_rows_fwd6<float>(const fvim_ctx*, const float*, int, int);
-template int launch_rows_fwd6<double>(const fvim_ctx*, const double*, int, int);
+template int launch_rows_fwd6<float>(const fvim_ctx*, const float*, int, int, const int*);
+template int launch_rows_fwd6<double>(const fvim_ctx*, const double*, int, int, const int*);
 template int launch_rows_fwd1<float>(const fvim_ctx*, const float*);
 template int launch_rows_fwd1<double>(const fvim_ctx*, const double*);
-template int launch_cols<float>(const fvim_ctx*, bool, void*, int);
-template int launch_cols<double>(const fvim_ctx*, bool, void*, int);
+template int launch_cols<float>(const fvim_ctx*, bool, void*, int, const int*);
+template int launch_cols<double>(const fvim_ctx*, bool, void*, int, const int*);
 template int launch_rows_inv6<float>(const fvim_ctx*, float*, float, int, int);
 template int launch_rows_inv6<double>(const fvim_ctx*, double*, double, int, int);
 template int launch_rows_inv1<float>(const fvim_ctx*, float*);

@@ -35,8 +35,10 @@ template <typename V> struct RowSm {
 
 template <typename T, bool INV, int N>
 __global__ void __launch_bounds__(512) k_cols_ct(typename Cx<T>::t* __restrict__ planes,
-                                                 const typename Cx<T>::t* __restrict__ tw, int h1, int kc) {
+                                                 const typename Cx<T>::t* __restrict__ tw, int h1, int kc,
+                                                 const int* __restrict__ zr) {
   typedef typename Cx<T>::t V;
+  if (zr && ((int)blockIdx.y / 6 < zr[0] || (int)blockIdx.y / 6 >= zr[1])) return;  // layer without input
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int T8 = N / 8;
   const int f = threadIdx.x % kc, t = threadIdx.x / kc;
@@ -62,7 +64,8 @@ struct ColPairSm {
 
 template <bool INV, int N>
 __global__ void __launch_bounds__(N / 2) k_cols_v(float2* __restrict__ planes, const float2* __restrict__ tw,
-                                                  int h1) {
+                                                  int h1, const int* __restrict__ zr) {
+  if (zr && ((int)blockIdx.y / 6 < zr[0] || (int)blockIdx.y / 6 >= zr[1])) return;  // layer without input
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);  // [N][8]
   constexpr int T8 = N / 8;
@@ -94,12 +97,13 @@ __device__ __forceinline__ void split_pair_ct(V zk, V zmk, V& A, V& B) {
 template <typename T, int N>
 __global__ void __launch_bounds__(256) k_rows_fwd6_ct(const T* __restrict__ eps_p, typename Cx<T>::t* __restrict__ spec,
                                                       T* __restrict__ nq, const typename Cx<T>::t* __restrict__ tw,
-                                                      int n2, int rb, int z0, T lam, T mu) {
+                                                      int n2, int rb, int z0, T lam, T mu, const int* __restrict__ zr) {
   typedef typename Cx<T>::t V;
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int T8 = N / 8, LD = N + N / 8, H1 = N / 2;
   const int r = threadIdx.x / T8, t = threadIdx.x % T8;
   const int z = z0 + blockIdx.y;
+  if (zr && (z < zr[0] || z >= zr[1])) return;  // layer without input
   const int x2 = blockIdx.x * rb + r;
   V v[3][8];
 #pragma unroll
@@ -191,11 +195,12 @@ __global__ void __launch_bounds__(256) k_rows_inv6_ct(const typename Cx<T>::t* _
 template <int N>
 __global__ void __launch_bounds__(256) k_rows_fwd6_v(const float* __restrict__ eps_p, float2* __restrict__ spec,
                                                      float* __restrict__ nq, const float2* __restrict__ tw, int n2,
-                                                     int rb, int z0, float lam, float mu) {
+                                                     int rb, int z0, float lam, float mu, const int* __restrict__ zr) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int T8 = N / 8, LD = N + N / 8, H1 = N / 2;
   const int r = threadIdx.x / T8, t = threadIdx.x % T8;
   const int z = z0 + blockIdx.y;
+  if (zr && (z < zr[0] || z >= zr[1])) return;  // layer without input
   const int x2b = blockIdx.x * rb, x2 = x2b + r;
   float* stg = reinterpret_cast<float*>(smraw);  // [6][rb][N]
   const int per_c = rb * N / 4;
@@ -254,7 +259,7 @@ inline int ct_rows(int n1, int n2) {
   return rb;
 }
 
-template <typename T, int N> void cols_n(const fvim_ctx* c, bool inverse, void* planes, int nplanes) {
+template <typename T, int N> void cols_n(const fvim_ctx* c, bool inverse, void* planes, int nplanes, const int* zr) {
   typedef typename Cx<T>::t V;
   if constexpr (sizeof(T) == 4 && N >= 64) {
     if (c->h1 % 8 == 0) {
@@ -262,10 +267,10 @@ template <typename T, int N> void cols_n(const fvim_ctx* c, bool inverse, void* 
       const size_t sm = (size_t)N * 8 * sizeof(float2);
       if (inverse) {
         smem_attr(k_cols_v<true, N>, sm);
-        k_cols_v<true, N><<<grid, N / 2, sm, c->stream>>>((float2*)planes, (const float2*)c->tw2, c->h1);
+        k_cols_v<true, N><<<grid, N / 2, sm, c->stream>>>((float2*)planes, (const float2*)c->tw2, c->h1, zr);
       } else {
         smem_attr(k_cols_v<false, N>, sm);
-        k_cols_v<false, N><<<grid, N / 2, sm, c->stream>>>((float2*)planes, (const float2*)c->tw2, c->h1);
+        k_cols_v<false, N><<<grid, N / 2, sm, c->stream>>>((float2*)planes, (const float2*)c->tw2, c->h1, zr);
       }
       return;
     }
@@ -278,14 +283,14 @@ template <typename T, int N> void cols_n(const fvim_ctx* c, bool inverse, void* 
   dim3 grid(c->h1 / kc, nplanes);
   if (inverse) {
     smem_attr(k_cols_ct<T, true, N>, smem);
-    k_cols_ct<T, true, N><<<grid, threads, smem, c->stream>>>((V*)planes, (const V*)c->tw2, c->h1, kc);
+    k_cols_ct<T, true, N><<<grid, threads, smem, c->stream>>>((V*)planes, (const V*)c->tw2, c->h1, kc, zr);
   } else {
     smem_attr(k_cols_ct<T, false, N>, smem);
-    k_cols_ct<T, false, N><<<grid, threads, smem, c->stream>>>((V*)planes, (const V*)c->tw2, c->h1, kc);
+    k_cols_ct<T, false, N><<<grid, threads, smem, c->stream>>>((V*)planes, (const V*)c->tw2, c->h1, kc, zr);
   }
 }
 
-template <typename T, int N> void rows_fwd_n(const fvim_ctx* c, const T* eps_p, int z0, int nzs) {
+template <typename T, int N> void rows_fwd_n(const fvim_ctx* c, const T* eps_p, int z0, int nzs, const int* zr) {
   typedef typename Cx<T>::t V;
   const int rb = ct_rows(N, c->n2);
   if constexpr (sizeof(T) == 4 && N >= 64) {
@@ -294,14 +299,14 @@ template <typename T, int N> void rows_fwd_n(const fvim_ctx* c, const T* eps_p, 
     smem_attr(k_rows_fwd6_v<N>, sm);
     k_rows_fwd6_v<N><<<grid, rb * (N / 8), sm, c->stream>>>((const float*)eps_p, (float2*)c->spec, (float*)c->nq,
                                                             (const float2*)c->tw1, c->n2, rb, z0, (float)c->lam,
-                                                            (float)c->mu);
+                                                            (float)c->mu, zr);
     return;
   }
   const size_t smem = (size_t)rb * 3 * (N + N / 8) * sizeof(V);
   dim3 grid(c->n2 / rb, nzs);
   smem_attr(k_rows_fwd6_ct<T, N>, smem);
   k_rows_fwd6_ct<T, N><<<grid, rb * (N / 8), smem, c->stream>>>(eps_p, (V*)c->spec, (T*)c->nq, (const V*)c->tw1,
-                                                              c->n2, rb, z0, (T)c->lam, (T)c->mu);
+                                                              c->n2, rb, z0, (T)c->lam, (T)c->mu, zr);
 }
 
 template <typename T, int N> void rows_inv_n(const fvim_ctx* c, T* out, T nq_scale, int z0, int nzs) {
@@ -319,10 +324,10 @@ template <typename T, int N> void rows_inv_n(const fvim_ctx* c, T* out, T nq_sca
 
 #define FVIM_CT_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
 
-template <typename T> bool launch_cols_ct(const fvim_ctx* c, bool inverse, void* planes, int nplanes) {
+template <typename T> bool launch_cols_ct(const fvim_ctx* c, bool inverse, void* planes, int nplanes, const int* zr) {
 #define CASE(N)                                 \
   if (c->n2 == N) {                             \
-    cols_n<T, N>(c, inverse, planes, nplanes);  \
+    cols_n<T, N>(c, inverse, planes, nplanes, zr); \
     return true;                                \
   }
   FVIM_CT_SIZES(CASE)
@@ -330,10 +335,10 @@ template <typename T> bool launch_cols_ct(const fvim_ctx* c, bool inverse, void*
   return false;
 }
 
-template <typename T> bool launch_rows_fwd6_ct(const fvim_ctx* c, const T* eps_p, int z0, int nzs) {
+template <typename T> bool launch_rows_fwd6_ct(const fvim_ctx* c, const T* eps_p, int z0, int nzs, const int* zr) {
 #define CASE(N)                              \
   if (c->n1 == N) {                          \
-    rows_fwd_n<T, N>(c, eps_p, z0, nzs);     \
+    rows_fwd_n<T, N>(c, eps_p, z0, nzs, zr); \
     return true;                             \
   }
   FVIM_CT_SIZES(CASE)
@@ -352,9 +357,9 @@ template <typename T> bool launch_rows_inv6_ct(const fvim_ctx* c, T* out, T nq_s
   return false;
 }
 
-template bool launch_cols_ct<float>(const fvim_ctx*, bool, void*, int);
-template bool launch_cols_ct<double>(const fvim_ctx*, bool, void*, int);
-template bool launch_rows_fwd6_ct<float>(const fvim_ctx*, const float*, int, int);
-template bool launch_rows_fwd6_ct<double>(const fvim_ctx*, const double*, int, int);
+template bool launch_cols_ct<float>(const fvim_ctx*, bool, void*, int, const int*);
+template bool launch_cols_ct<double>(const fvim_ctx*, bool, void*, int, const int*);
+template bool launch_rows_fwd6_ct<float>(const fvim_ctx*, const float*, int, int, const int*);
+template bool launch_rows_fwd6_ct<double>(const fvim_ctx*, const double*, int, int, const int*);
 template bool launch_rows_inv6_ct<float>(const fvim_ctx*, float*, float, int, int);
 template bool launch_rows_inv6_ct<double>(const fvim_ctx*, double*, double, int, int);

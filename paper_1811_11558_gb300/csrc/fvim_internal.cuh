@@ -406,13 +406,16 @@ template <typename T> struct Mat {
 };
 
 // launchers (defined in the .cu files, instantiated for float and double)
-template <typename T> int launch_rows_fwd6(const fvim_ctx* c, const T* eps_p, int z0, int nzs);
+// zr (device, two ints) or NULL: only layers zr[0] <= z < zr[1] hold non-zero input; the forward
+// passes skip the others and the depth kernel reads them as zero
+template <typename T> int launch_rows_fwd6(const fvim_ctx* c, const T* eps_p, int z0, int nzs, const int* zr = nullptr);
 template <typename T> int launch_rows_fwd1(const fvim_ctx* c, const T* f);
-template <typename T> int launch_cols(const fvim_ctx* c, bool inverse, void* planes, int nplanes);
+template <typename T> int launch_cols(const fvim_ctx* c, bool inverse, void* planes, int nplanes, const int* zr = nullptr);
 template <typename T> int launch_rows_inv6(const fvim_ctx* c, T* out, T nq_scale, int z0, int nzs);
 template <typename T> int launch_rows_inv1(const fvim_ctx* c, T* f);
 // eps_in: the spectrum holds eps_p (Hooke's law applied per mode) instead of w = C:eps_p
-template <typename T> int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps_in = false);
+template <typename T>
+int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps_in = false, const int* zr = nullptr);
 template <typename T> int launch_boussinesq(const fvim_ctx* c, int out_kind, bool want_vol, bool want_u3);
 template <typename T> int launch_return_map(const fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep);
 template <typename T> int launch_commit(const fvim_ctx* c, const T* d_eps, const T* d_eps_p, const T* d_ep);
@@ -428,14 +431,17 @@ int launch_fft2_fwd_cluster(const fvim_ctx* c, const float* src);
 int launch_fft2_inv_cluster(const fvim_ctx* c, float* out, int nq_mode, float nq_scale);
 
 // compile-time-length FFT kernels (fft_ct.cu); false when the length has no variant
-template <typename T> bool launch_cols_ct(const fvim_ctx* c, bool inverse, void* planes, int nplanes);
-template <typename T> bool launch_rows_fwd6_ct(const fvim_ctx* c, const T* eps_p, int z0, int nzs);
+template <typename T> bool launch_cols_ct(const fvim_ctx* c, bool inverse, void* planes, int nplanes, const int* zr = nullptr);
+template <typename T> bool launch_rows_fwd6_ct(const fvim_ctx* c, const T* eps_p, int z0, int nzs, const int* zr = nullptr);
 template <typename T> bool launch_rows_inv6_ct(const fvim_ctx* c, T* out, T nq_scale, int z0, int nzs);
 
 // launch sequences of the entry points (capi.cu), used by the solvers
-template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, int kind, T* u3);
+// zr: see launch_rows_fwd6; honoured for FVIM_STRAIN output only
+template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, int kind, T* u3, const int* zr = nullptr);
 template <typename T> int apply_boussinesq_t(fvim_ctx* c, const T* p, T* u3, T* vol, int kind);
-template <typename T> int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep);
+// zr (device, two ints) or NULL: receives the layer range [zr[0], zr[1]) of the voxels that
+// flow (reset by the caller to {INT_MAX-ish, 0} first)
+template <typename T> int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep, int* zr = nullptr);
 template <typename T> int commit_t(fvim_ctx* c, const T* d_eps, const T* d_eps_p, const T* d_ep);
 
 // true when e is an error; the error is kept as this host thread's last CUDA error

@@ -461,6 +461,19 @@ struct PKS {
 };
 static_assert(sizeof(PKS) <= 128, "the DF-SANE step is kept at byte 128 of the scalar block");
 
+// layer range [zr[0], zr[1]) of the voxels that flow in the last return map (byte 200 of the
+// scalar block), reset before each return map; the Mindlin apply of the plastic strain
+// increment skips the forward transforms of the other layers, where the increment is zero
+// (the layer-level form of the sparse plastic support noted in Sec. 3.2)
+inline int* flow_range(fvim_ctx* c) { return reinterpret_cast<int*>(static_cast<char*>(c->sv[V_PKS]) + 200); }
+inline int reset_flow_range(fvim_ctx* c) {
+  int* zr = flow_range(c);
+  if (FVIM_CU(cudaMemsetAsync(zr, 0x7f, sizeof(int), c->stream)) ||
+      FVIM_CU(cudaMemsetAsync(zr + 1, 0, sizeof(int), c->stream)))
+    return FVIM_ERR_CUDA;
+  return FVIM_OK;
+}
+
 // sum the partials [nblk][NV] of a reduction grid in a fixed order (one block)
 template <int NV> __device__ __forceinline__ void fin_sum(const double* part, int nblk, double (&out)[NV]) {
   __shared__ double sh[NV][RT];
@@ -751,8 +764,9 @@ template <typename T> struct DF {
   int eval(const T* x, T* Fx, double* f) {
     auto seq = [&]() -> int {
       int r;
-      if ((r = return_map_t<T>(c, x, S<T>(c, V_DEP), S<T>(c, V_EP)))) return r;
-      if ((r = apply_mindlin_t<T>(c, S<T>(c, V_DEP), S<T>(c, V_TMP), FVIM_STRAIN, nullptr))) return r;
+      if ((r = reset_flow_range(c))) return r;
+      if ((r = return_map_t<T>(c, x, S<T>(c, V_DEP), S<T>(c, V_EP), flow_range(c)))) return r;
+      if ((r = apply_mindlin_t<T>(c, S<T>(c, V_DEP), S<T>(c, V_TMP), FVIM_STRAIN, nullptr, flow_range(c)))) return r;
       k_df_res<T><<<grd, RT, 0, c->stream>>>(x, S<T>(c, V_B), S<T>(c, V_TMP), Fx, (const double*)c->sv[V_WZ], lgxy,
                                             n, (double*)c->sv[V_PART]);
       FVIM_CUDA_CHECK_LAUNCH();
@@ -861,7 +875,9 @@ int plasticity_t(fvim_ctx* c, const T* dT, T* dE, T* deps_p, T* dep, const fvim_
   // outputs: dE = x and its return map
   if (FVIM_CU(cudaMemcpyAsync(dE, x, n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream))) return FVIM_ERR_CUDA;
   if (deps_p || dep) {
-    if ((rc = return_map_t<T>(c, x, deps_p ? deps_p : S<T>(c, V_DEP), dep ? dep : S<T>(c, V_EP)))) return rc;
+    if ((rc = reset_flow_range(c))) return rc;
+    if ((rc = return_map_t<T>(c, x, deps_p ? deps_p : S<T>(c, V_DEP), dep ? dep : S<T>(c, V_EP), flow_range(c))))
+      return rc;
   }
   if (iters) *iters = k;
   if (res) *res = sqrt(f);
@@ -909,7 +925,8 @@ int solve_contact_t(fvim_ctx* c, const T* h, const double* loads, int n_inc, con
       if (rep) { rep->df_iters += dfi; rep->residual_evals += ev; }
       if (rc && rc != FVIM_ERR_NOT_CONVERGED) return rc;
       // dU = N[C:deps_p].e3 at z = 0
-      if ((rc = apply_mindlin_t<T>(c, S<T>(c, V_DEP), S<T>(c, V_TMP), FVIM_STRAIN, dU))) return rc;
+      // V_DEP is the increment of the last return map, whose flow range is current
+      if ((rc = apply_mindlin_t<T>(c, S<T>(c, V_DEP), S<T>(c, V_TMP), FVIM_STRAIN, dU, flow_range(c)))) return rc;
       c->n_applies++;
       k_diff2<T><<<gs, RT, 0, c->stream>>>(dU, dUp, ns, (double*)c->sv[V_PART]);
       FVIM_CUDA_CHECK_LAUNCH();
