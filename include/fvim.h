@@ -24,6 +24,8 @@
  *   return FVIM_OK or a negative status.
  * - Pressure p >= 0 pushes into the body (a force p e3 per unit area, Sec. 1.1),
  *   so sigma_33 = -p on the surface; u3 > 0 is a displacement into the body.
+ * - A context is used by one host thread at a time; different contexts may be used from
+ *   different threads at once (each solver call runs on the context's own stream).
  */
 #ifndef FVIM_H
 #define FVIM_H

@@ -23,6 +23,7 @@ namespace {
 constexpr int RT = 256;       // threads of a reduction block
 constexpr int RMAXB = 1024;   // blocks of a reduction grid
 constexpr int NVMAX = 2;      // values reduced per pass
+constexpr size_t kScalarBlock = 256;  // bytes of the solver's device scalar block (V_PKS)
 
 // surface buffers [N2][N1]
 enum { S_P = 0, S_POLD, S_T, S_G, S_U, S_R, S_H, S_H0, S_DU, S_DUPREV, S_TPREV, S_DT, S_NSURF };
@@ -42,7 +43,7 @@ template <typename T> int ensure_ws(fvim_ctx* c) {
   if (FVIM_CU(cudaMalloc(&c->sv[V_EP], nv * sizeof(T)))) return FVIM_ERR_OOM;
   if (FVIM_CU(cudaMalloc(&c->sv[V_PART], (size_t)RMAXB * NVMAX * sizeof(double)))) return FVIM_ERR_OOM;
   if (FVIM_CU(cudaMalloc(&c->sv[V_WZ], (size_t)c->nz * sizeof(double)))) return FVIM_ERR_OOM;
-  if (FVIM_CU(cudaMalloc(&c->sv[V_PKS], 256))) return FVIM_ERR_OOM;
+  if (FVIM_CU(cudaMalloc(&c->sv[V_PKS], kScalarBlock))) return FVIM_ERR_OOM;
   if (FVIM_CU(cudaMallocHost(&c->h_part, (size_t)RMAXB * NVMAX * sizeof(double) + 256))) {
     c->h_part = nullptr;
     return FVIM_ERR_OOM;
@@ -465,6 +466,7 @@ static_assert(sizeof(PKS) <= 128, "the DF-SANE step is kept at byte 128 of the s
 // scalar block), reset before each return map; the Mindlin apply of the plastic strain
 // increment skips the forward transforms of the other layers, where the increment is zero
 // (the layer-level form of the sparse plastic support noted in Sec. 3.2)
+static_assert(200 + 2 * sizeof(int) <= kScalarBlock, "flow range inside the scalar block");
 inline int* flow_range(fvim_ctx* c) { return reinterpret_cast<int*>(static_cast<char*>(c->sv[V_PKS]) + 200); }
 inline int reset_flow_range(fvim_ctx* c) {
   int* zr = flow_range(c);
