@@ -23,7 +23,8 @@ namespace {
 template <typename T>
 __global__ void k_return_map(const T* __restrict__ d_eps, const T* __restrict__ sig_n, const T* __restrict__ ep,
                              T* __restrict__ d_eps_p, T* __restrict__ d_ep, size_t nxy, size_t nvox, T lam, T mu,
-                             T sy, T Eh, int* __restrict__ zr) {
+                             T sy, T Eh, int* __restrict__ zr, const void* const* d_eps_at) {
+  if (d_eps_at) d_eps = static_cast<const T*>(*d_eps_at);  // input chosen on the device
   const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= nvox) return;
   const size_t z = v / nxy, xy = v - z * nxy;
@@ -246,7 +247,8 @@ template <typename T> int apply_boussinesq_t(fvim_ctx* c, const T* p, T* u3, T* 
   return FVIM_OK;
 }
 
-template <typename T> int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep, int* zr) {
+template <typename T>
+int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep, int* zr, const void* const* d_eps_at) {
   const size_t nv = nvox(c);
   const int threads = 256;
   const unsigned blocks = (unsigned)((nv + threads - 1) / threads);
@@ -254,7 +256,7 @@ template <typename T> int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, 
   const int rc = timed(c, PROF_RETURN_MAP, nk, [&] {
     k_return_map<T><<<blocks, threads, 0, c->stream>>>(d_eps, (const T*)c->st_sig, (const T*)c->st_ep, d_eps_p, d_ep,
                                                        (size_t)c->n1 * c->n2, nv, (T)c->lam, (T)c->mu,
-                                                       (T)c->sigma_y, (T)c->E_h, zr);
+                                                       (T)c->sigma_y, (T)c->E_h, zr, d_eps_at);
     FVIM_CUDA_CHECK_LAUNCH();
     return FVIM_OK;
   });
@@ -281,8 +283,8 @@ template int apply_mindlin_t<float>(fvim_ctx*, const float*, float*, int, float*
 template int apply_mindlin_t<double>(fvim_ctx*, const double*, double*, int, double*, const int*);
 template int apply_boussinesq_t<float>(fvim_ctx*, const float*, float*, float*, int);
 template int apply_boussinesq_t<double>(fvim_ctx*, const double*, double*, double*, int);
-template int return_map_t<float>(fvim_ctx*, const float*, float*, float*, int*);
-template int return_map_t<double>(fvim_ctx*, const double*, double*, double*, int*);
+template int return_map_t<float>(fvim_ctx*, const float*, float*, float*, int*, const void* const*);
+template int return_map_t<double>(fvim_ctx*, const double*, double*, double*, int*, const void* const*);
 template int commit_t<float>(fvim_ctx*, const float*, const float*, const float*);
 template int commit_t<double>(fvim_ctx*, const double*, const double*, const double*);
 

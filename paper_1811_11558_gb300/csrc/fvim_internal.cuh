@@ -360,7 +360,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
-#define FVIM_NSOLVER_BUFS 24
+#define FVIM_NSOLVER_BUFS 26
 
 struct fvim_ctx {
   int n1, n2, nz, h1;
@@ -440,8 +440,11 @@ template <typename T> bool launch_rows_inv6_ct(const fvim_ctx* c, T* out, T nq_s
 template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, int kind, T* u3, const int* zr = nullptr);
 template <typename T> int apply_boussinesq_t(fvim_ctx* c, const T* p, T* u3, T* vol, int kind);
 // zr (device, two ints) or NULL: receives the layer range [zr[0], zr[1]) of the voxels that
-// flow (reset by the caller to {INT_MAX-ish, 0} first)
-template <typename T> int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep, int* zr = nullptr);
+// flow (reset by the caller to {INT_MAX-ish, 0} first).  d_eps_at (device) or NULL: a device
+// word holding the input pointer, read by the kernel in place of d_eps.
+template <typename T>
+int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep, int* zr = nullptr,
+                 const void* const* d_eps_at = nullptr);
 template <typename T> int commit_t(fvim_ctx* c, const T* d_eps, const T* d_eps_p, const T* d_ep);
 
 // true when e is an error; the error is kept as this host thread's last CUDA error

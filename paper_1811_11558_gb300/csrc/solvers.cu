@@ -24,11 +24,12 @@ constexpr int RT = 256;       // threads of a reduction block
 constexpr int RMAXB = 1024;   // blocks of a reduction grid
 constexpr int NVMAX = 2;      // values reduced per pass
 constexpr size_t kScalarBlock = 256;  // bytes of the solver's device scalar block (V_PKS)
+constexpr size_t kDfsBytes = 1024;     // bytes of the device DF-SANE state (V_DFS)
 
 // surface buffers [N2][N1]
 enum { S_P = 0, S_POLD, S_T, S_G, S_U, S_R, S_H, S_H0, S_DU, S_DUPREV, S_TPREV, S_DT, S_NSURF };
 // volume buffers [Nz][6][N2][N1] and the scalar field [Nz][N2][N1]
-enum { V_X = S_NSURF, V_F, V_XT, V_FT, V_B, V_DEP, V_TMP, V_DE, V_EP, V_PART, V_WZ, V_PKS, V_END };
+enum { V_X = S_NSURF, V_F, V_XT, V_FT, V_B, V_DEP, V_TMP, V_DE, V_EP, V_PART, V_WZ, V_PKS, V_DFS, V_END };
 static_assert(V_END <= FVIM_NSOLVER_BUFS, "workspace slots");
 
 template <typename T> size_t esz() { return sizeof(T); }
@@ -44,7 +45,8 @@ template <typename T> int ensure_ws(fvim_ctx* c) {
   if (FVIM_CU(cudaMalloc(&c->sv[V_PART], (size_t)RMAXB * NVMAX * sizeof(double)))) return FVIM_ERR_OOM;
   if (FVIM_CU(cudaMalloc(&c->sv[V_WZ], (size_t)c->nz * sizeof(double)))) return FVIM_ERR_OOM;
   if (FVIM_CU(cudaMalloc(&c->sv[V_PKS], kScalarBlock))) return FVIM_ERR_OOM;
-  if (FVIM_CU(cudaMallocHost(&c->h_part, (size_t)RMAXB * NVMAX * sizeof(double) + 256))) {
+  if (FVIM_CU(cudaMalloc(&c->sv[V_DFS], kDfsBytes))) return FVIM_ERR_OOM;
+  if (FVIM_CU(cudaMallocHost(&c->h_part, (size_t)RMAXB * NVMAX * sizeof(double) + 256 + kDfsBytes))) {
     c->h_part = nullptr;
     return FVIM_ERR_OOM;
   }
@@ -81,6 +83,8 @@ struct SolverRT {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   std::vector<std::pair<GraphKey, cudaGraphExec_t>> cg, df;  // CG batches, residual evaluations
+  cudaGraphExec_t dfloop = nullptr;                          // device DF-SANE loop (WHILE node)
+  bool dfloop_failed = false;                                // building it failed: host loop
 };
 constexpr size_t kMaxGraphs = 8;
 
@@ -783,6 +787,271 @@ template <typename T> struct DF {
   }
 };
 
+// ---- DF-SANE iterations on the device ---------------------------------------------------
+// The loop below the initial evaluations runs as one CUDA graph: a WHILE node whose body is
+// one trial evaluation (trial point, return map, Mindlin apply, residual norm, <s,s> and
+// <s,y>) followed by a one-thread kernel that takes the host loop's decisions (accept the
+// trial, try the opposite direction, shrink both steps, update sigma and the history, test
+// convergence, stagnation and the caps) and sets the loop condition.  The current point and
+// the trial point swap roles through pointers held in device memory.  Every decision uses the
+// same formulas and FP64 values as the host loop; the trial count is capped, so the loop ends.
+struct DFS {
+  const void* px[2];  // the two point buffers: x = px[cur], trial = px[1 - cur]
+  void* pF[2];        // their residuals
+  const void* xtr;    // px[1 - cur] (read by the return map)
+  double f, nF0, fmax, eta, ap, am, fp, fm, ftrial, best_old, tol_abs, tol_rel, gamma, smin, smax, tmin, tmax;
+  double sy[2];
+  double hist[32];    // ring of the accepted residuals, hist[i & 31] for i < len
+  int len, k, bt, phase, done, conv, bad, cur, trials, max_iter, max_trials, evals;
+};
+static_assert(sizeof(DFS) <= kDfsBytes, "device DF-SANE state");
+constexpr int kDfsM = 10, kDfsStag = 30;
+
+// trial = x + coef F, coef = -ap sigma (phase 0) or +am sigma (phase 1)
+template <typename T>
+__global__ void k_dfd_trial(const DFS* __restrict__ s, const double* __restrict__ dsig, size_t n) {
+  const int cur = s->cur;
+  const T* a = static_cast<const T*>(s->px[cur]);
+  const T* b = static_cast<const T*>(s->pF[cur]);
+  T* dst = const_cast<T*>(static_cast<const T*>(s->px[1 - cur]));
+  const double coef = (s->phase == 0 ? -s->ap : s->am) * *dsig;
+  if constexpr (sizeof(T) == 4) {
+    const float cf = (float)coef;
+    for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < (n >> 2); i += (size_t)gridDim.x * RT) {
+      const float4 x = reinterpret_cast<const float4*>(a)[i];
+      const float4 y = reinterpret_cast<const float4*>(b)[i];
+      reinterpret_cast<float4*>(dst)[i] =
+          make_float4(fmaf(cf, y.x, x.x), fmaf(cf, y.y, x.y), fmaf(cf, y.z, x.z), fmaf(cf, y.w, x.w));
+    }
+  } else {
+    for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) dst[i] = a[i] + coef * b[i];
+  }
+}
+
+// residual of the trial point into its residual buffer; ||F||^2 into s->ftrial (last block)
+template <typename T>
+__global__ void k_dfd_res(DFS* s, const T* __restrict__ b, const T* __restrict__ tmp, const double* __restrict__ wz,
+                          int lgxy, size_t n, double* part, unsigned* cnt) {
+  const int cur = s->cur;
+  const T* x = static_cast<const T*>(s->px[1 - cur]);
+  T* F = static_cast<T*>(s->pF[1 - cur]);
+  double v[1] = {0};
+  if constexpr (sizeof(T) == 4) {
+    const size_t n4 = n >> 2;
+    const int lg4 = lgxy - 2;
+    for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n4; i += (size_t)gridDim.x * RT) {
+      const float4 a = reinterpret_cast<const float4*>(x)[i];
+      const float4 c = reinterpret_cast<const float4*>(b)[i];
+      const float4 d = reinterpret_cast<const float4*>(tmp)[i];
+      const float4 f = make_float4(a.x - c.x - d.x, a.y - c.y - d.y, a.z - c.z - d.z, a.w - c.w - d.w);
+      reinterpret_cast<float4*>(F)[i] = f;
+      const float q = f.x * f.x + f.y * f.y + f.z * f.z + f.w * f.w;
+      v[0] += plane_weight(wz, (unsigned)(i >> lg4)) * (double)q;
+    }
+  } else {
+    for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
+      const T f = x[i] - b[i] - tmp[i];
+      F[i] = f;
+      v[0] += plane_weight(wz, (unsigned)(i >> lgxy)) * (double)f * (double)f;
+    }
+  }
+  block_reduce<1>(v, part);
+  if (last_block(cnt)) {
+    double t[1];
+    fin_sum<1>(part, gridDim.x, t);
+    if (threadIdx.x == 0) s->ftrial = t[0];
+    rearm(cnt);
+  }
+}
+
+// <s, s> and <s, y> of the trial (s = trial - x, y = F(trial) - F(x)) into s->sy (last block)
+template <typename T>
+__global__ void k_dfd_sy(DFS* s, const double* __restrict__ wz, int lgxy, size_t n, double* part, unsigned* cnt) {
+  const int cur = s->cur;
+  const T* x = static_cast<const T*>(s->px[cur]);
+  const T* xn = static_cast<const T*>(s->px[1 - cur]);
+  const T* F = static_cast<const T*>(s->pF[cur]);
+  const T* Fn = static_cast<const T*>(s->pF[1 - cur]);
+  double v[2] = {0, 0};
+  if constexpr (sizeof(T) == 4) {
+    const size_t n4 = n >> 2;
+    const int lg4 = lgxy - 2;
+    for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n4; i += (size_t)gridDim.x * RT) {
+      const float4 a = reinterpret_cast<const float4*>(x)[i];
+      const float4 an = reinterpret_cast<const float4*>(xn)[i];
+      const float4 f = reinterpret_cast<const float4*>(F)[i];
+      const float4 fn = reinterpret_cast<const float4*>(Fn)[i];
+      const float s0 = an.x - a.x, s1 = an.y - a.y, s2 = an.z - a.z, s3 = an.w - a.w;
+      const float y0 = fn.x - f.x, y1 = fn.y - f.y, y2 = fn.z - f.z, y3 = fn.w - f.w;
+      const double w = plane_weight(wz, (unsigned)(i >> lg4));
+      v[0] += w * (double)(s0 * s0 + s1 * s1 + s2 * s2 + s3 * s3);
+      v[1] += w * (double)(s0 * y0 + s1 * y1 + s2 * y2 + s3 * y3);
+    }
+  } else {
+    for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
+      const double w = plane_weight(wz, (unsigned)(i >> lgxy));
+      const double a = (double)xn[i] - (double)x[i];
+      const double y = (double)Fn[i] - (double)F[i];
+      v[0] += w * a * a;
+      v[1] += w * a * y;
+    }
+  }
+  block_reduce<2>(v, part);
+  if (last_block(cnt)) {
+    double t[2];
+    fin_sum<2>(part, gridDim.x, t);
+    if (threadIdx.x == 0) {
+      s->sy[0] = t[0];
+      s->sy[1] = t[1];
+    }
+    rearm(cnt);
+  }
+}
+
+// the host loop's decisions after one trial evaluation (one thread)
+__global__ void k_dfd_decide(DFS* s, double* dsig, cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  s->trials += 1;
+  s->evals += 1;
+  const double ft = s->ftrial;
+  bool acc = false;
+  if (s->phase == 0) {
+    s->fp = ft;
+    if (ft <= s->fmax + s->eta - s->gamma * s->ap * s->ap * s->f) acc = true;
+    else s->phase = 1;
+  } else {
+    s->fm = ft;
+    if (ft <= s->fmax + s->eta - s->gamma * s->am * s->am * s->f) {
+      acc = true;
+    } else {
+      const double f = s->f, ap = s->ap, am = s->am;
+      s->ap = fmin(fmax(ap * ap * f / (s->fp + (2 * ap - 1) * f), s->tmin * ap), s->tmax * ap);
+      s->am = fmin(fmax(am * am * f / (s->fm + (2 * am - 1) * f), s->tmin * am), s->tmax * am);
+      s->phase = 0;
+      s->bt += 1;
+      if (s->bt >= 60) s->done = 1;  // line search failed: stop, not converged
+    }
+  }
+  if (acc) {
+    double sigma = s->sy[1] != 0 ? s->sy[0] / s->sy[1] : INFINITY;
+    if (!(fabs(sigma) >= s->smin && fabs(sigma) <= s->smax)) {
+      const double nf = sqrt(ft);
+      sigma = nf > 1 ? 1.0 : (nf >= 1e-5 ? 1.0 / nf : 1e5);
+    }
+    *dsig = sigma;
+    s->cur ^= 1;
+    s->xtr = s->px[1 - s->cur];
+    s->f = ft;
+    s->hist[s->len & 31] = ft;
+    s->len += 1;
+    s->k += 1;
+    // the checks at the top of the next iteration
+    if (!isfinite(s->f)) {
+      s->bad = 1;
+      s->done = 1;
+    } else if (sqrt(s->f) <= s->tol_abs + s->tol_rel * s->nF0) {
+      s->conv = 1;
+      s->done = 1;
+    } else {
+      if (s->len > kDfsStag) {
+        s->best_old = fmin(s->best_old, s->hist[(s->len - 1 - kDfsStag) & 31]);
+        double best_new = INFINITY;
+        for (int j = s->len - kDfsStag; j < s->len; ++j) best_new = fmin(best_new, s->hist[j & 31]);
+        if (best_new > 0.81 * s->best_old) s->done = 1;
+      }
+      if (s->k >= s->max_iter) s->done = 1;
+      if (!s->done) {
+        double fm = 0;
+        for (int j = s->len > kDfsM ? s->len - kDfsM : 0; j < s->len; ++j) fm = fmax(fm, s->hist[j & 31]);
+        s->fmax = fm;
+        s->eta = s->nF0 / ((1.0 + s->k) * (1.0 + s->k));
+        s->ap = 1;
+        s->am = 1;
+        s->bt = 0;
+        s->phase = 0;
+      }
+    }
+  }
+  if (s->trials >= s->max_trials) s->done = 1;
+  cudaGraphSetConditional(cond, s->done ? 0u : 1u);
+}
+
+static bool device_dfsane_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("FVIM_DEVICE_DFSANE");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+inline DFS* dfs_dev(fvim_ctx* c) { return static_cast<DFS*>(c->sv[V_DFS]); }
+inline double* dfs_sigma(fvim_ctx* c) { return reinterpret_cast<double*>(static_cast<char*>(c->sv[V_PKS]) + 128); }
+inline unsigned* dfs_count(fvim_ctx* c) { return reinterpret_cast<unsigned*>(static_cast<char*>(c->sv[V_PKS]) + 196); }
+
+// The WHILE graph of the device DF-SANE loop (built once per context; the material constants
+// and the buffers are fixed, the points and the scalars live in the device state).
+template <typename T> int build_dfloop(fvim_ctx* c, SolverRT* r, size_t n, int grd, int lgxy) {
+  cudaGraph_t g = nullptr;
+  if (FVIM_CU(cudaGraphCreate(&g, 0))) return FVIM_ERR_CUDA;
+  cudaGraphConditionalHandle cond;
+  alignas(cudaGraphNodeParams) unsigned char cpbuf[sizeof(cudaGraphNodeParams)];
+  memset(cpbuf, 0, sizeof(cpbuf));
+  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cpbuf);
+  cudaGraphNode_t node;
+  if (FVIM_CU(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault))) {
+    cudaGraphDestroy(g);
+    return FVIM_ERR_CUDA;
+  }
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (FVIM_CU(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp))) {
+    cudaGraphDestroy(g);
+    return FVIM_ERR_CUDA;
+  }
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if (FVIM_CU(cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal))) {
+    cudaGraphDestroy(g);
+    return FVIM_ERR_CUDA;
+  }
+  DFS* dfs = dfs_dev(c);
+  const void* const* xtr_at =
+      reinterpret_cast<const void* const*>(reinterpret_cast<const char*>(dfs) + offsetof(DFS, xtr));
+  auto seq = [&]() -> int {
+    int e;
+    k_dfd_trial<T><<<grd, RT, 0, c->stream>>>(dfs, dfs_sigma(c), n);
+    FVIM_CUDA_CHECK_LAUNCH();
+    if ((e = reset_flow_range(c))) return e;
+    if ((e = return_map_t<T>(c, nullptr, S<T>(c, V_DEP), S<T>(c, V_EP), flow_range(c), xtr_at))) return e;
+    if ((e = apply_mindlin_t<T>(c, S<T>(c, V_DEP), S<T>(c, V_TMP), FVIM_STRAIN, nullptr, flow_range(c)))) return e;
+    k_dfd_res<T><<<grd, RT, 0, c->stream>>>(dfs, S<T>(c, V_B), S<T>(c, V_TMP), (const double*)c->sv[V_WZ], lgxy, n,
+                                            (double*)c->sv[V_PART], dfs_count(c));
+    k_dfd_sy<T><<<grd, RT, 0, c->stream>>>(dfs, (const double*)c->sv[V_WZ], lgxy, n, (double*)c->sv[V_PART],
+                                           dfs_count(c));
+    k_dfd_decide<<<1, 32, 0, c->stream>>>(dfs, dfs_sigma(c), cond);
+    FVIM_CUDA_CHECK_LAUNCH();
+    return FVIM_OK;
+  };
+  const int rc = seq();
+  cudaGraph_t out = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(c->stream, &out);
+  if (rc != FVIM_OK || FVIM_CU(ce)) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return rc != FVIM_OK ? rc : FVIM_ERR_CUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (FVIM_CU(ie)) {
+    cudaGetLastError();
+    return FVIM_ERR_CUDA;
+  }
+  r->dfloop = ex;
+  return FVIM_OK;
+}
+
 template <typename T>
 int plasticity_t(fvim_ctx* c, const T* dT, T* dE, T* deps_p, T* dep, const fvim_opts* o, int* iters, double* res,
                  long* evals_out, bool warm = false) {
@@ -831,7 +1100,65 @@ int plasticity_t(fvim_ctx* c, const T* dT, T* dE, T* deps_p, T* dep, const fvim_
   // last kStag iterations is not 10 % below the best one before them
   const int kStag = 30;
   double best_old = INFINITY;
-  for (k = 0; k < o->df_max_iter; ++k) {
+  SolverRT* srt = rt(c);
+  bool device_loop = srt && !c->prof && graphs_enabled() && device_dfsane_enabled() && o->df_max_iter > 0 &&
+                     isfinite(f) && !(sqrt(f) <= o->df_tol_abs + o->df_tol_rel * nF0);
+  if (device_loop && !srt->dfloop && !srt->dfloop_failed) {
+    if (build_dfloop<T>(c, srt, n, df.grd, df.lgxy) != FVIM_OK) {
+      srt->dfloop_failed = true;  // the host loop below takes over
+      cudaGetLastError();
+    }
+  }
+  bool ran_device = false;
+  if (device_loop && srt->dfloop) {
+    ran_device = true;
+    DFS* hs = reinterpret_cast<DFS*>(reinterpret_cast<char*>(c->h_part) + (size_t)RMAXB * NVMAX * sizeof(double) + 256);
+    memset(hs, 0, sizeof(DFS));
+    hs->px[0] = x;
+    hs->px[1] = xt;
+    hs->pF[0] = F;
+    hs->pF[1] = Ft;
+    hs->xtr = xt;
+    hs->f = f;
+    hs->nF0 = nF0;
+    hs->fmax = f;
+    hs->eta = nF0;
+    hs->ap = hs->am = 1.0;
+    hs->best_old = INFINITY;
+    hs->tol_abs = o->df_tol_abs;
+    hs->tol_rel = o->df_tol_rel;
+    hs->gamma = gamma;
+    hs->smin = smin;
+    hs->smax = smax;
+    hs->tmin = tmin;
+    hs->tmax = tmax;
+    hs->hist[0] = f;
+    hs->len = 1;
+    hs->max_iter = o->df_max_iter;
+    hs->max_trials = o->df_max_iter * 121 + 1;
+    DFS* ds = dfs_dev(c);
+    if (FVIM_CU(cudaMemcpyAsync(ds, hs, sizeof(DFS), cudaMemcpyHostToDevice, c->stream)) ||
+        FVIM_CU(cudaMemsetAsync(dfs_count(c), 0, sizeof(unsigned), c->stream)) ||
+        FVIM_CU(cudaGraphLaunch(srt->dfloop, c->stream)) ||
+        FVIM_CU(cudaMemcpyAsync(hs, ds, sizeof(DFS), cudaMemcpyDeviceToHost, c->stream)) ||
+        FVIM_CU(cudaStreamSynchronize(c->stream)))
+      return FVIM_ERR_CUDA;
+    c->n_applies += hs->evals;
+    evals += hs->evals;
+    k = hs->k;
+    f = hs->f;
+    conv_ok = hs->conv != 0;
+    if (hs->bad) return FVIM_ERR_NONFINITE;
+    x = const_cast<T*>(static_cast<const T*>(hs->px[hs->cur]));
+    xt = const_cast<T*>(static_cast<const T*>(hs->px[1 - hs->cur]));
+    F = static_cast<T*>(hs->pF[hs->cur]);
+    Ft = static_cast<T*>(hs->pF[1 - hs->cur]);
+    c->sv[V_X] = x;
+    c->sv[V_XT] = xt;
+    c->sv[V_F] = F;
+    c->sv[V_FT] = Ft;
+  }
+  for (k = ran_device ? k : 0; !ran_device && k < o->df_max_iter; ++k) {
     if (!isfinite(f)) return FVIM_ERR_NONFINITE;
     if (sqrt(f) <= o->df_tol_abs + o->df_tol_rel * nF0) { conv_ok = true; break; }
     if (hist.size() > (size_t)kStag) {
@@ -972,6 +1299,8 @@ void solver_drop_graphs(fvim_ctx* c) {
   if (!r) return;
   drop(r->cg);
   drop(r->df);
+  if (r->dfloop) cudaGraphExecDestroy(r->dfloop);
+  r->dfloop = nullptr;
 }
 
 void solver_release(fvim_ctx* c) {
@@ -979,6 +1308,7 @@ void solver_release(fvim_ctx* c) {
   if (r) {
     drop(r->cg);
     drop(r->df);
+    if (r->dfloop) cudaGraphExecDestroy(r->dfloop);
     if (r->stream) cudaStreamDestroy(r->stream);
     if (r->ev_in) cudaEventDestroy(r->ev_in);
     if (r->ev_out) cudaEventDestroy(r->ev_out);
