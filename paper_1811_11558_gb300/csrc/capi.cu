@@ -228,6 +228,23 @@ template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, i
 template <typename T> int apply_boussinesq_t(fvim_ctx* c, const T* p, T* u3, T* vol, int kind) {
   int rc;
   int nk = 0;
+  if (u3 && !vol && c->n2 >= 16) {
+    // surface displacement only: rows, fused column pass (transform, compliance, inverse), rows
+    bool fused = false;
+    if ((rc = timed(c, PROF_ROWS_FWD1, nk, [&] { return launch_rows_fwd1<T>(c, p); }))) return rc;
+    if ((rc = timed(c, PROF_BOUSSINESQ, nk, [&] {
+           fused = launch_cols_conv_ct<T>(c);
+           FVIM_CUDA_CHECK_LAUNCH();
+           return FVIM_OK;
+         })))
+      return rc;
+    if (fused) {
+      if ((rc = timed(c, PROF_ROWS_INV1, nk, [&] { return launch_rows_inv1<T>(c, u3); }))) return rc;
+      c->last_kernels = nk;
+      return FVIM_OK;
+    }
+    nk = 0;  // no variant for this N2: the general sequence below
+  }
   if ((rc = timed(c, PROF_ROWS_FWD1, nk, [&] { return launch_rows_fwd1<T>(c, p); }))) return rc;
   if ((rc = timed(c, PROF_COLS_FWD, nk, [&] { return launch_cols<T>(c, false, c->surf, 1); }))) return rc;
   if ((rc = timed(c, PROF_BOUSSINESQ, nk,

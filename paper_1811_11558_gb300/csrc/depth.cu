@@ -300,12 +300,19 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
   // 1. load the tile (coalesced KT-wide rows, every copy in flight before one wait) and
   //    the depth nodes
   // (layers outside zr hold no input: their spectrum was not computed and reads as zero)
-  const int zlo = zr ? zr[0] : 0, zhi = zr ? zr[1] : nz;
-  for (int idx = threadIdx.x; idx < nz * 6 * KT; idx += blockDim.x) {
-    const int zc = idx / KT, j = idx & (KT - 1);
-    const int zl = zc / 6;
-    if (zl >= zlo && zl < zhi) cp_async_cx(W + idx, spec + (size_t)zc * plane + colofs + j);
-    else W[idx] = mk<V>(0, 0);
+  if (!zr) {
+    for (int idx = threadIdx.x; idx < nz * 6 * KT; idx += blockDim.x) {
+      const int zc = idx / KT, j = idx & (KT - 1);
+      cp_async_cx(W + idx, spec + (size_t)zc * plane + colofs + j);
+    }
+  } else {
+    const int zlo = zr[0], zhi = zr[1];
+    for (int idx = threadIdx.x; idx < nz * 6 * KT; idx += blockDim.x) {
+      const int zc = idx / KT, j = idx & (KT - 1);
+      const int zl = zc / 6;
+      if (zl >= zlo && zl < zhi) cp_async_cx(W + idx, spec + (size_t)zc * plane + colofs + j);
+      else W[idx] = mk<V>(0, 0);
+    }
   }
   for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];
   cp_async_wait_all();
@@ -574,15 +581,22 @@ __global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* _
 
   // 1. load the tile (16-byte copies, two FP32 complex values each) and the depth nodes
   // (layers outside zr hold no input: their spectrum was not computed and reads as zero)
-  const int zlo = zr ? zr[0] : 0, zhi = zr ? zr[1] : nz;
-  for (int idx = threadIdx.x; idx < nz * 6 * (KT / 2); idx += blockDim.x) {
-    const int zc = idx / (KT / 2), j = 2 * (idx % (KT / 2));
-    const int zl = zc / 6;
-    if (zl >= zlo && zl < zhi) {
+  if (!zr) {
+    for (int idx = threadIdx.x; idx < nz * 6 * (KT / 2); idx += blockDim.x) {
+      const int zc = idx / (KT / 2), j = 2 * (idx % (KT / 2));
       cp_async_16(W + zc * KT + j, spec + (size_t)zc * plane + colofs + j);
-    } else {
-      W[zc * KT + j] = mk<V>(0, 0);
-      W[zc * KT + j + 1] = mk<V>(0, 0);
+    }
+  } else {
+    const int zlo = zr[0], zhi = zr[1];
+    for (int idx = threadIdx.x; idx < nz * 6 * (KT / 2); idx += blockDim.x) {
+      const int zc = idx / (KT / 2), j = 2 * (idx % (KT / 2));
+      const int zl = zc / 6;
+      if (zl >= zlo && zl < zhi) {
+        cp_async_16(W + zc * KT + j, spec + (size_t)zc * plane + colofs + j);
+      } else {
+        W[zc * KT + j] = mk<V>(0, 0);
+        W[zc * KT + j + 1] = mk<V>(0, 0);
+      }
     }
   }
   for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];

@@ -85,6 +85,41 @@ __global__ void __launch_bounds__(N / 2) k_cols_v(float2* __restrict__ planes, c
   for (int m = 0; m < 8; ++m) col[(size_t)(t + m * T8) * rs] = make_float4(v[0][m].x, v[0][m].y, v[1][m].x, v[1][m].y);
 }
 
+// Surface displacement of a pressure, column pass fused: forward FFT along x2 of kc k1
+// columns, multiplication by the surface compliance u3_hat = (1 - nu) / (mu q) p_hat (zero on
+// mode 0 and on the Nyquist row k2 = N2/2, as the Boussinesq kernel), inverse FFT, in one
+// kernel (a column is whole inside the CTA).  The row passes stay separate.
+template <typename T, int N>
+__global__ void __launch_bounds__(512) k_cols_conv(typename Cx<T>::t* __restrict__ plane,
+                                                   const typename Cx<T>::t* __restrict__ tw, int h1, int kc, T w1,
+                                                   T w2, T nu, T mu) {
+  typedef typename Cx<T>::t V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int T8 = N / 8;
+  const int f = threadIdx.x % kc, t = threadIdx.x / kc;
+  const int k1 = blockIdx.x * kc + f;
+  V* col = plane + k1;
+  V v[1][8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) v[0][m] = col[(size_t)(t + m * T8) * h1];
+  ColSm<V> sm{reinterpret_cast<V*>(smraw), kc, f};
+  fft_ct<V, false, N, 1, 1>(v, t, sm, tw);
+  const T q1 = w1 * (T)k1;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int k2 = t + m * T8;
+    const int k2s = k2 < N / 2 ? k2 : k2 - N;
+    const T q2 = w2 * (T)k2s;
+    const T q = sqrt(q1 * q1 + q2 * q2);
+    const bool none = (k1 == 0 && k2 == 0) || k2 == N / 2;
+    v[0][m] = none ? mk<V>(0, 0) : cscale(v[0][m], ((T)1 - nu) / (mu * q));
+  }
+  __syncthreads();  // the exchange area is reused by the inverse transform
+  fft_ct<V, true, N, 1, 1>(v, t, sm, tw);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) col[(size_t)(t + m * T8) * h1] = v[0][m];
+}
+
 template <typename V>
 __device__ __forceinline__ void split_pair_ct(V zk, V zmk, V& A, V& B) {
   typedef decltype(V::x) T;
@@ -335,6 +370,29 @@ template <typename T> bool launch_cols_ct(const fvim_ctx* c, bool inverse, void*
   return false;
 }
 
+template <typename T, int N> void cols_conv_n(const fvim_ctx* c) {
+  typedef typename Cx<T>::t V;
+  int kc = (int)(64 / sizeof(V));
+  while (kc > 1 && kc * (N / 8) > 512) kc >>= 1;
+  if (kc > c->h1) kc = c->h1;
+  const size_t smem = (size_t)kc * N * sizeof(V);
+  smem_attr(k_cols_conv<T, N>, smem);
+  const double two_pi = 6.283185307179586476925;
+  k_cols_conv<T, N><<<c->h1 / kc, kc * (N / 8), smem, c->stream>>>(
+      (V*)c->surf, (const V*)c->tw2, c->h1, kc, (T)(two_pi / c->L1), (T)(two_pi / c->L2), (T)c->nu, (T)c->mu);
+}
+
+template <typename T> bool launch_cols_conv_ct(const fvim_ctx* c) {
+#define CASE(N)              \
+  if (c->n2 == N) {          \
+    cols_conv_n<T, N>(c);    \
+    return true;             \
+  }
+  FVIM_CT_SIZES(CASE)
+#undef CASE
+  return false;
+}
+
 template <typename T> bool launch_rows_fwd6_ct(const fvim_ctx* c, const T* eps_p, int z0, int nzs, const int* zr) {
 #define CASE(N)                              \
   if (c->n1 == N) {                          \
@@ -358,6 +416,8 @@ template <typename T> bool launch_rows_inv6_ct(const fvim_ctx* c, T* out, T nq_s
 }
 
 template bool launch_cols_ct<float>(const fvim_ctx*, bool, void*, int, const int*);
+template bool launch_cols_conv_ct<float>(const fvim_ctx*);
+template bool launch_cols_conv_ct<double>(const fvim_ctx*);
 template bool launch_cols_ct<double>(const fvim_ctx*, bool, void*, int, const int*);
 template bool launch_rows_fwd6_ct<float>(const fvim_ctx*, const float*, int, int, const int*);
 template bool launch_rows_fwd6_ct<double>(const fvim_ctx*, const double*, int, int, const int*);

@@ -432,6 +432,8 @@ int launch_fft2_inv_cluster(const fvim_ctx* c, float* out, int nq_mode, float nq
 
 // compile-time-length FFT kernels (fft_ct.cu); false when the length has no variant
 template <typename T> bool launch_cols_ct(const fvim_ctx* c, bool inverse, void* planes, int nplanes, const int* zr = nullptr);
+// surface compliance applied in the column pass (fft_ct.cu); false when N2 has no variant
+template <typename T> bool launch_cols_conv_ct(const fvim_ctx* c);
 template <typename T> bool launch_rows_fwd6_ct(const fvim_ctx* c, const T* eps_p, int z0, int nzs, const int* zr = nullptr);
 template <typename T> bool launch_rows_inv6_ct(const fvim_ctx* c, T* out, T nq_scale, int z0, int nzs);
 

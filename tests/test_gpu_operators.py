@@ -171,11 +171,13 @@ def test_boussinesq_parity(n1, n2, z, L1, L2, prec, kind, monkeypatch):
     torch.cuda.synchronize()
     assert rel_l2(u3.cpu().numpy(), u3_ref) < TOL[prec]
     assert rel_l2(vol.cpu().numpy(), vol_ref) < TOL[prec]
-    # surface only (no volume output) gives the same displacement
+    # surface only (no volume output; its column pass transforms, applies the compliance and
+    # transforms back in one kernel) gives the same displacement up to rounding
     u3b = torch.empty_like(u3)
     ctx.apply_boussinesq(to_dev(torch, p, dt), u3=u3b)
     torch.cuda.synchronize()
-    assert torch.equal(u3, u3b)
+    assert rel_l2(u3b.cpu().numpy(), u3.cpu().numpy()) < (1e-14 if prec == "fp64" else 1e-6)
+    assert rel_l2(u3b.cpu().numpy(), u3_ref) < TOL[prec]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
