@@ -141,8 +141,9 @@ const char* fvim_strerror(int status);
 
 /* fvim_last_cuda_error -- description of the last CUDA runtime error that made an entry
  * point return FVIM_ERR_CUDA (or that a solver recovered from by launching directly
- * instead of through a captured graph) in the calling host thread; "no error" if none.
- * The paper has no counterpart: it is the diagnostic behind FVIM_ERR_CUDA. */
+ * instead of through a captured graph) in the calling host thread, followed by the source
+ * file and line of the runtime call that returned it; "no error" if none.  The string is
+ * owned by the library and stays valid until the thread's next failing call.  The paper has no counterpart: it is the diagnostic behind FVIM_ERR_CUDA. */
 const char* fvim_last_cuda_error(void);
 
 /* fvim_last_kernel_count -- number of kernels the last entry point launched. */

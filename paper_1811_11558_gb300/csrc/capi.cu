@@ -1,6 +1,7 @@
 // C ABI of libfvim (declarations and argument contracts in include/fvim.h).
 #include <math.h>
 #include <stdlib.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <new>
@@ -10,10 +11,14 @@
 #include "fvim_internal.cuh"
 
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
+static thread_local char g_last_cuda_msg[256];
 
-bool fvim_cuda_failed(cudaError_t e) {
+bool fvim_cuda_failed(cudaError_t e, const char* file, int line) {
   if (e == cudaSuccess) return false;
   g_last_cuda = e;
+  const char* base = file ? strrchr(file, '/') : nullptr;
+  base = base ? base + 1 : (file ? file : "?");
+  snprintf(g_last_cuda_msg, sizeof g_last_cuda_msg, "%s (%s:%d)", cudaGetErrorString(e), base, line);
   return true;
 }
 
@@ -307,7 +312,7 @@ template int commit_t<double>(fvim_ctx*, const double*, const double*, const dou
 
 extern "C" {
 
-const char* fvim_last_cuda_error(void) { return g_last_cuda == cudaSuccess ? "no error" : cudaGetErrorString(g_last_cuda); }
+const char* fvim_last_cuda_error(void) { return g_last_cuda == cudaSuccess ? "no error" : g_last_cuda_msg; }
 
 const char* fvim_strerror(int s) {
   switch (s) {

@@ -910,7 +910,7 @@ int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps
   if constexpr (sizeof(T) == 4) if (KT == 16 && C <= 8 && smr <= 227 * 1024) {
 #define DEPTHR(CV, EI)                                                                                          \
   if (CR == CV && eps_in == EI) {                                                                               \
-    cudaFuncSetAttribute(k_mindlin_depth_r<T, 16, CV, EI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr); \
+    smem_cap(k_mindlin_depth_r<T, 16, CV, EI>); \
     k_mindlin_depth_r<T, 16, CV, EI><<<grid, 16 * nchr, smr, c->stream>>>(                                       \
         (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, n2, h1, nchr, w1, w2, (T)c->lam, (T)c->mu, (T)c->nu,  \
         out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz, zr);                                                    \
@@ -923,7 +923,7 @@ int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps
   }
 #define DEPTH(KTV, EI)                                                                                         \
   if (KT == KTV && eps_in == EI) {                                                                             \
-    cudaFuncSetAttribute(k_mindlin_depth<T, KTV, EI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+    smem_cap(k_mindlin_depth<T, KTV, EI>);  \
     k_mindlin_depth<T, KTV, EI><<<grid, threads, smem, c->stream>>>(                                             \
         (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, n2, h1, C, nch, prow, w1, w2, (T)c->lam, (T)c->mu,   \
         (T)c->nu, out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz, zr);                                       \

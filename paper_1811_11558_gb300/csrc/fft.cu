@@ -431,7 +431,7 @@ template <typename T> int row_block(int n1, int n2) {
 }
 
 template <typename K> void set_smem(K kern, size_t smem) {
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  smem_cap(kern);
 }
 
 }  // namespace

@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(256) k_rows_fwd6_v(const float* __restrict__ e
 }
 
 template <typename K> void smem_attr(K kern, size_t smem) {
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  smem_cap(kern);
 }
 
 inline int ct_rows(int n1, int n2) {

@@ -357,6 +357,23 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Raises a kernel's dynamic shared-memory cap to the device's opt-in maximum.  The value is
+// the same on every call: contexts used from several host threads launch one kernel with
+// different sizes, and a cap set to the exact size of one launch could be lowered under
+// another thread's launch of the same kernel.
+inline int smem_optin_max() {
+  static const int v = [] {
+    int dev = 0, m = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&m, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return m > 0 ? m : 48 * 1024;
+  }();
+  return v;
+}
+template <typename K> inline void smem_cap(K kern) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
+}
+
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
@@ -449,11 +466,11 @@ int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep, int* zr = nul
                  const void* const* d_eps_at = nullptr);
 template <typename T> int commit_t(fvim_ctx* c, const T* d_eps, const T* d_eps_p, const T* d_ep);
 
-// true when e is an error; the error is kept as this host thread's last CUDA error
-// (fvim_last_cuda_error)
-bool fvim_cuda_failed(cudaError_t e);
-#define FVIM_CU(call) fvim_cuda_failed(call)
-#define FVIM_CUDA_CHECK_LAUNCH()                                  \
-  do {                                                            \
-    if (fvim_cuda_failed(cudaGetLastError())) return FVIM_ERR_CUDA; \
+// true when e is an error; the error and the source line that saw it are kept as this host
+// thread's last CUDA error (fvim_last_cuda_error)
+bool fvim_cuda_failed(cudaError_t e, const char* file = nullptr, int line = 0);
+#define FVIM_CU(call) fvim_cuda_failed((call), __FILE__, __LINE__)
+#define FVIM_CUDA_CHECK_LAUNCH()                                                        \
+  do {                                                                                  \
+    if (fvim_cuda_failed(cudaGetLastError(), __FILE__, __LINE__)) return FVIM_ERR_CUDA; \
   } while (0)
