@@ -505,8 +505,8 @@ def scaling_metrics(sizes=(16, 32, 64, 128), reps=20):
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each kernel on this
 # workload, from one capture of the current kernels (profiles/ summaries); a kernel missing
 # here reports null.
-TRAFFIC_BYTES = {"rows_fwd6": 755.3e6, "cols_fwd": 749.8e6, "mindlin_depth": 753.1e6, "cols_inv": 749.8e6,
-                 "rows_inv6": 758.1e6}
+TRAFFIC_BYTES = {"rows_fwd6": 755.2e6, "cols_fwd": 749.7e6, "mindlin_depth": 750.0e6, "cols_inv": 749.8e6,
+                 "rows_inv6": 758.0e6}
 
 
 def _operator_input(seed=SEED):
