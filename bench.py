@@ -144,6 +144,7 @@ def run_gpu(args):
     ep = inputs.plastic_strain_field(N1, N2, z, seed=SEED + rank, dtype=np.float32)
     vox = N1 * N2 * NZ
     ctx = Context(N1, N2, z, 1.0, 1.0, precision="fp32", E=E, nu=NU)
+    plan = ctx.autotune(reps=20)       # the depth kernel's tile plan for this grid
     d_in = torch.from_numpy(ep).cuda()
     d_out = torch.empty_like(d_in)
     stream = torch.cuda.current_stream()
@@ -252,7 +253,8 @@ def run_gpu(args):
         "peak_kind": peak_kind,
         "unit": "GB/s",
         "frac": round(achieved / peak, 4),
-        "traffic": TRAFFIC_BYTES.get(dom_name),
+        "traffic": TRAFFIC_BYTES.get(dom_name) if plan["depth_chunk"] == TRAFFIC_DEPTH_CHUNK or
+        dom_name != "mindlin_depth" else None,
         "alg_bytes": alg_bytes,
         "avg_launch_ms": round(avg_ms, 5),
     }
@@ -280,6 +282,7 @@ def run_gpu(args):
                             "apply and download on three streams over three buffer slots"},
         "gpu_launches": kernels_per_step * args.steps,
         "kernel_ms": kernel_ms,
+        "tile_plan": plan,
         "roofline": roofline,
         "clocks": clocks,
     }
@@ -287,6 +290,7 @@ def run_gpu(args):
         line["solves"] = solve_metrics()
         line["solves"]["rough"] = rough_metrics()
         line["solves"]["stream"] = stream_metrics()
+        line["solves"]["batch"] = batch_metrics()
         line["scaling_sweep"] = scaling_metrics()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sample_modes=256, sample_planes=None)
@@ -327,6 +331,7 @@ def solve_metrics(repeats=3, served=32, slots=16):
     for prec in ("fp64", "fp32"):
         ctx = Context(c["n"], c["n"], c["z"], 1.0, 1.0, precision=prec, E=E, nu=NU, sigma_y=c["sigma_y"],
                       E_h=c["E_h"])
+        ctx.autotune()
         h = torch.from_numpy(c["h"]).to("cuda", ctx.dtype)
         p = torch.empty(ctx.surf_shape, dtype=ctx.dtype, device="cuda")
         opts = ctx.default_opts(relax=0.5, max_iter=400)
@@ -345,6 +350,7 @@ def solve_metrics(repeats=3, served=32, slots=16):
     srv = Server(slots=slots)
     reqs = [Request(i, c["n"], c["z"], c["h"], c["loads"], precision="fp32", E=E, nu=NU, sigma_y=c["sigma_y"],
                     E_h=c["E_h"], opts={"relax": 0.5, "max_iter": 400}) for i in range(served)]
+    srv.prepare(reqs[:1])                       # the grid's tuned tile plan
     srv.run(reqs[:slots])                       # warm the context pool
     res, wall = srv.run(reqs)
     lat = percentiles([r.latency for r in res])
@@ -372,6 +378,7 @@ def rough_metrics(n=1024, nz=32, depth=0.05, seed=1813):
     z = inputs.uniform_depth(nz, depth)
     h = inputs.self_affine_surface(n, 1.0, 0.8, 4, 8, 64, 0.1, seed=seed)
     ctx = Context(n, n, z, 1.0, 1.0, precision="fp32", E=E, nu=NU, sigma_y=0.05 * es, E_h=0.1 * E)
+    ctx.autotune()
     hd = torch.from_numpy(h).to("cuda", torch.float32)
     p = torch.zeros(ctx.surf_shape, dtype=torch.float32, device="cuda")
     out = {"workload": "rough_%dx%dx%d_fp32" % (n, n, nz), "depth": depth, "seed": seed}
@@ -406,6 +413,108 @@ def rough_metrics(n=1024, nz=32, depth=0.05, seed=1813):
     return out
 
 
+def batch_problems(n_prob=64, seed=1814):
+    """Uneven elastic-plastic contact problems: grids n^2 with n drawn from {64, 128, 256, 512},
+    nz from {8, 16, 32}; half paraboloids (R = 0.5, depth 0.5), half seeded self-affine surfaces
+    (H uniform in [0.6, 0.9], flat PSD for 4 <= |k| < 8, power law to k_s = max(8, n / 16),
+    rms slope 0.1, depth 0.05); total load log-uniform over the decade below the load of a 10 %
+    elastic contact fraction (Hertz: pi a^2 = 0.1, W = 4 E* a^3 / (3 R); rough: mean pressure
+    0.1 E* slope / 2), five increments; sigma_y = 0.05 E*, E_h = 0.1 E."""
+    from paper_1811_11558_gb300 import inputs
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    es = E / (1 - NU * NU)
+    probs = []
+    for i in range(n_prob):
+        n = int(2 ** rng.integers(6, 10))
+        nz = int(rng.choice([8, 16, 32]))
+        rough = bool(rng.integers(0, 2))
+        u = float(rng.uniform(-1.0, 0.0))
+        if rough:
+            hurst = float(rng.uniform(0.6, 0.9))
+            h = inputs.self_affine_surface(n, 1.0, hurst, 4, 8, max(8, n // 16), 0.1, seed=seed + 1 + i)
+            z = inputs.uniform_depth(nz, 0.05)
+            w10 = 0.1 * es * 0.1 / 2.0
+            relax = 0.3
+        else:
+            h = inputs.hertz_profile(n, n, 1.0, 1.0, 0.5)
+            z = inputs.uniform_depth(nz, 0.5)
+            a = np.sqrt(0.1 / np.pi)
+            w10 = 4.0 * es * a ** 3 / (3.0 * 0.5)
+            relax = 0.5
+        W = w10 * 10.0 ** u
+        probs.append({"n": n, "nz": nz, "rough": rough, "z": z, "h": h, "loads": [W * (k + 1) / 5 for k in range(5)],
+                      "relax": relax})
+    return probs
+
+
+def batch_metrics(n_prob=64, slots=16, seed=1814, max_iter=40, n64=4):
+    """Batched uneven solves: n_prob problems (batch_problems) submitted at once to the
+    server (slots contexts, one stream and one set of captured graphs each, FP32 operators,
+    FP64 reductions), aggregate solves/s and per-problem latency; plain FP64 and FP32 one at a
+    time on the first n64 problems of the smallest grid, with the FP32 pressure error."""
+    import torch
+
+    from paper_1811_11558_gb300 import Context
+    from paper_1811_11558_gb300.serve import Request, Server, percentiles
+
+    es = E / (1 - NU * NU)
+    probs = batch_problems(n_prob, seed)
+
+    def req(i, pb, prec="fp32"):
+        return Request(i, pb["n"], pb["z"], pb["h"], pb["loads"], precision=prec, E=E, nu=NU, sigma_y=0.05 * es,
+                       E_h=0.1 * E, opts={"relax": pb["relax"], "max_iter": max_iter, "tol": 1e-6})
+
+    srv = Server(slots=slots)
+    t0 = time.perf_counter()
+    plans = srv.prepare([req(i, pb) for i, pb in enumerate(probs)])   # one tuned context per shape
+    prep_s = time.perf_counter() - t0
+    seen, warm = set(), []
+    for i, pb in enumerate(probs):          # one request per shape warms the context pool
+        key = (pb["n"], pb["nz"], pb["rough"])
+        if key not in seen:
+            seen.add(key)
+            warm.append(req(i, pb))
+    srv.run(warm)
+    res, wall = srv.run([req(i, pb) for i, pb in enumerate(probs)])
+    lat = percentiles([r.latency for r in res])
+    conv = sum(1 for r in res if r.report.get("status", 0) == 0)
+    small = [i for i, pb in enumerate(probs) if pb["n"] == min(q["n"] for q in probs)][:n64]
+    t = {"fp64": [], "fp32": []}
+    err = []
+    for i in small:
+        pb = probs[i]
+        press = {}
+        for prec in ("fp64", "fp32"):
+            ctx = Context(pb["n"], pb["n"], pb["z"], 1.0, 1.0, precision=prec, E=E, nu=NU, sigma_y=0.05 * es,
+                          E_h=0.1 * E)
+            ctx.autotune()
+            hd = torch.from_numpy(np.ascontiguousarray(pb["h"])).to("cuda", ctx.dtype)
+            p = torch.empty(ctx.surf_shape, dtype=ctx.dtype, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.solve_contact(hd, pb["loads"], p, ctx.default_opts(relax=pb["relax"], max_iter=max_iter,
+                                                                   **({"tol": 1e-6} if prec == "fp32" else {})),
+                              allow_not_converged=True)
+            t[prec].append(time.perf_counter() - t0)
+            press[prec] = p.cpu().numpy().astype(np.float64)
+            ctx.close()
+        err.append(float(np.linalg.norm(press["fp32"] - press["fp64"]) / np.linalg.norm(press["fp64"])))
+    return {"workload": "batch_%d_uneven" % n_prob, "grids": sorted({pb["n"] for pb in probs}),
+            "nz": sorted({pb["nz"] for pb in probs}), "rough": sum(pb["rough"] for pb in probs),
+            "slots": slots, "alg1_cap": max_iter, "converged": conv,
+            "tile_plans": {"shapes": len(plans), "tuning_s": prep_s,
+                           "depth_chunk": sorted({(p["n"], p["nz"], p["depth_chunk"]) for p in plans.values()})},
+            "fp32_served": {"solves_per_s": n_prob / wall, "wall_s": wall, "p50_ms": 1e3 * lat[50],
+                            "p99_ms": 1e3 * lat[99], "arrivals": "all at t = 0"},
+            "sample_n%d" % probs[small[0]]["n"] if small else "sample": {
+                "problems": small, "fp64_plain_ms": [1e3 * x for x in t["fp64"]],
+                "fp32_plain_ms": [1e3 * x for x in t["fp32"]], "fp32_vs_fp64_pressure_rel_l2": err},
+            "per_problem": [{"n": pb["n"], "nz": pb["nz"], "rough": pb["rough"], "ms": 1e3 * (r.finished - r.admitted),
+                             "status": r.report.get("status", 0), "iters": r.report.get("alg1_iters")}
+                            for pb, r in zip(probs, res)]}
+
+
 def stream_metrics(n_req=12, slots=8, seed=1815):
     """Served request stream, FP32 vs plain FP64: requests with grids drawn uniformly in log2
     from {128, 256}, nz = round(16 x 2^U) in [16, 32], seeded self-affine surfaces (H 0.8, rms
@@ -429,6 +538,7 @@ def stream_metrics(n_req=12, slots=8, seed=1815):
         reqs.append(Request(i, n, z, h, [1e-4 * (k + 1) / 5 for k in range(5)], precision="fp32", E=E, nu=NU,
                             sigma_y=0.05 * es, E_h=0.1 * E, opts={"relax": 0.3, "max_iter": 100, "tol": 1e-6}))
     srv = Server(slots=slots)
+    srv.prepare(reqs)                                   # tuned tile plan per shape
     srv.run(reqs[:4])                                   # warm the context pool
     # single-stream capacity: one request at a time
     t0 = time.perf_counter()
@@ -449,6 +559,7 @@ def stream_metrics(n_req=12, slots=8, seed=1815):
     p64 = []
     for r in reqs[:4]:
         ctx = Context(r.n, r.n, r.z, 1.0, 1.0, precision="fp64", E=E, nu=NU, sigma_y=r.sigma_y, E_h=r.E_h)
+        ctx.autotune()
         hd = torch.from_numpy(np.ascontiguousarray(r.h)).to("cuda", torch.float64)
         p = torch.empty(ctx.surf_shape, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
@@ -487,6 +598,7 @@ def scaling_metrics(sizes=(16, 32, 64, 128), reps=20):
         for n in sizes:
             z = inputs.uniform_depth(n, 1.0)
             ctx = Context(n, n, z, 1.0, 1.0, precision=prec, E=E, nu=NU)
+            ctx.autotune()
             ep = torch.from_numpy(inputs.plastic_strain_field(n, n, z, seed=n)).to("cuda", ctx.dtype)
             o = torch.empty_like(ep)
             for _ in range(3):
@@ -505,6 +617,7 @@ def scaling_metrics(sizes=(16, 32, 64, 128), reps=20):
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each kernel on this
 # workload, from one capture of the current kernels (profiles/ summaries); a kernel missing
 # here reports null.
+TRAFFIC_DEPTH_CHUNK = 4     # depth tile plan of that capture
 TRAFFIC_BYTES = {"rows_fwd6": 755.2e6, "cols_fwd": 749.7e6, "mindlin_depth": 750.0e6, "cols_inv": 749.8e6,
                  "rows_inv6": 758.0e6}
 

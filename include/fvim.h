@@ -143,8 +143,49 @@ const char* fvim_strerror(int status);
  * point return FVIM_ERR_CUDA (or that a solver recovered from by launching directly
  * instead of through a captured graph) in the calling host thread, followed by the source
  * file and line of the runtime call that returned it; "no error" if none.  The string is
- * owned by the library and stays valid until the thread's next failing call.  The paper has no counterpart: it is the diagnostic behind FVIM_ERR_CUDA. */
+ * owned by the library and stays valid until the thread's next failing call.  The paper
+ * has no counterpart: it is the diagnostic behind FVIM_ERR_CUDA. */
 const char* fvim_last_cuda_error(void);
+
+/*
+ * Tile plan of the per-wavevector depth kernel.  The paper has no counterpart: its depth
+ * integral (Sec. 3.2) is evaluated here by exact O(Nz) exponential recursions whose depth
+ * range is cut into chunks of depth_chunk nodes, one thread per chunk, the chunk carries
+ * being combined by a log-depth scan.  Every launchable chunk length gives the same operator
+ * up to the rounding order of that scan; the fastest one depends on the grid.
+ *   depth_chunk   chunk length in use (fvim_set_plan: 0 selects the default rule,
+ *                 max(2, ceil(Nz / 16)))
+ *   tuned         1 if depth_chunk came from a timing run (fvim_autotune) in this process
+ *   n_cand, cand[i], cand_ms[i]   fvim_autotune only: the chunk lengths timed and the median
+ *                 time of one depth-kernel launch with each (ms)
+ */
+#define FVIM_PLAN_MAX_CAND 8
+typedef struct fvim_plan {
+  int depth_chunk;
+  int tuned;
+  int n_cand;
+  int cand[FVIM_PLAN_MAX_CAND];
+  float cand_ms[FVIM_PLAN_MAX_CAND];
+} fvim_plan;
+
+/* fvim_autotune -- times the depth kernel on ctx's grid with every launchable chunk length
+ * of {2, 3, 4, 6, 8, 12, 16} and the default, `reps` launches each on ctx's stream over its
+ * (zeroed) spectrum scratch, and keeps the fastest (the default unless another is more than
+ * 2 % faster) for ctx and for every context of the same grid, precision and depth spacing
+ * (uniform or not) created later in this process.  Synchronises ctx's stream; leaves the
+ * plastic state untouched; drops ctx's captured solver graphs when the plan changes.
+ * out (host) or NULL receives the plan and the timings.  FVIM_ERR_ARG: NULL ctx, reps
+ * outside [1, 1000], or ctx's stream is capturing a graph; FVIM_ERR_CUDA on a device error
+ * (the plan is then unchanged). */
+int fvim_autotune(fvim_ctx* ctx, int reps, fvim_plan* out);
+
+/* fvim_get_plan -- the plan ctx uses (host out; cand fields zero). */
+int fvim_get_plan(const fvim_ctx* ctx, fvim_plan* out);
+
+/* fvim_set_plan -- forces plan->depth_chunk on ctx alone (other fields ignored); the process
+ * table is not changed.  FVIM_ERR_ARG if that chunk length is not launchable on ctx's grid
+ * (more than 256 chunk threads per tile, or the tile does not fit in shared memory). */
+int fvim_set_plan(fvim_ctx* ctx, const fvim_plan* plan);
 
 /* fvim_last_kernel_count -- number of kernels the last entry point launched. */
 int fvim_last_kernel_count(const fvim_ctx* ctx);

@@ -361,6 +361,8 @@ int fvim_create(fvim_ctx** out, int n1, int n2, int nz, const double* z_nodes, d
     if (fabs((z_nodes[i] - z_nodes[i - 1]) - h) > 1e-12 * fabs(z_nodes[nz - 1])) c->uniform = 0;
   c->hz = h;
   fvim_set_material(c, 1.0, 0.3, INFINITY, 0.0);
+  // a grid tuned earlier in this process starts with its tuned tile plan
+  if ((c->depth_chunk = plan_lookup(c)) > 0) c->plan_tuned = 1;
   int rc;
   const size_t es = precision == FVIM_FP64 ? 8 : 4;
   const size_t cs = 2 * es;

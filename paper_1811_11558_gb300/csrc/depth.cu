@@ -881,12 +881,40 @@ __global__ void k_boussinesq(typename Cx<T>::t* __restrict__ spec, typename Cx<T
 
 }  // namespace
 
-template <typename T>
-int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps_in, const int* zr) {
+// Launch configuration of the depth kernel for chunk length C (nodes per chunk thread).
+// Every valid C gives the same operator up to the rounding order of the chunk scan.
+template <typename T> struct DepthCfg {
+  bool ok;        // launchable (threads, shared memory)
+  bool reg;       // FP32 register variant
+  int C, nch, KT, threads;
+  size_t smem;
+};
+
+int depth_chunk_default(int nz) {
+  const int C = (nz + 15) / 16;
+  return C < 2 ? 2 : C;
+}
+
+template <typename T> DepthCfg<T> depth_cfg(const fvim_ctx* c, int C) {
   typedef typename Cx<T>::t V;
-  const int nz = c->nz, h1 = c->h1, n2 = c->n2;
-  int C = (nz + 15) / 16;
-  if (C < 2) C = 2;
+  DepthCfg<T> d{};
+  const int nz = c->nz, h1 = c->h1;
+  d.ok = false;
+  if (C < 2 || C > nz) return d;
+  if constexpr (sizeof(T) == 4) {
+    // FP32, 16-column tiles, at most 8 nodes per chunk: the register variant (C rounded up
+    // to an instantiated chunk length)
+    if (h1 >= KT_MAX && C <= 8) {
+      const int CR = C <= 2 ? 2 : (C <= 3 ? 3 : (C <= 4 ? 4 : (C <= 6 ? 6 : 8)));
+      const int nchr = (nz + CR - 1) / CR;
+      const size_t smr = (size_t)nz * 6 * 16 * sizeof(V) + (size_t)(2 * nchr) * 16 * sizeof(Mom<V>) +
+                         (size_t)3 * 16 * sizeof(V) + (size_t)nz * sizeof(T);
+      if (smr <= 227 * 1024 && 16 * nchr <= 256) {
+        d = DepthCfg<T>{true, true, CR, nchr, 16, 16 * nchr, smr};
+        return d;
+      }
+    }
+  }
   const int nch = (nz + C - 1) / C;
   const int prow = nz > 2 * nch + 1 ? nz : 2 * nch + 1;
   // tile width: 16 k1 columns (128-byte rows in FP32), narrower where the depth column of
@@ -896,23 +924,36 @@ int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps
     return (size_t)nz * 6 * kt * sizeof(V) + (size_t)prow * kt * sizeof(Mom<V>) + (size_t)nz * sizeof(T);
   };
   while (KT > 2 && smem_of(KT) > 227 * 1024) KT >>= 1;
-  const size_t smem = smem_of(KT);
-  if (smem > 227 * 1024) return FVIM_ERR_UNSUPPORTED;
-  const int threads = KT * nch;
+  d.C = C;
+  d.nch = nch;
+  d.KT = KT;
+  d.threads = KT * nch;
+  d.smem = smem_of(KT);
+  d.reg = false;
+  d.ok = d.smem <= 227 * 1024 && d.threads <= 256;
+  return d;
+}
+
+bool depth_chunk_ok(const fvim_ctx* c, int C) {
+  return c->prec == FVIM_FP64 ? depth_cfg<double>(c, C).ok : depth_cfg<float>(c, C).ok;
+}
+
+template <typename T>
+int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps_in, const int* zr) {
+  typedef typename Cx<T>::t V;
+  const int nz = c->nz, h1 = c->h1, n2 = c->n2;
+  const DepthCfg<T> d = depth_cfg<T>(c, c->depth_chunk > 0 ? c->depth_chunk : depth_chunk_default(nz));
+  if (!d.ok) return FVIM_ERR_UNSUPPORTED;
+  const int KT = d.KT, C = d.C, nch = d.nch;
+  const int prow = nz > 2 * nch + 1 ? nz : 2 * nch + 1;
   dim3 grid(h1 / KT, n2);
   const T w1 = (T)(kTwoPi / c->L1), w2 = (T)(kTwoPi / c->L2);
-  // FP32, 16-column tiles, at most 8 nodes per chunk: the register variant (C rounded up
-  // to an instantiated chunk length; any C >= 2 is exact)
-  const int CR = C <= 2 ? 2 : (C <= 3 ? 3 : (C <= 4 ? 4 : (C <= 6 ? 6 : 8)));
-  const int nchr = (nz + CR - 1) / CR;
-  const size_t smr = (size_t)nz * 6 * 16 * sizeof(V) + (size_t)(2 * nchr) * 16 * sizeof(Mom<V>) +
-                     (size_t)3 * 16 * sizeof(V) + (size_t)nz * sizeof(T);
-  if constexpr (sizeof(T) == 4) if (KT == 16 && C <= 8 && smr <= 227 * 1024) {
+  if constexpr (sizeof(T) == 4) if (d.reg) {
 #define DEPTHR(CV, EI)                                                                                          \
-  if (CR == CV && eps_in == EI) {                                                                               \
-    smem_cap(k_mindlin_depth_r<T, 16, CV, EI>); \
-    k_mindlin_depth_r<T, 16, CV, EI><<<grid, 16 * nchr, smr, c->stream>>>(                                       \
-        (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, n2, h1, nchr, w1, w2, (T)c->lam, (T)c->mu, (T)c->nu,  \
+  if (C == CV && eps_in == EI) {                                                                                \
+    smem_cap(k_mindlin_depth_r<T, 16, CV, EI>);                                                                 \
+    k_mindlin_depth_r<T, 16, CV, EI><<<grid, d.threads, d.smem, c->stream>>>(                                   \
+        (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, n2, h1, nch, w1, w2, (T)c->lam, (T)c->mu, (T)c->nu,   \
         out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz, zr);                                                    \
   }
     DEPTHR(2, false) DEPTHR(3, false) DEPTHR(4, false) DEPTHR(6, false) DEPTHR(8, false)
@@ -923,8 +964,8 @@ int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps
   }
 #define DEPTH(KTV, EI)                                                                                         \
   if (KT == KTV && eps_in == EI) {                                                                             \
-    smem_cap(k_mindlin_depth<T, KTV, EI>);  \
-    k_mindlin_depth<T, KTV, EI><<<grid, threads, smem, c->stream>>>(                                             \
+    smem_cap(k_mindlin_depth<T, KTV, EI>);                                                                     \
+    k_mindlin_depth<T, KTV, EI><<<grid, d.threads, d.smem, c->stream>>>(                                       \
         (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, n2, h1, C, nch, prow, w1, w2, (T)c->lam, (T)c->mu,   \
         (T)c->nu, out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz, zr);                                       \
   }

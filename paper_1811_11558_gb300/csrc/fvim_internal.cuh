@@ -408,7 +408,16 @@ struct fvim_ctx {
   long n_applies;  // Mindlin applies issued by the solvers
   int fft2_cl;     // whole-plane cluster FFTs usable: -1 not yet known, 0 no, 1 yes
   void* srt;       // solver runtime (solvers.cu): own stream, events, captured CUDA graphs
+  int depth_chunk; // depth nodes per chunk thread of the depth kernel; 0: depth_chunk_default
+  int plan_tuned;  // depth_chunk came from a timing run (fvim_autotune) in this process
 };
+
+// tile plan of the depth kernel (depth.cu): default chunk length, and whether a chunk length
+// gives a launchable configuration on this context's grid and precision
+int depth_chunk_default(int nz);
+bool depth_chunk_ok(const fvim_ctx* c, int chunk);
+// process-wide plan table (tune.cu): the tuned chunk length of a grid, or 0
+int plan_lookup(const fvim_ctx* c);
 
 // kernel kinds for fvim_profile_read
 enum ProfSlot {

@@ -48,6 +48,20 @@ class Report(ctypes.Structure):
                 "residual_evals": self.residual_evals, "mindlin_applies": self.mindlin_applies}
 
 
+PLAN_MAX_CAND = 8
+
+
+class Plan(ctypes.Structure):
+    """fvim_plan (include/fvim.h)."""
+    _fields_ = [("depth_chunk", ctypes.c_int), ("tuned", ctypes.c_int), ("n_cand", ctypes.c_int),
+                ("cand", ctypes.c_int * PLAN_MAX_CAND), ("cand_ms", ctypes.c_float * PLAN_MAX_CAND)]
+
+    def as_dict(self):
+        n = self.n_cand
+        return {"depth_chunk": self.depth_chunk, "tuned": bool(self.tuned),
+                "timings_ms": {int(self.cand[i]): float(self.cand_ms[i]) for i in range(n)}}
+
+
 class FvimError(RuntimeError):
     def __init__(self, status, what):
         msg = "%s failed: %s (status %d)" % (what, strerror(status), status)
@@ -91,6 +105,9 @@ def lib():
         "fvim_solve_contact": (i, [vp, vp, ctypes.POINTER(d), i, ctypes.POINTER(Opts), vp, ctypes.POINTER(Report)]),
         "fvim_reset_state": (i, [vp]),
         "fvim_footprint": (ctypes.c_size_t, [i, i, i, i]),
+        "fvim_autotune": (i, [vp, i, ctypes.POINTER(Plan)]),
+        "fvim_get_plan": (i, [vp, ctypes.POINTER(Plan)]),
+        "fvim_set_plan": (i, [vp, ctypes.POINTER(Plan)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -191,6 +208,26 @@ class Context:
             if cnt[s]:
                 out[name.decode()] = (ms[s], cnt[s])
         return out
+
+    def autotune(self, reps=20):
+        """Time the depth kernel's chunk lengths on this grid (on the current stream) and keep
+        the fastest for this context and later ones of the same grid; returns the plan."""
+        pl = Plan()
+        self._stream()
+        _check(lib().fvim_autotune(self._h, int(reps), ctypes.byref(pl)), "fvim_autotune")
+        return pl.as_dict()
+
+    @property
+    def plan(self):
+        pl = Plan()
+        _check(lib().fvim_get_plan(self._h, ctypes.byref(pl)), "fvim_get_plan")
+        return pl.as_dict()
+
+    def set_plan(self, depth_chunk=0):
+        """Force the depth chunk length on this context (0: the default rule)."""
+        pl = Plan()
+        pl.depth_chunk = int(depth_chunk)
+        _check(lib().fvim_set_plan(self._h, ctypes.byref(pl)), "fvim_set_plan")
 
     def last_kernel_count(self):
         return lib().fvim_last_kernel_count(self._h)

@@ -123,6 +123,28 @@ class Server:
         with self.pool_lock:
             self.pool.setdefault(req.shape, []).append((ctx, stream))
 
+    def prepare(self, requests, autotune=True, reps=20):
+        """Before serving: create one pooled context per distinct shape of `requests` and, with
+        autotune, time the depth kernel's tile plans on it while nothing else runs on the
+        device (fvim_autotune); later contexts of that grid start with the tuned plan, so
+        every request of a shape runs the same kernels alone and in a mix.  Returns
+        {shape index: plan}."""
+        torch = self.torch
+        plans = {}
+        seen = set()
+        for req in requests:
+            if req.shape in seen:
+                continue
+            seen.add(req.shape)
+            ctx, stream = self._context(req)
+            with torch.cuda.stream(stream):
+                if autotune and not ctx.plan["tuned"]:
+                    ctx.autotune(reps)
+            stream.synchronize()
+            plans[len(plans)] = dict(ctx.plan, n=req.n, nz=int(np.asarray(req.z).size), precision=req.precision)
+            self._recycle(req, ctx, stream)
+        return plans
+
     def solve(self, req, t0=None):
         """Solve one request (admission included); returns a Result."""
         torch = self.torch

@@ -61,3 +61,13 @@ def test_product_path_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", src, re.M), f
+
+
+def test_plan_entry_points_check_arguments_without_gpu():
+    from paper_1811_11558_gb300 import fvim
+
+    L = fvim.lib()
+    pl = fvim.Plan()
+    assert L.fvim_autotune(None, 10, ctypes.byref(pl)) == -1
+    assert L.fvim_get_plan(None, ctypes.byref(pl)) == -1
+    assert L.fvim_set_plan(None, ctypes.byref(pl)) == -1

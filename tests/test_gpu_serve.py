@@ -81,3 +81,26 @@ def test_new_shapes_arriving_while_others_capture_graphs():
     for a, m in zip(alone, mix):
         assert m is not None and m.report["n_increments"] == 2
         assert np.array_equal(a.pressure, m.pressure)
+
+
+def test_prepared_pool_runs_tuned_plans_alone_and_in_the_mix():
+    """Server.prepare tunes the depth kernel's tile plan once per shape before serving; every
+    later context of that grid starts with the tuned plan, so a request gives the same bits
+    alone (fresh server, fresh contexts) and in the mix."""
+    require_gpu()
+    from paper_1811_11558_gb300.serve import Request, Server
+
+    reqs = []
+    for i, (n, nz) in enumerate([(64, 10), (64, 14), (32, 9), (64, 10), (32, 9), (64, 14)]):
+        z = inputs.uniform_depth(nz, 0.5)
+        h = inputs.hertz_profile(n, n, 1.0, 1.0, 0.5)
+        reqs.append(Request(i, n, z, h, [1e-3 * (1 + i % 3), 3e-3], precision="fp32", sigma_y=0.05 * ES,
+                            E_h=0.1, opts={"max_iter": 100}))
+    srv = Server(slots=4)
+    plans = srv.prepare(reqs, reps=3)
+    assert len(plans) == 3 and all(p["tuned"] for p in plans.values())
+    mix, _ = srv.run(reqs)
+    alone = [Server(slots=1).solve(r) for r in reqs[:3]]
+    for a, m in zip(alone, mix[:3]):
+        assert np.array_equal(a.pressure, m.pressure)
+        assert a.report["alg1_iters"] == m.report["alg1_iters"]
