@@ -291,6 +291,7 @@ def run_gpu(args):
         line["solves"]["rough"] = rough_metrics()
         line["solves"]["stream"] = stream_metrics()
         line["solves"]["batch"] = batch_metrics()
+        line["solves"]["epp_sweep"] = epp_metrics()
         line["scaling_sweep"] = scaling_metrics()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sample_modes=256, sample_planes=None)
@@ -413,6 +414,49 @@ def rough_metrics(n=1024, nz=32, depth=0.05, seed=1813):
     return out
 
 
+def epp_metrics(n=128, nz=32, depth=0.25, ratios=(2.0, 4.0, 8.0, 16.0)):
+    """Elastic-perfectly-plastic Hertz load sweep (E_h = 0; the paper's App. C.2 comparison is
+    elastic-perfectly-plastic, on an 81 x 81 x 32 grid): paraboloid R = 0.5 on n x n, nz nodes to
+    the given depth, sigma_y = 0.05 E*, increments at W / W_y = ratios with W_y the elastic onset
+    load (p0 = 1.6 sigma_y).  FP32 and FP64 one solve each (tuned plans), with the peak pressure,
+    contact area and peak plastic strain of every increment taken from the FP32 run."""
+    import torch
+
+    from paper_1811_11558_gb300 import Context, inputs
+
+    es = E / (1 - NU * NU)
+    sy = 0.05 * es
+    a_y = np.pi * 0.5 * 1.6 * sy / (2 * es)
+    w_y = 2 * np.pi * a_y ** 2 * 1.6 * sy / 3
+    z = inputs.uniform_depth(nz, depth)
+    h = inputs.hertz_profile(n, n, 1.0, 1.0, 0.5)
+    out = {"workload": "epp_hertz_%dx%dx%d" % (n, n, nz), "W_over_W_y": list(ratios), "relax": 0.5}
+    press = {}
+    for prec in ("fp32", "fp64"):
+        ctx = Context(n, n, z, 1.0, 1.0, precision=prec, E=E, nu=NU, sigma_y=sy, E_h=0.0)
+        ctx.autotune()
+        hd = torch.from_numpy(h).to("cuda", ctx.dtype)
+        p = torch.empty(ctx.surf_shape, dtype=ctx.dtype, device="cuda")
+        opts = ctx.default_opts(relax=0.5, max_iter=200)
+        rows = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r in ratios:     # one increment per call (the state carries over), to read each state
+            rep = ctx.solve_contact(hd, [r * w_y], p, opts, allow_not_converged=True)
+            ep = torch.empty(ctx.scal_shape, dtype=ctx.dtype, device="cuda")
+            ctx.get_state(None, ep, None)
+            rows.append({"W_over_W_y": r, "p_max_over_sigma_y": float(p.max()) / sy,
+                         "area": rep["contact_area"][-1], "e_p_max": float(ep.max()),
+                         "alg1_iters": rep["alg1_iters"][-1], "status": rep["status"]})
+        torch.cuda.synchronize()
+        out[prec] = {"ms_per_sweep": 1e3 * (time.perf_counter() - t0), "increments": rows}
+        press[prec] = p.cpu().numpy().astype(np.float64)
+        ctx.close()
+    out["fp32_vs_fp64_pressure_rel_l2"] = float(np.linalg.norm(press["fp32"] - press["fp64"]) /
+                                                np.linalg.norm(press["fp64"]))
+    return out
+
+
 def batch_problems(n_prob=64, seed=1814):
     """Uneven elastic-plastic contact problems: grids n^2 with n drawn from {64, 128, 256, 512},
     nz from {8, 16, 32}; half paraboloids (R = 0.5, depth 0.5), half seeded self-affine surfaces
@@ -448,7 +492,7 @@ def batch_problems(n_prob=64, seed=1814):
     return probs
 
 
-def batch_metrics(n_prob=64, slots=16, seed=1814, max_iter=40, n64=4):
+def batch_metrics(n_prob=64, slots=16, seed=1814, max_iter=60, n64=4):
     """Batched uneven solves: n_prob problems (batch_problems) submitted at once to the
     server (slots contexts, one stream and one set of captured graphs each, FP32 operators,
     FP64 reductions), aggregate solves/s and per-problem latency; plain FP64 and FP32 one at a

@@ -117,6 +117,34 @@ def test_solve_contact_fp32_matches_oracle_hertz():
     assert np.abs(np.array(rep["contact_area"]) - g["areas"]).max() <= 1e-4 + 1.0 / 1024
 
 
+EPP = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "epp_hertz_32x32x8.npz")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_solve_contact_perfectly_plastic_sweep(prec):
+    """E_h = 0 (elastic-perfectly-plastic) Hertz sweep W / W_y = 2, 4, 8 on 32 x 32 x 8: the GPU
+    Algorithm 1 against the oracle's stored solution."""
+    torch = require_gpu()
+    g = np.load(EPP)
+    n, nz = 32, 8
+    z = inputs.uniform_depth(nz, float(g["depth"]))
+    h = inputs.hertz_profile(n, n, 1.0, 1.0, R)
+    ctx = _ctx(n, z, prec, sigma_y=float(g["sigma_y"]), E_h=0.0)
+    dt = ctx.dtype
+    p = torch.empty(ctx.surf_shape, dtype=dt, device="cuda")
+    kw = dict(cg_tol=1e-13, df_tol_rel=1e-11) if prec == "fp64" else {}
+    opts = ctx.default_opts(relax=float(g["relax"]), max_iter=400, **kw)
+    rep = ctx.solve_contact(to_dev(torch, h, dt), [float(w) for w in g["loads"]], p, opts)
+    ep = torch.empty(ctx.scal_shape, dtype=dt, device="cuda")
+    ctx.get_state(None, ep, None)
+    torch.cuda.synchronize()
+    assert rep["status"] == 0 and rep["n_increments"] == 3
+    tol = 1e-7 if prec == "fp64" else 2e-5
+    assert rel_l2(p.cpu().numpy(), g["p"]) < tol
+    assert rel_l2(ep.cpu().numpy(), g["e_p"]) < (1e-6 if prec == "fp64" else 1e-4)
+    assert np.abs(np.array(rep["contact_area"]) - g["areas"]).max() <= (0 if prec == "fp64" else 1.0 / 1024)
+
+
 ROUGH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rough_32x32x8.npz")
 
 
