@@ -414,12 +414,13 @@ def rough_metrics(n=1024, nz=32, depth=0.05, seed=1813):
     return out
 
 
-def epp_metrics(n=128, nz=32, depth=0.25, ratios=(2.0, 4.0, 8.0, 16.0)):
+def epp_metrics(n=128, nz=32, depth=0.25, ratios=(2.0, 3.0, 4.0)):
     """Elastic-perfectly-plastic Hertz load sweep (E_h = 0; the paper's App. C.2 comparison is
     elastic-perfectly-plastic, on an 81 x 81 x 32 grid): paraboloid R = 0.5 on n x n, nz nodes to
     the given depth, sigma_y = 0.05 E*, increments at W / W_y = ratios with W_y the elastic onset
     load (p0 = 1.6 sigma_y).  FP32 and FP64 one solve each (tuned plans), with the peak pressure,
-    contact area and peak plastic strain of every increment taken from the FP32 run."""
+    contact area and peak plastic strain of every increment, for both.  (At W / W_y = 8 on this
+    grid Algorithm 1 with relaxation 0.5 does not converge in either precision.)"""
     import torch
 
     from paper_1811_11558_gb300 import Context, inputs
@@ -437,7 +438,7 @@ def epp_metrics(n=128, nz=32, depth=0.25, ratios=(2.0, 4.0, 8.0, 16.0)):
         ctx.autotune()
         hd = torch.from_numpy(h).to("cuda", ctx.dtype)
         p = torch.empty(ctx.surf_shape, dtype=ctx.dtype, device="cuda")
-        opts = ctx.default_opts(relax=0.5, max_iter=200)
+        opts = ctx.default_opts(relax=0.5, max_iter=150)
         rows = []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
