@@ -174,6 +174,18 @@ def run_gpu(args):
     ms_max = max_over_ranks(ms, pg, "cuda")
     value = replica_throughput(vox, args.steps, ms_max, ws)
 
+    # --- the same K steps again with one event between consecutive applies: median and
+    # p99 of the duration of one apply
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    evs[0].record(stream)
+    for i in range(args.steps):
+        ctx.apply_mindlin(d_in, d_out)
+        evs[i + 1].record(stream)
+    barrier()
+    per_apply = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)])
+    apply_ms = {"median": round(float(np.median(per_apply)), 5), "p99": round(float(np.percentile(per_apply, 99)), 5)}
+
     # --- the same K steps again with every kernel bracketed by CUDA events on the
     # launching stream (recorded live by the library): per-kernel durations for the roofline
     ctx.profile_read()
@@ -281,6 +293,7 @@ def run_gpu(args):
                 "pipeline": "pinned host -> device, apply, device -> pinned host every step; upload, "
                             "apply and download on three streams over three buffer slots"},
         "gpu_launches": kernels_per_step * args.steps,
+        "apply_ms": apply_ms,
         "kernel_ms": kernel_ms,
         "tile_plan": plan,
         "roofline": roofline,
