@@ -573,11 +573,12 @@ def batch_metrics(n_prob=64, slots=16, seed=1814, max_iter=60, n64=4):
                             for pb, r in zip(probs, res)]}
 
 
-def stream_metrics(n_req=12, slots=8, seed=1815):
+def stream_metrics(n_req=12, slots=8, seed=1815, rate_sweep=(0.4, 1.0, 1.5)):
     """Served request stream, FP32 vs plain FP64: requests with grids drawn uniformly in log2
     from {128, 256}, nz = round(16 x 2^U) in [16, 32], seeded self-affine surfaces (H 0.8, rms
     slope 0.1), five-increment ramps to the paper's rough-surface load; Poisson arrivals at
-    0.7 x the single-stream FP32 capacity; p50 / p99 latency from arrival to result.  The FP64
+    0.7 x the single-stream FP32 capacity, then swept over rate_sweep x that capacity; p50 / p99
+    latency from arrival to result.  The FP64
     baseline solves the first four requests one at a time; its solves/s is the mix's mean
     service time per size class applied to the whole stream."""
     import torch
@@ -608,8 +609,18 @@ def stream_metrics(n_req=12, slots=8, seed=1815):
         r.arrival = float(a)
     res, wall = srv.run(reqs)
     lat = percentiles([r.latency for r in res])
-    sat, swall = srv.run([Request(r.rid, r.n, r.z, r.h, r.loads, precision="fp32", E=E, nu=NU, sigma_y=r.sigma_y,
-                                  E_h=r.E_h, opts=r.opts) for r in reqs])
+    def fresh(arrivals):
+        return [Request(r.rid, r.n, r.z, r.h, r.loads, precision="fp32", E=E, nu=NU, sigma_y=r.sigma_y,
+                        E_h=r.E_h, opts=r.opts, arrival=float(a)) for r, a in zip(reqs, arrivals)]
+
+    sat, swall = srv.run(fresh(np.zeros(n_req)))
+    # the arrival rate swept as a multiple of the single-stream capacity
+    sweep = []
+    for f in rate_sweep:
+        rs, rw = srv.run(fresh(poisson_arrivals(n_req, f * cap, seed + 1)))
+        lt = percentiles([r.latency for r in rs])
+        sweep.append({"rate_over_capacity": f, "arrival_rate_per_s": f * cap, "solves_per_s": n_req / rw,
+                      "p50_ms": 1e3 * lt[50], "p99_ms": 1e3 * lt[99]})
     # plain FP64, one request at a time
     from paper_1811_11558_gb300 import Context
 
@@ -634,6 +645,7 @@ def stream_metrics(n_req=12, slots=8, seed=1815):
             "nz": sorted({int(np.asarray(r.z).size) for r in reqs}), "slots": slots,
             "single_stream_fp32_solves_per_s": cap, "arrival_rate_per_s": rate,
             "fp32_served_poisson": {"solves_per_s": n_req / wall, "p50_ms": 1e3 * lat[50], "p99_ms": 1e3 * lat[99]},
+            "fp32_served_rate_sweep": sweep,
             "fp32_served_saturated": {"solves_per_s": n_req / swall,
                                       "p50_ms": 1e3 * percentiles([r.latency for r in sat])[50],
                                       "p99_ms": 1e3 * percentiles([r.latency for r in sat])[99]},
