@@ -53,24 +53,30 @@ __global__ void __launch_bounds__(512) k_cols_ct(typename Cx<T>::t* __restrict__
 }
 
 // FP32 column FFTs with 16-byte global accesses: a thread owns two adjacent columns (one
-// float4 per row holds both), so every load and store moves 16 bytes; 8 columns per CTA.
-// Interleaved exchange: entry p of column c at buf[p * 8 + c].
-struct ColPairSm {
+// float4 per row holds both), so every load and store moves 16 bytes; CW columns per CTA
+// (CW = 16: every row access of a CTA is one whole 128-byte line).
+// Interleaved exchange: entry p of column c at buf[p * CW + c].
+template <int CW> struct ColPairSm {
   float2* buf;
   int f2;  // column pair
-  __device__ __forceinline__ void put(int g, int p, float2 x) const { buf[p * 8 + 2 * f2 + g] = x; }
-  __device__ __forceinline__ float2 get(int g, int p) const { return buf[p * 8 + 2 * f2 + g]; }
+  __device__ __forceinline__ void put(int g, int p, float2 x) const { buf[p * CW + 2 * f2 + g] = x; }
+  __device__ __forceinline__ float2 get(int g, int p) const { return buf[p * CW + 2 * f2 + g]; }
 };
 
-template <bool INV, int N>
-__global__ void __launch_bounds__(N / 2) k_cols_v(float2* __restrict__ planes, const float2* __restrict__ tw,
-                                                  int h1, const int* __restrict__ zr) {
+template <int N, int CW> struct ColsV {
+  static constexpr int threads = N / 16 * CW;
+  static constexpr int min_blocks = CW == 16 ? 1024 / threads : 1;  // CW = 16: 64 registers
+};
+
+template <bool INV, int N, int CW>
+__global__ void __launch_bounds__(ColsV<N, CW>::threads, ColsV<N, CW>::min_blocks)
+    k_cols_v(float2* __restrict__ planes, const float2* __restrict__ tw, int h1, const int* __restrict__ zr) {
   if (zr && ((int)blockIdx.y / 6 < zr[0] || (int)blockIdx.y / 6 >= zr[1])) return;  // layer without input
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* sm = reinterpret_cast<float2*>(smraw);  // [N][8]
-  constexpr int T8 = N / 8;
-  const int f2 = threadIdx.x & 3, t = threadIdx.x >> 2;
-  float4* col = reinterpret_cast<float4*>(planes + (size_t)blockIdx.y * N * h1 + (size_t)blockIdx.x * 8 + 2 * f2);
+  float2* sm = reinterpret_cast<float2*>(smraw);  // [N][CW]
+  constexpr int T8 = N / 8, NP = CW / 2;
+  const int f2 = threadIdx.x % NP, t = threadIdx.x / NP;
+  float4* col = reinterpret_cast<float4*>(planes + (size_t)blockIdx.y * N * h1 + (size_t)blockIdx.x * CW + 2 * f2);
   const size_t rs = (size_t)h1 / 2;  // row stride in float4
   float2 v[2][8];
 #pragma unroll
@@ -79,7 +85,7 @@ __global__ void __launch_bounds__(N / 2) k_cols_v(float2* __restrict__ planes, c
     v[0][m] = make_float2(a.x, a.y);
     v[1][m] = make_float2(a.z, a.w);
   }
-  ColPairSm x{sm, f2};
+  ColPairSm<CW> x{sm, f2};
   fft_ct<float2, INV, N, 2, 1>(v, t, x, tw);
 #pragma unroll
   for (int m = 0; m < 8; ++m) col[(size_t)(t + m * T8) * rs] = make_float4(v[0][m].x, v[0][m].y, v[1][m].x, v[1][m].y);
@@ -294,19 +300,29 @@ inline int ct_rows(int n1, int n2) {
   return rb;
 }
 
+template <int N, int CW> void cols_v_launch(const fvim_ctx* c, bool inverse, void* planes, int nplanes, const int* zr) {
+  dim3 grid(c->h1 / CW, nplanes);
+  const size_t sm = (size_t)N * CW * sizeof(float2);
+  if (inverse) {
+    smem_attr(k_cols_v<true, N, CW>, sm);
+    k_cols_v<true, N, CW><<<grid, ColsV<N, CW>::threads, sm, c->stream>>>((float2*)planes, (const float2*)c->tw2,
+                                                                          c->h1, zr);
+  } else {
+    smem_attr(k_cols_v<false, N, CW>, sm);
+    k_cols_v<false, N, CW><<<grid, ColsV<N, CW>::threads, sm, c->stream>>>((float2*)planes, (const float2*)c->tw2,
+                                                                           c->h1, zr);
+  }
+}
+
 template <typename T, int N> void cols_n(const fvim_ctx* c, bool inverse, void* planes, int nplanes, const int* zr) {
   typedef typename Cx<T>::t V;
   if constexpr (sizeof(T) == 4 && N >= 64) {
+    if (N <= 512 && c->h1 % 16 == 0) {
+      cols_v_launch<N, 16>(c, inverse, planes, nplanes, zr);
+      return;
+    }
     if (c->h1 % 8 == 0) {
-      dim3 grid(c->h1 / 8, nplanes);
-      const size_t sm = (size_t)N * 8 * sizeof(float2);
-      if (inverse) {
-        smem_attr(k_cols_v<true, N>, sm);
-        k_cols_v<true, N><<<grid, N / 2, sm, c->stream>>>((float2*)planes, (const float2*)c->tw2, c->h1, zr);
-      } else {
-        smem_attr(k_cols_v<false, N>, sm);
-        k_cols_v<false, N><<<grid, N / 2, sm, c->stream>>>((float2*)planes, (const float2*)c->tw2, c->h1, zr);
-      }
+      cols_v_launch<N, 8>(c, inverse, planes, nplanes, zr);
       return;
     }
   }
