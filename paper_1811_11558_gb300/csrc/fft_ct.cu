@@ -326,7 +326,7 @@ template <typename T, int N> void cols_n(const fvim_ctx* c, bool inverse, void* 
       return;
     }
   }
-  int kc = (int)(64 / sizeof(V));
+  int kc = (int)(128 / sizeof(V));  // 128-byte rows
   while (kc > 1 && kc * (N / 8) > 512) kc >>= 1;
   if (kc > c->h1) kc = c->h1;
   const int threads = kc * (N / 8);
@@ -388,7 +388,7 @@ template <typename T> bool launch_cols_ct(const fvim_ctx* c, bool inverse, void*
 
 template <typename T, int N> void cols_conv_n(const fvim_ctx* c) {
   typedef typename Cx<T>::t V;
-  int kc = (int)(64 / sizeof(V));
+  int kc = (int)(128 / sizeof(V));  // 128-byte rows
   while (kc > 1 && kc * (N / 8) > 512) kc >>= 1;
   if (kc > c->h1) kc = c->h1;
   const size_t smem = (size_t)kc * N * sizeof(V);
