@@ -40,7 +40,8 @@ def test_uneven_batch_is_seeded_and_spans_the_stated_mix():
 
 
 def test_rough_surfaces_of_the_batch_have_the_stated_slope():
-    """Spectral rms slope sqrt(mean |grad h|^2) = 0.1 for every self-affine surface of the batch."""
+    """Spectral rms slope sqrt(mean |grad h|^2) = 0.1 for the self-affine surfaces among the first
+    twelve problems."""
     for p in bench.batch_problems()[:12]:
         if not p["rough"]:
             continue
