@@ -766,11 +766,22 @@ __global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* _
   // 5. forward over the chunk: - branch from its carry (scan value of the chunk above),
   //    + branch = own part + carry from below propagated up, image term, epilogue, rotate
   //    back, store
-  Mom<V> A, Pin;
+  //    (the carry from below is folded into the per-node + branch first, so that it is not
+  //    live during the output loop)
+  if (ch + 1 < nch) {
+    const Mom<V> Pin = SP[(ch + 1) * KT + kt];
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+      if (n0 + l < nend) {
+        Mom<V> P = Pin;
+        propP(P, g.q * (zs[e1] - zs[n0 + l]));
+        mom_add(Ploc[l], P);
+      }
+    }
+  }
+  Mom<V> A;
   if (ch > 0) A = SA[(ch - 1) * KT + kt];
   else mom_zero(A);
-  if (ch + 1 < nch) Pin = SP[(ch + 1) * KT + kt];
-  else mom_zero(Pin);
   V tr[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) tr[j] = TR[3 * kt + j];
@@ -782,9 +793,7 @@ __global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* _
   for (int l = 0; l < C; ++l) {
     const int i = n0 + l;
     if (i < nend) {
-      Mom<V> P = Pin;
-      propP(P, g.q * (zs[e1] - zs[i]));
-      mom_add(P, Ploc[l]);
+      const Mom<V>& P = Ploc[l];
       V e[6];
       kelvin_strain<T, V>(A, P, w, g.q, nu, mu, e);
       if (!uniform && l > 0) ex = dexp<T>(-g.q * zs[i]);
