@@ -179,6 +179,12 @@ typedef struct fvim_plan {
  * (the plan is then unchanged). */
 int fvim_autotune(fvim_ctx* ctx, int reps, fvim_plan* out);
 
+/* fvim_plan_candidates -- the chunk lengths fvim_autotune would time on a grid (n1, n2, nz,
+ * precision as in fvim_create), in timing order, written to chunks[0..] (host, at most
+ * max_chunks); returns their number.  Host computation only (no device, no context).
+ * FVIM_ERR_ARG on a grid fvim_create refuses or a bad output array. */
+int fvim_plan_candidates(int n1, int n2, int nz, int precision, int* chunks, int max_chunks);
+
 /* fvim_get_plan -- the plan ctx uses (host out; cand fields zero). */
 int fvim_get_plan(const fvim_ctx* ctx, fvim_plan* out);
 

@@ -129,6 +129,24 @@ int fvim_autotune(fvim_ctx* c, int reps, fvim_plan* out) {
   return FVIM_OK;
 }
 
+int fvim_plan_candidates(int n1, int n2, int nz, int precision, int* chunks, int max_chunks) {
+  if (n1 < 4 || n2 < 2 || (n1 & (n1 - 1)) || (n2 & (n2 - 1)) || n1 > 1024 || n2 > 1024 || nz < 2 || nz > 512)
+    return FVIM_ERR_ARG;
+  if ((precision != FVIM_FP32 && precision != FVIM_FP64) || !chunks || max_chunks < 1) return FVIM_ERR_ARG;
+  // the launch rules need the grid and precision only: a host-side description of the grid
+  fvim_ctx g;
+  memset(&g, 0, sizeof(g));
+  g.n1 = n1;
+  g.n2 = n2;
+  g.nz = nz;
+  g.h1 = n1 / 2;
+  g.prec = precision;
+  const std::vector<int> cand = candidates(&g);
+  const int n = (int)cand.size() < max_chunks ? (int)cand.size() : max_chunks;
+  for (int i = 0; i < n; ++i) chunks[i] = cand[i];
+  return n;
+}
+
 int fvim_get_plan(const fvim_ctx* c, fvim_plan* out) {
   if (!c || !out) return FVIM_ERR_ARG;
   memset(out, 0, sizeof(*out));

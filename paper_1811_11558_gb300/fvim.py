@@ -62,6 +62,15 @@ class Plan(ctypes.Structure):
                 "timings_ms": {int(self.cand[i]): float(self.cand_ms[i]) for i in range(n)}}
 
 
+def plan_candidates(n1, n2, nz, precision="fp32"):
+    """Chunk lengths the depth-kernel tuner times on this grid (host computation only)."""
+    buf = (ctypes.c_int * PLAN_MAX_CAND)()
+    prec = FVIM_FP32 if precision == "fp32" else FVIM_FP64
+    n = lib().fvim_plan_candidates(int(n1), int(n2), int(nz), prec, buf, PLAN_MAX_CAND)
+    _check(n if n < 0 else 0, "fvim_plan_candidates")
+    return list(buf[:n])
+
+
 class FvimError(RuntimeError):
     def __init__(self, status, what):
         msg = "%s failed: %s (status %d)" % (what, strerror(status), status)
@@ -107,6 +116,7 @@ def lib():
         "fvim_footprint": (ctypes.c_size_t, [i, i, i, i]),
         "fvim_autotune": (i, [vp, i, ctypes.POINTER(Plan)]),
         "fvim_get_plan": (i, [vp, ctypes.POINTER(Plan)]),
+        "fvim_plan_candidates": (i, [i, i, i, i, ctypes.POINTER(i), i]),
         "fvim_set_plan": (i, [vp, ctypes.POINTER(Plan)]),
     }
     for name, (res, args) in sig.items():

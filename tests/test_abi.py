@@ -71,3 +71,23 @@ def test_plan_entry_points_check_arguments_without_gpu():
     assert L.fvim_autotune(None, 10, ctypes.byref(pl)) == -1
     assert L.fvim_get_plan(None, ctypes.byref(pl)) == -1
     assert L.fvim_set_plan(None, ctypes.byref(pl)) == -1
+
+
+def test_plan_candidates_follow_the_launch_limits():
+    """Host-only query of the chunk lengths the tuner times: a chunk length is launchable when
+    the chunk threads of a 16-column tile fit one 256-thread block and the tile fits in shared
+    memory; the default rule max(2, ceil(Nz / 16)) is always among them."""
+    import pytest
+    from paper_1811_11558_gb300 import fvim
+
+    for n, nz, prec in [(512, 64, "fp32"), (512, 32, "fp32"), (64, 8, "fp32"), (128, 28, "fp64"),
+                        (32, 300, "fp32"), (32, 300, "fp64"), (4, 2, "fp64")]:
+        c = fvim.plan_candidates(n, n, nz, prec)
+        assert max(2, -(-nz // 16)) in c and all(2 <= x <= nz for x in c) and len(set(c)) == len(c)
+    # Nz = 64 in FP32: 2 and 3 nodes per chunk would need 32 and 22 chunk threads per column
+    assert fvim.plan_candidates(512, 512, 64, "fp32") == [4, 6, 8, 12, 16]
+    assert fvim.plan_candidates(64, 64, 8, "fp32") == [2, 3, 4, 6, 8]
+    with pytest.raises(fvim.FvimError):
+        fvim.plan_candidates(6, 8, 8)
+    with pytest.raises(fvim.FvimError):
+        fvim.plan_candidates(8, 8, 1)

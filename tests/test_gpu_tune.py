@@ -81,6 +81,9 @@ def test_autotune_keeps_the_fastest_per_grid():
     pl = ctx.autotune(reps=5)
     t = pl["timings_ms"]
     assert pl["tuned"] and pl["depth_chunk"] in t and len(t) >= 4
+    from paper_1811_11558_gb300 import fvim
+
+    assert sorted(t) == sorted(fvim.plan_candidates(128, 64, 28, "fp32"))
     assert all(v > 0 for v in t.values())
     # the default rule (2 here) stays unless another length is more than 2 % faster
     assert pl["depth_chunk"] == 2 or t[pl["depth_chunk"]] < 0.98 * t[2]
