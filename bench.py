@@ -271,6 +271,9 @@ def run_gpu(args):
         "avg_launch_ms": round(avg_ms, 5),
     }
     kernel_ms = {k: round(v[0] / v[1], 5) for k, v in prof.items()}
+    # every kernel of the apply moves the whole field once (48 B per voxel): its fraction of the
+    # measured copy bandwidth
+    kernel_frac = {k: round(alg_bytes / (v[0] / v[1] / 1e3) / 1e9 / peak, 4) for k, v in prof.items()}
 
     line = {
         "metric": METRIC,
@@ -295,6 +298,7 @@ def run_gpu(args):
         "gpu_launches": kernels_per_step * args.steps,
         "apply_ms": apply_ms,
         "kernel_ms": kernel_ms,
+        "kernel_hbm_frac": kernel_frac,
         "tile_plan": plan,
         "roofline": roofline,
         "clocks": clocks,
