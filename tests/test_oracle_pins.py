@@ -214,11 +214,11 @@ def test_free_surface_and_real_output(n1, n2, monkeypatch):
         assert np.abs(top[c]).max() < 1e-12 * np.abs(w).max()
 
 
-def test_translation_invariance_and_linearity_bruteforce():
-    """Brute force on a 4x4x3 grid (Sec. 1.3 translation invariance; Thm 1 linearity):
-    the operator assembled column by column from unit impulses is circulant in-plane,
-    linear, and maps real fields to real fields."""
-    n1 = n2 = 4
+@pytest.mark.parametrize("n1,n2", [(4, 4), (5, 3)])
+def test_translation_invariance_and_linearity_bruteforce(n1, n2):
+    """Brute force on 4x4x3 and 5x3x3 grids (Sec. 1.3 translation invariance; Thm 1
+    linearity): the operator assembled column by column from unit impulses is circulant
+    in-plane and linear."""
     z = np.array([0.0, 0.1, 0.25])
     nz = z.size
     rng = np.random.default_rng(5)
