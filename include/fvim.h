@@ -50,7 +50,7 @@ enum {
   FVIM_ERR_NONFINITE = -4,     /* non-finite value detected                        */
   FVIM_ERR_NOT_CONVERGED = -5, /* iteration cap reached before the tolerance       */
   FVIM_ERR_TIMEOUT = -6,       /* bounded device wait expired                      */
-  FVIM_ERR_UNSUPPORTED = -7    /* valid request this build does not support       */
+  FVIM_ERR_UNSUPPORTED = -7    /* valid request the library does not support      */
 };
 
 typedef struct fvim_ctx fvim_ctx;

@@ -24,7 +24,7 @@ Method (the paper's, in its order; no blocking, fusion or cutoff):
    * Nyquist modes: no operator contribution (they are not in Z^2_N).
 4. sigma = C:grad^sym N[w] - w (Sec. 6.1), or the strain grad^sym N[w]; inverse DFT.
 
-Readings of the paper where it is silent or garbled (each stated again in the design doc):
+Readings of the paper where it is silent or garbled:
 * no 1/(4 pi^2) factor in front of the Fourier series (Thm 1 / App. B garble);
 * every Delta of the Kelvin kernel is taken at -q, the Boussinesq kernel of the image
   term at +q (the standard convolution of a surface traction with B);
