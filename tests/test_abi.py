@@ -91,3 +91,18 @@ def test_plan_candidates_follow_the_launch_limits():
         fvim.plan_candidates(6, 8, 8)
     with pytest.raises(fvim.FvimError):
         fvim.plan_candidates(8, 8, 1)
+
+
+def test_no_cpu_fallback():
+    """Without a CUDA device the binding refuses to build a context, and it never accepts host
+    tensors as device buffers: there is no CPU path to fall back on."""
+    import numpy as np
+    import pytest
+    torch = pytest.importorskip("torch")
+    from paper_1811_11558_gb300 import fvim
+
+    with pytest.raises(TypeError):
+        fvim._ptr(torch.zeros(3), torch.float32, (3,), "x")
+    if not torch.cuda.is_available():
+        with pytest.raises(RuntimeError):
+            fvim.Context(8, 8, np.array([0.0, 0.1]))
