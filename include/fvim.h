@@ -66,7 +66,9 @@ typedef struct fvim_ctx fvim_ctx;
  *   precision  FVIM_FP32 or FVIM_FP64: element type of every array argument.
  *   stream     cudaStream_t to enqueue on (NULL = legacy default stream).
  * The context allocates its scratch on the current CUDA device (FVIM_ERR_OOM if
- * that fails).  Material defaults: E = 1, nu = 0.3, sigma_y = inf, E_h = 0.
+ * that fails).  Material defaults: E = 1, nu = 0.3, sigma_y = inf, E_h = 0.  A grid
+ * whose depth-kernel tile plan was tuned earlier in this process (fvim_autotune) starts
+ * with that plan.
  */
 int fvim_create(fvim_ctx** out, int n1, int n2, int nz, const double* z_nodes,
                 double L1, double L2, int precision, void* stream);
