@@ -413,3 +413,112 @@ def test_mindlin_cheng_on_axis_derivation():
         e11 = (4 * 0.3 - 3) / (zf + cv) ** 3 + 6 * cv / (zf + cv) ** 4 + 1 / abs(zf - cv) ** 3
         assert abs(s33v - e33) < 1e-12
         assert abs(s11v - e11) < 1e-12
+
+
+# Real-space single-mode pins on a non-square cell (Sec. 3.1 periodic cell and DFT, Thm 1).
+# The whole apply (DFT of the nodal values, mode grid, per-mode operator, inverse DFT and
+# its 1/(N1 N2)) is driven with a field that holds one in-plane mode, and the real-space
+# output is compared, node by node, with the independent Navier-ODE solve of that mode.
+# N1 != N2 and L1 != L2, so pairing k1 with L2 (or k2 with L1), a wrong DFT normalisation,
+# a missing conjugate mode or a transposed axis each change the result by O(1).
+SM_GRID = dict(n1=8, n2=6, L1=1.3, L2=0.7)
+SM_Z = np.array([0.0, 0.04, 0.1, 0.19, 0.3])
+SM_MODES = [(1, 0), (0, 1), (2, -1)]
+
+
+def _single_mode_case(k1, k2, seed):
+    n1, n2, L1, L2 = SM_GRID["n1"], SM_GRID["n2"], SM_GRID["L1"], SM_GRID["L2"]
+    q1, q2 = 2 * np.pi * k1 / L1, 2 * np.pi * k2 / L2
+    x1 = np.arange(n1) * L1 / n1
+    x2 = np.arange(n2) * L2 / n2
+    phase = np.exp(1j * (q2 * x2[:, None] + q1 * x1[None, :]))   # [N2, N1]
+    rng = np.random.default_rng(seed)
+    c6 = (rng.standard_normal((SM_Z.size, 6)) + 1j * rng.standard_normal((SM_Z.size, 6))) * 1e-3
+    eps_p = (c6[:, :, None, None] * phase[None, None]).real        # [Nz, 6, N2, N1]
+    return q1, q2, phase, c6, eps_p
+
+
+def _hooke6_c(e6):
+    """lambda tr(e) I + 2 mu e on six stored components (last axis)."""
+    w = 2 * MU * e6
+    w[..., :3] += LAM * (e6[..., 0] + e6[..., 1] + e6[..., 2])[..., None]
+    return w
+
+
+def _grad_to_strain6(g):
+    """sym(grad u) of [.., 3, 3] gradients as six stored components."""
+    pairs = ((0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1))
+    return np.stack([0.5 * (g[..., i, j] + g[..., j, i]) for i, j in pairs], axis=-1)
+
+
+def _single_mode_mindlin_error(k1, k2, seed=11):
+    n1, n2, L1, L2 = SM_GRID["n1"], SM_GRID["n2"], SM_GRID["L1"], SM_GRID["L2"]
+    q1, q2, phase, c6, eps_p = _single_mode_case(k1, k2, seed)
+    w6 = _hooke6_c(c6)
+    g, u = ode.solve_mode(q1, q2, SM_Z, w6, LAM, MU)
+    e6 = _grad_to_strain6(g)                                        # [Nz, 6]
+    s6 = _hooke6_c(e6) - w6
+    want_e = (e6[:, :, None, None] * phase[None, None]).real
+    want_s = (s6[:, :, None, None] * phase[None, None]).real
+    want_u3 = (u[0, 2] * phase).real
+    got_e = op.mindlin_apply(eps_p, SM_Z, L1, L2, E, NU, "strain")
+    got_s, got_u3 = op.mindlin_apply(eps_p, SM_Z, L1, L2, E, NU, "stress", with_surface=True)
+    return (np.abs(got_e - want_e).max() / np.abs(want_e).max(),
+            np.abs(got_s - want_s).max() / np.abs(want_s).max(),
+            np.abs(got_u3 - want_u3).max() / np.abs(want_u3).max())
+
+
+@pytest.mark.parametrize("k1,k2", SM_MODES)
+def test_single_mode_real_space_mindlin_non_square_cell(k1, k2):
+    """Sec. 3.1 (cell ]-L1/2, L1/2[ x ]-L2/2, L2/2[, modes q = 2 pi (k1/L1, k2/L2), DFT of
+    the nodal values) with Thm 1: a one-mode plastic strain on an 8x6 grid of a 1.3 x 0.7
+    cell gives, at every voxel, the strain, the stress sigma = C:eps - w and the surface u3
+    of the Navier-ODE solution of that mode (App. B), to 1e-11."""
+    err = _single_mode_mindlin_error(k1, k2)
+    assert max(err) < 1e-11, err
+
+
+@pytest.mark.parametrize("k1,k2", SM_MODES)
+def test_single_mode_real_space_boussinesq_non_square_cell(k1, k2):
+    """Eq. (M:conv) and Eq. (B:fourier) on the same non-square cell: a one-mode surface
+    pressure gives the Navier-ODE strain at every node and the surface u3, to 1e-11."""
+    n1, n2, L1, L2 = SM_GRID["n1"], SM_GRID["n2"], SM_GRID["L1"], SM_GRID["L2"]
+    q1, q2 = 2 * np.pi * k1 / L1, 2 * np.pi * k2 / L2
+    x1 = np.arange(n1) * L1 / n1
+    x2 = np.arange(n2) * L2 / n2
+    phase = np.exp(1j * (q2 * x2[:, None] + q1 * x1[None, :]))
+    P = 0.4 - 0.9j
+    p = (P * phase).real
+    g, u = ode.solve_mode(q1, q2, SM_Z, np.zeros((SM_Z.size, 6)), LAM, MU, t_applied=[0, 0, P])
+    e6 = _grad_to_strain6(g)
+    want_e = (e6[:, :, None, None] * phase[None, None]).real
+    want_u3 = (u[0, 2] * phase).real
+    got_u3, got_e = op.boussinesq_apply(p, SM_Z, L1, L2, E, NU, "strain")
+    assert np.abs(got_e - want_e).max() < 1e-11 * np.abs(want_e).max()
+    assert np.abs(got_u3 - want_u3).max() < 1e-11 * np.abs(want_u3).max()
+
+
+def test_planted_cell_length_swap_is_caught(monkeypatch):
+    """A plausible mistake in the mode grid (k1 paired with L2 and k2 with L1) fails the
+    real-space single-mode pin above by O(1) on every mode it changes."""
+    orig = op.mode_grid
+    monkeypatch.setattr(op, "mode_grid", lambda N1, N2, L1, L2: orig(N1, N2, L2, L1))
+    op._MODE_CACHE.clear()
+    try:
+        for k1, k2 in SM_MODES:
+            assert max(_single_mode_mindlin_error(k1, k2)) > 1e-2
+    finally:
+        op._MODE_CACHE.clear()
+
+
+def test_planted_dft_normalisation_error_is_caught(monkeypatch):
+    """A plausible mistake in the DFT assembly (the inverse transform's 1/(N1 N2) dropped,
+    or applied twice) fails the real-space single-mode pin."""
+    ifft2 = np.fft.ifft2
+    n = SM_GRID["n1"] * SM_GRID["n2"]
+    for f in (n, 1.0 / n):
+        monkeypatch.setattr(op.np.fft, "ifft2", lambda a, *args, _f=f, **kw: ifft2(a, *args, **kw) * _f)
+        try:
+            assert max(_single_mode_mindlin_error(1, 0)) > 1e-2
+        finally:
+            monkeypatch.undo()
