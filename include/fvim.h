@@ -118,14 +118,18 @@ int fvim_return_map(fvim_ctx* ctx, const void* d_eps, void* d_eps_p, void* d_ep)
  * e_p += d_ep (Sec. 4.2 update(S)).  d_eps, d_eps_p: [Nz][6][N2][N1]; d_ep: [Nz][N2][N1]. */
 int fvim_commit_state(fvim_ctx* ctx, const void* d_eps, const void* d_eps_p, const void* d_ep);
 
-/* fvim_get_state / fvim_set_state -- device-to-device copies of the plastic state:
- * eps_p [Nz][6][N2][N1] (accumulated plastic strain), e_p [Nz][N2][N1],
- * sigma [Nz][6][N2][N1].  Any pointer may be NULL to skip that field. */
+/* fvim_get_state / fvim_set_state -- device-to-device copies of the plastic state S_n of
+ * Sec. 4.2 (the state S that Algorithm 1 of Sec. 5.2 updates after each converged
+ * increment): eps_p [Nz][6][N2][N1] (accumulated plastic strain), e_p [Nz][N2][N1]
+ * (cumulated plastic strain of the hardening law, Sec. 4.1), and sigma [Nz][6][N2][N1],
+ * the stress of the last converged increment that the trial stress of the return map
+ * starts from.  Any pointer may be NULL to skip that field. */
 int fvim_get_state(fvim_ctx* ctx, void* eps_p, void* e_p, void* sigma);
 int fvim_set_state(fvim_ctx* ctx, const void* eps_p, const void* e_p, const void* sigma);
 
-/* fvim_reset_state -- virgin state: eps_p = 0, e_p = 0, sigma = 0 and no contact pressure
- * (stream ordered).  Lets one context serve a sequence of independent problems. */
+/* fvim_reset_state -- virgin state S_0 of Algorithm 1 (Sec. 5.2): eps_p = 0, e_p = 0,
+ * sigma = 0 and no contact pressure (stream ordered).  Lets one context serve a sequence
+ * of independent problems. */
 int fvim_reset_state(fvim_ctx* ctx);
 
 /* fvim_footprint -- device bytes a context of this grid and precision holds once its
@@ -211,9 +215,13 @@ const char* fvim_profile_name(int slot);
 
 /* ------------------------------------------------------------------------------------
  * Solvers.  Vectors live on the device in the context's precision; every reduction
- * (dot products, norms, the total load) is accumulated in FP64 in a fixed order, so
- * repeated runs give bitwise identical results.  The loops run on the host and read
- * back a few FP64 scalars per iteration; every loop has an iteration cap.
+ * (dot products, norms, the total load) is accumulated in FP64 in a fixed order (block
+ * partials summed in block order by the last block to finish), so repeated runs give
+ * bitwise identical results.  The iteration logic runs on the device: the contact CG's
+ * scalars (step, conjugation, rigid shift, load scaling, stop test) are kept in device
+ * memory and the host reads one small status block per batch of iterations; DF-SANE's
+ * line search runs inside one captured CUDA graph (a device-side loop) and the host
+ * reads its state once per solve.  Every loop has an iteration cap.
  * ------------------------------------------------------------------------------------ */
 #define FVIM_MAX_INCREMENTS 64
 
@@ -301,8 +309,12 @@ int fvim_solve_contact(fvim_ctx* ctx, const void* h, const double* loads, int n_
  * Returns FVIM_ERR_UNSUPPORTED, before any device work, when the scratch the grid needs
  * exceeds FVIM_NOALLOC_SCRATCH_BYTES (e.g. 128 x 128 x 32 fits in FP32, 512 x 512 x 64
  * does not).  It never calls cudaMalloc, cudaFree or any allocating routine.
- * The first call on each device looks up the array's device address (cudaGetSymbolAddress,
- * with that device current); make that first call before any stream capture.
+ * Every call looks up the array's device address in the current context
+ * (cudaGetSymbolAddress, a host-side lookup that allocates nothing), so a device reset or
+ * a caller's own context never sees a stale address.  The first call on a device may load
+ * the library's device code there: make that first call before any stream capture.
+ * The depth nodes travel as a kernel argument (no host-to-device copy), and a grid tuned
+ * earlier in the process (fvim_autotune) runs its tuned depth tile plan.
  * Every call shares the one array and leaves its contents behind (each call overwrites
  * every region before reading it, so nothing has to be cleared): two calls that overlap
  * on the GPU (different streams, or different host threads on one device) race on it.

@@ -11,11 +11,12 @@
 //
 // The array lives in every device that loads the library until the process exits.
 // Host code must not use the symbol's name as a device address: its device address is
-// fetched once per device with cudaGetSymbolAddress, with that device current.
+// looked up with cudaGetSymbolAddress, with the caller's device current, on every call.
+// The lookup is host-side and allocates nothing; it is not cached, because the address
+// belongs to the current context (a cudaDeviceReset, or a caller running in a context of
+// its own on the same device, loads the module again, possibly at another address).
 #include <math.h>
 #include <string.h>
-
-#include <mutex>
 
 #include "fvim_internal.cuh"
 
@@ -23,24 +24,20 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[FVIM_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// device address of the scratch array on the current device (set up on first use)
+// device address of the scratch array in the current context
 int scratch_address(void** out) {
-  int dev = 0;
-  if (FVIM_CU(cudaGetDevice(&dev))) return FVIM_ERR_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return FVIM_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    if (FVIM_CU(cudaGetSymbolAddress(&p, g_noalloc_scratch)) || !p) return FVIM_ERR_CUDA;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  void* p = nullptr;
+  if (FVIM_CU(cudaGetSymbolAddress(&p, g_noalloc_scratch)) || !p) return FVIM_ERR_CUDA;
+  *out = p;
   return FVIM_OK;
 }
+
+// depth nodes passed by value as a kernel argument (4 KB at most), so that no host-to-device
+// copy from the caller's pageable array is needed
+constexpr int kMaxNodes = 512;
+struct Nodes {
+  double z[kMaxNodes];
+};
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -53,20 +50,18 @@ template <typename T> __global__ void k_twiddles(typename Cx<T>::t* tw, int n) {
   tw[k] = mk<typename Cx<T>::t>((T)c, (T)s);
 }
 
-template <typename T> __global__ void k_nodes(T* zd, const double* __restrict__ zs, int nz) {
+template <typename T> __global__ void k_nodes(T* zd, const __grid_constant__ Nodes zs, int nz) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nz) zd[i] = (T)zs[i];
+  if (i < nz) zd[i] = (T)zs.z[i];
 }
 
 template <typename T>
 int run(fvim_ctx* c, unsigned char* base, const T* eps_p, T* out, int kind, T* u3) {
   typedef typename Cx<T>::t V;
   const int n1 = c->n1, n2 = c->n2, nz = c->nz;
-  // layout of the scratch: depth nodes (double copy + T), twiddles, spectrum, Nyquist rows,
-  // surface spectrum; every region is written before it is read, nothing needs zeroing
+  // layout of the scratch: depth nodes, twiddles, spectrum, Nyquist rows, surface spectrum;
+  // every region is written before it is read, nothing needs zeroing
   size_t off = 0;
-  double* zsrc = (double*)(base + off);
-  off += align256((size_t)nz * sizeof(double));
   c->z_dev = base + off;
   off += align256((size_t)nz * sizeof(T));
   c->tw1 = base + off;
@@ -82,9 +77,10 @@ int run(fvim_ctx* c, unsigned char* base, const T* eps_p, T* out, int kind, T* u
   c->surf_nq = base + off;
   off += align256((size_t)n2 * sizeof(T));
   if (off > (size_t)FVIM_NOALLOC_SCRATCH_BYTES) return FVIM_ERR_UNSUPPORTED;
-  if (FVIM_CU(cudaMemcpyAsync(zsrc, c->z_host, (size_t)nz * sizeof(double), cudaMemcpyHostToDevice, c->stream)))
-    return FVIM_ERR_CUDA;
-  k_nodes<T><<<(nz + 127) / 128, 128, 0, c->stream>>>((T*)c->z_dev, zsrc, nz);
+  Nodes zn;
+  memset(&zn, 0, sizeof(zn));
+  memcpy(zn.z, c->z_host, (size_t)nz * sizeof(double));
+  k_nodes<T><<<(nz + 127) / 128, 128, 0, c->stream>>>((T*)c->z_dev, zn, nz);
   k_twiddles<T><<<(n1 + 127) / 128, 128, 0, c->stream>>>((V*)c->tw1, n1);
   k_twiddles<T><<<(n2 + 127) / 128, 128, 0, c->stream>>>((V*)c->tw2, n2);
   FVIM_CUDA_CHECK_LAUNCH();
@@ -109,7 +105,7 @@ extern "C" int fvim_apply_mindlin_noalloc(int n1, int n2, int nz, const double* 
                                           double E, double nu, int precision, const void* eps_p, void* out,
                                           int out_kind, void* u3_surface, void* stream) {
   if (!pow2(n1) || !pow2(n2) || n1 < 4 || n2 < 2 || n1 > 1024 || n2 > 1024) return FVIM_ERR_ARG;
-  if (nz < 2 || nz > 512 || !z_nodes || !(L1 > 0) || !(L2 > 0)) return FVIM_ERR_ARG;
+  if (nz < 2 || nz > kMaxNodes || !z_nodes || !(L1 > 0) || !(L2 > 0)) return FVIM_ERR_ARG;
   if (precision != FVIM_FP32 && precision != FVIM_FP64) return FVIM_ERR_ARG;
   if (!(E > 0) || !(nu > -1.0 && nu < 0.5)) return FVIM_ERR_ARG;
   if (!eps_p || !out || eps_p == out) return FVIM_ERR_ARG;
@@ -120,7 +116,7 @@ extern "C" int fvim_apply_mindlin_noalloc(int n1, int n2, int nz, const double* 
   // size check before any device work
   const size_t es = precision == FVIM_FP64 ? 8 : 4, cs = 2 * es;
   const size_t h1 = (size_t)n1 / 2;
-  const size_t need = align256((size_t)nz * 8) + align256((size_t)nz * es) + align256((size_t)n1 * cs) +
+  const size_t need = align256((size_t)nz * es) + align256((size_t)n1 * cs) +
                       align256((size_t)n2 * cs) + align256((size_t)nz * 6 * n2 * h1 * cs) +
                       align256((size_t)nz * 6 * n2 * es) + align256((size_t)n2 * h1 * cs) +
                       align256((size_t)n2 * es);
@@ -148,6 +144,9 @@ extern "C" int fvim_apply_mindlin_noalloc(int n1, int n2, int nz, const double* 
   for (int i = 1; i < nz; ++i)
     if (fabs((z_nodes[i] - z_nodes[i - 1]) - h) > 1e-12 * fabs(z_nodes[nz - 1])) c.uniform = 0;
   c.hz = h;
+  // a grid tuned earlier in this process (fvim_autotune) runs its tuned depth tile plan, as a
+  // context created for it would (host-only table lookup)
+  if ((c.depth_chunk = plan_lookup(&c)) > 0) c.plan_tuned = 1;
   if (precision == FVIM_FP64)
     return run<double>(&c, (unsigned char*)base, (const double*)eps_p, (double*)out, out_kind, (double*)u3_surface);
   return run<float>(&c, (unsigned char*)base, (const float*)eps_p, (float*)out, out_kind, (float*)u3_surface);

@@ -5,8 +5,11 @@
 //     the implicit incremental equation (Sec. 4.2, Sec. 4.3);
 //   * coupling: Algorithm 1 (Sec. 5.2).
 // Vectors stay on the device in the context's precision.  Every reduction is a grid of
-// fixed blocks writing FP64 partial sums, added on the host in block order, so results
-// are bitwise reproducible.  Loops run on the host and are capped.
+// fixed blocks writing FP64 partial sums that the last block to finish adds in block order
+// (the host-loop fallbacks add them on the host in the same order), so results are bitwise
+// reproducible.  The CG's scalar logic runs in single-block finisher kernels and the host
+// reads one status block per batch of captured iterations; DF-SANE's line search runs as a
+// device-side loop (a WHILE node of one captured graph).  Every loop is capped.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>

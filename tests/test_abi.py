@@ -63,6 +63,19 @@ def test_product_path_does_not_import_oracle():
                 assert not re.search(r"^\s*(from|import)\s+oracle", src, re.M), f
 
 
+def test_input_generators_load_nothing_of_the_cuda_path():
+    """The oracle's golden-value scripts import the seeded input generators only: importing
+    them loads neither the ctypes binding nor libfvim.so."""
+    import subprocess
+    import sys
+
+    code = ("import sys; sys.path.insert(0, %r); import paper_1811_11558_gb300.inputs; "
+            "print(any(m.endswith('.fvim') for m in sys.modules))" % ROOT)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "False"
+
+
 def test_plan_entry_points_check_arguments_without_gpu():
     from paper_1811_11558_gb300 import fvim
 
