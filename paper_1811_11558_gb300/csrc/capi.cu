@@ -177,6 +177,38 @@ static bool use_fft2_cluster(fvim_ctx* c) {
   return c->fft2_cl == 1;
 }
 
+// one-pass 2-D FFTs through L2 (FP32 grids of fft2d_l2.cu), selected by the environment
+// variable FVIM_FFT2_FUSED=1 (decided once per context); the default is the separate row and
+// column kernels, which are faster at 512 x 512 although they move twice the bytes (the
+// one-pass kernels are bound by L1 and shared-memory traffic at 24 warps per SM)
+static bool use_fft2_fused(fvim_ctx* c) {
+  if (c->fft2_fused < 0) {
+    const char* e = getenv("FVIM_FFT2_FUSED");
+    c->fft2_fused = (e && e[0] == '1' && fft2_fused_available(c)) ? 1 : 0;
+  }
+  return c->fft2_fused == 1;
+}
+
+// Mindlin apply in three passes: 2-D FFT of the eps_p planes, the depth operator with Hooke's
+// law per mode, inverse 2-D FFT (the k1 = N1/2 column of the stress output is -C:eps_p, times
+// N2 because it skips the column transforms that the 1/(N1 N2) normalisation undoes)
+template <typename T> int apply_mindlin_fused(fvim_ctx* c, const T* eps_p, T* out, int kind, T* u3, const int* zr,
+                                              int& nk) {
+  if constexpr (sizeof(T) == 4) {
+    int rc;
+    if ((rc = timed(c, PROF_FFT2_FWD, nk, [&] { return launch_fft2_fwd_fused(c, eps_p, zr); }))) return rc;
+    if ((rc = timed(c, PROF_MINDLIN_DEPTH, nk,
+                    [&] { return launch_mindlin_depth<T>(c, kind, u3 != nullptr, true, zr); })))
+      return rc;
+    const int mode = kind == FVIM_STRESS ? 1 : 0;
+    if ((rc = timed(c, PROF_FFT2_INV, nk, [&] { return launch_fft2_inv_fused(c, out, mode, -(float)c->n2); })))
+      return rc;
+    return FVIM_OK;
+  } else {
+    return FVIM_ERR_UNSUPPORTED;
+  }
+}
+
 template <typename T> int apply_mindlin_cluster(fvim_ctx* c, const T* eps_p, T* out, int kind, T* u3, int& nk) {
   if constexpr (sizeof(T) == 4) {
     int rc;
@@ -194,9 +226,64 @@ template <typename T> int apply_mindlin_cluster(fvim_ctx* c, const T* eps_p, T* 
   }
 }
 
+// Mindlin apply on a direct-DFT grid: row and column DFTs of the eps_p planes, the depth
+// operator with Hooke's law per mode (Nyquist modes of even sides and the padding columns
+// carry no operator term there), column and row inverse DFTs; the surface displacement
+// spectrum takes the same inverse path
+template <typename T> int apply_mindlin_gen(fvim_ctx* c, const T* eps_p, T* out, int kind, T* u3, int& nk) {
+  int rc;
+  const size_t planes = (size_t)c->nz * 6;
+  const T scale = (T)(1.0 / ((double)c->n1 * (double)c->n2));
+  if ((rc = timed(c, PROF_ROWS_FWD6, nk, [&] { return launch_dft_rows_fwd<T>(c, eps_p, c->spec, planes * c->n2); })))
+    return rc;
+  if ((rc = timed(c, PROF_COLS_FWD, nk, [&] { return launch_dft_cols<T>(c, false, c->spec, (int)planes); }))) return rc;
+  if ((rc = timed(c, PROF_MINDLIN_DEPTH, nk, [&] { return launch_mindlin_depth<T>(c, kind, u3 != nullptr, true); })))
+    return rc;
+  if ((rc = timed(c, PROF_COLS_INV, nk, [&] { return launch_dft_cols<T>(c, true, c->spec, (int)planes); }))) return rc;
+  if ((rc = timed(c, PROF_ROWS_INV6, nk,
+                  [&] { return launch_dft_rows_inv<T>(c, c->spec, out, planes * c->n2, scale); })))
+    return rc;
+  if (u3) {
+    if ((rc = timed(c, PROF_COLS_INV, nk, [&] { return launch_dft_cols<T>(c, true, c->surf, 1); }))) return rc;
+    if ((rc = timed(c, PROF_ROWS_INV1, nk, [&] { return launch_dft_rows_inv<T>(c, c->surf, u3, c->n2, scale); })))
+      return rc;
+  }
+  return FVIM_OK;
+}
+
+// Boussinesq apply on a direct-DFT grid (same sequence as the FFT path, direct DFTs)
+template <typename T> int apply_boussinesq_gen(fvim_ctx* c, const T* p, T* u3, T* vol, int kind, int& nk) {
+  int rc;
+  const T scale = (T)(1.0 / ((double)c->n1 * (double)c->n2));
+  if ((rc = timed(c, PROF_ROWS_FWD1, nk, [&] { return launch_dft_rows_fwd<T>(c, p, c->surf, c->n2); }))) return rc;
+  if ((rc = timed(c, PROF_COLS_FWD, nk, [&] { return launch_dft_cols<T>(c, false, c->surf, 1); }))) return rc;
+  if ((rc = timed(c, PROF_BOUSSINESQ, nk,
+                  [&] { return launch_boussinesq<T>(c, kind, vol != nullptr, u3 != nullptr); })))
+    return rc;
+  if (vol) {
+    const size_t planes = (size_t)c->nz * 6;
+    if ((rc = timed(c, PROF_COLS_INV, nk, [&] { return launch_dft_cols<T>(c, true, c->spec, (int)planes); })))
+      return rc;
+    if ((rc = timed(c, PROF_ROWS_INV6, nk,
+                    [&] { return launch_dft_rows_inv<T>(c, c->spec, vol, planes * c->n2, scale); })))
+      return rc;
+  }
+  if (u3) {
+    if ((rc = timed(c, PROF_COLS_INV, nk, [&] { return launch_dft_cols<T>(c, true, c->surf, 1); }))) return rc;
+    if ((rc = timed(c, PROF_ROWS_INV1, nk, [&] { return launch_dft_rows_inv<T>(c, c->surf, u3, c->n2, scale); })))
+      return rc;
+  }
+  return FVIM_OK;
+}
+
 template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, int kind, T* u3, const int* zr) {
   int rc;
   int nk = 0;
+  if (c->gen) {
+    if ((rc = apply_mindlin_gen<T>(c, eps_p, out, kind, u3, nk))) return rc;
+    c->last_kernels = nk;
+    return FVIM_OK;
+  }
   if (use_fft2_cluster(c)) {
     if ((rc = apply_mindlin_cluster<T>(c, eps_p, out, kind, u3, nk))) return rc;
     if (u3) {
@@ -209,6 +296,15 @@ template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, i
   // a known layer range of the input skips the forward passes of the empty layers (the
   // Nyquist side array of those layers is left stale, so only for strain output)
   const int* zin = kind == FVIM_STRAIN ? zr : nullptr;
+  if (sizeof(T) == 4 && use_fft2_fused(c)) {
+    if ((rc = apply_mindlin_fused<T>(c, eps_p, out, kind, u3, zin, nk))) return rc;
+    if (u3) {
+      if ((rc = timed(c, PROF_COLS_INV, nk, [&] { return launch_cols<T>(c, true, c->surf, 1); }))) return rc;
+      if ((rc = timed(c, PROF_ROWS_INV1, nk, [&] { return launch_rows_inv1<T>(c, u3); }))) return rc;
+    }
+    c->last_kernels = nk;
+    return FVIM_OK;
+  }
   if ((rc = timed(c, PROF_ROWS_FWD6, nk, [&] { return launch_rows_fwd6<T>(c, eps_p, 0, c->nz, zin); }))) return rc;
   if ((rc = timed(c, PROF_COLS_FWD, nk, [&] { return launch_cols<T>(c, false, c->spec, c->nz * 6, zin); })))
     return rc;
@@ -233,6 +329,11 @@ template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, i
 template <typename T> int apply_boussinesq_t(fvim_ctx* c, const T* p, T* u3, T* vol, int kind) {
   int rc;
   int nk = 0;
+  if (c->gen) {
+    if ((rc = apply_boussinesq_gen<T>(c, p, u3, vol, kind, nk))) return rc;
+    c->last_kernels = nk;
+    return FVIM_OK;
+  }
   if (u3 && !vol && c->n2 >= 16) {
     // surface displacement only: rows, fused column pass (transform, compliance, inverse), rows
     bool fused = false;
@@ -255,7 +356,9 @@ template <typename T> int apply_boussinesq_t(fvim_ctx* c, const T* p, T* u3, T* 
   if ((rc = timed(c, PROF_BOUSSINESQ, nk,
                   [&] { return launch_boussinesq<T>(c, kind, vol != nullptr, u3 != nullptr); })))
     return rc;
-  if (vol && sizeof(T) == 4 && use_fft2_cluster(c)) {
+  if (vol && sizeof(T) == 4 && use_fft2_fused(c)) {
+    if ((rc = timed(c, PROF_FFT2_INV, nk, [&] { return launch_fft2_inv_fused(c, (float*)vol, 0, 0.f); }))) return rc;
+  } else if (vol && sizeof(T) == 4 && use_fft2_cluster(c)) {
     if ((rc = timed(c, PROF_FFT2_INV, nk, [&] { return launch_fft2_inv_cluster(c, (float*)vol, 0, 0.f); }))) return rc;
   } else if (vol) {
     if ((rc = timed(c, PROF_COLS_INV, nk, [&] { return launch_cols<T>(c, true, c->spec, c->nz * 6); }))) return rc;
@@ -310,6 +413,19 @@ template int return_map_t<double>(fvim_ctx*, const double*, double*, double*, in
 template int commit_t<float>(fvim_ctx*, const float*, const float*, const float*);
 template int commit_t<double>(fvim_ctx*, const double*, const double*, const double*);
 
+bool grid_gen(int n1, int n2) { return !is_pow2(n1) || !is_pow2(n2); }
+
+bool grid_ok(int n1, int n2) {
+  const bool p1 = is_pow2(n1) && n1 >= 4 && n1 <= 1024, p2 = is_pow2(n2) && n2 >= 2 && n2 <= 1024;
+  if (p1 && p2) return true;
+  // direct-DFT grids: odd sides 3..255, the other side odd or a power of two up to 256
+  const bool o1 = (n1 & 1) && n1 >= 3 && n1 <= 255, o2 = (n2 & 1) && n2 >= 3 && n2 <= 255;
+  const bool q1 = is_pow2(n1) && n1 >= 4 && n1 <= 256, q2 = is_pow2(n2) && n2 >= 2 && n2 <= 256;
+  return (o1 || q1) && (o2 || q2) && (o1 || o2);
+}
+
+int spec_stride(int n1, int n2) { return grid_gen(n1, n2) ? (n1 / 2 + 1 + 15) / 16 * 16 : n1 / 2; }
+
 extern "C" {
 
 const char* fvim_last_cuda_error(void) { return g_last_cuda == cudaSuccess ? "no error" : g_last_cuda_msg; }
@@ -332,7 +448,7 @@ int fvim_create(fvim_ctx** out, int n1, int n2, int nz, const double* z_nodes, d
                 void* stream) {
   if (!out) return FVIM_ERR_ARG;
   *out = nullptr;
-  if (!is_pow2(n1) || !is_pow2(n2) || n1 < 4 || n2 < 2 || n1 > 1024 || n2 > 1024) return FVIM_ERR_ARG;
+  if (!grid_ok(n1, n2)) return FVIM_ERR_ARG;
   if (nz < 2 || nz > 512 || !z_nodes) return FVIM_ERR_ARG;
   if (!(L1 > 0) || !(L2 > 0)) return FVIM_ERR_ARG;
   if (precision != FVIM_FP32 && precision != FVIM_FP64) return FVIM_ERR_ARG;
@@ -343,10 +459,13 @@ int fvim_create(fvim_ctx** out, int n1, int n2, int nz, const double* z_nodes, d
   if (!c) return FVIM_ERR_OOM;
   memset(c, 0, sizeof(*c));
   c->fft2_cl = -1;
+  c->fft2_fused = -1;
   c->n1 = n1;
   c->n2 = n2;
   c->nz = nz;
-  c->h1 = n1 / 2;
+  c->gen = grid_gen(n1, n2) ? 1 : 0;
+  c->h1 = spec_stride(n1, n2);
+  c->hs = c->gen ? n1 / 2 + 1 : c->h1;
   c->prec = precision;
   c->L1 = L1;
   c->L2 = L2;
@@ -474,10 +593,11 @@ size_t fvim_footprint(int n1, int n2, int nz, int precision) {
   if (n1 < 1 || n2 < 1 || nz < 1) return 0;
   const size_t es = precision == FVIM_FP64 ? 8 : 4;
   const size_t ns = (size_t)n1 * n2, nv = ns * nz;
-  const size_t spec = (size_t)nz * 6 * n2 * (n1 / 2) * 2 * es + (size_t)nz * 6 * n2 * es;
+  const size_t h = (size_t)spec_stride(n1, n2);
+  const size_t spec = (size_t)nz * 6 * n2 * h * 2 * es + (size_t)nz * 6 * n2 * es;
   const size_t state = nv * 6 * es * 2 + nv * es + ns * es;
   const size_t solver = 8 * nv * 6 * es + nv * es + 13 * ns * es + 64 * 1024;
-  return spec + state + solver + (size_t)(n1 + n2) * 2 * es + ns * 2 * es;
+  return spec + state + solver + (size_t)(n1 + n2) * 2 * es + (size_t)n2 * h * 2 * es;
 }
 
 int fvim_sync(fvim_ctx* c) {

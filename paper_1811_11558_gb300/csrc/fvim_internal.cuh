@@ -262,6 +262,20 @@ template <int REM> struct StageRadix {
   static constexpr int v = (REM == 2) ? 2 : ((REM == 4 || REM == 16) ? 4 : ((REM % 8 == 0) ? 8 : 4));
 };
 
+// twiddles w^1..w^7 of a radix-8 butterfly (w = tw[idx]) from three table reads: w, w^2, w^4
+// are read, w^3 = w w^2, w^5 = w^4 w, w^6 = w^4 w^2, w^7 = w^4 w^3 (three table reads instead of
+// seven: the reads of one stage are scattered, a table read per product was the costly part)
+template <typename V, bool INV>
+__device__ __forceinline__ void twiddles8(const V* __restrict__ tw, int idx, V (&w)[8]) {
+  w[1] = twiddle<V, INV>(tw, idx);
+  w[2] = twiddle<V, INV>(tw, 2 * idx);
+  w[4] = twiddle<V, INV>(tw, 4 * idx);
+  w[3] = cmul(w[1], w[2]);
+  w[5] = cmul(w[4], w[1]);
+  w[6] = cmul(w[4], w[2]);
+  w[7] = cmul(w[4], w[3]);
+}
+
 template <typename V, bool INV, int N, int R, int NS>
 __device__ __forceinline__ void stage_ct(V (&v)[8], int (&pos)[8], int t, const V* __restrict__ tw) {
   constexpr int T8 = N / 8;
@@ -269,8 +283,10 @@ __device__ __forceinline__ void stage_ct(V (&v)[8], int (&pos)[8], int t, const 
     const int k = t & (NS - 1);
     if constexpr (NS > 1) {
       constexpr int step = N / (NS * 8);
+      V w[8];
+      twiddles8<V, INV>(tw, k * step, w);
 #pragma unroll
-      for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], twiddle<V, INV>(tw, r * k * step));
+      for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], w[r]);
     }
     dft8<V, INV>(v);
     const int base = (t / NS) * NS * 8 + k;
@@ -286,8 +302,11 @@ __device__ __forceinline__ void stage_ct(V (&v)[8], int (&pos)[8], int t, const 
 #pragma unroll
       for (int r = 0; r < 4; ++r) u[r] = v[2 * r + g];
       if constexpr (NS > 1) {
-#pragma unroll
-        for (int r = 1; r < 4; ++r) u[r] = cmul(u[r], twiddle<V, INV>(tw, r * k * step));
+        // w, w^2 read, w^3 = w w^2
+        const V w1 = twiddle<V, INV>(tw, k * step), w2 = twiddle<V, INV>(tw, 2 * k * step);
+        u[1] = cmul(u[1], w1);
+        u[2] = cmul(u[2], w2);
+        u[3] = cmul(u[3], cmul(w1, w2));
       }
       dft4<V, INV>(u);
       const int base = (b / NS) * NS * 4 + k;
@@ -315,8 +334,26 @@ __device__ __forceinline__ void stage_ct(V (&v)[8], int (&pos)[8], int t, const 
   }
 }
 
-template <typename V, bool INV, int N, int NF, int NS, class Sm>
-__device__ __forceinline__ void fft_ct(V (&v)[NF][8], int t, const Sm& sm, const V* __restrict__ tw) {
+// barrier over the whole CTA (the default exchange synchronisation of fft_ct)
+struct CtaSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+// barrier over a group of NG threads (a multiple of 32, whole warps): the warp itself, or a
+// named barrier id (1..15) shared by the group's warps only
+template <int NG> struct GroupSync {
+  int id;
+  __device__ __forceinline__ void operator()() const {
+    if constexpr (NG == 32) {
+      __syncwarp();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(NG) : "memory");
+    }
+  }
+};
+
+template <typename V, bool INV, int N, int NF, int NS, class Sm, class Sync = CtaSync>
+__device__ __forceinline__ void fft_ct(V (&v)[NF][8], int t, const Sm& sm, const V* __restrict__ tw,
+                                       const Sync& sync = Sync()) {
   constexpr int R = StageRadix<N / NS>::v;
   int pos[8];
 #pragma unroll
@@ -328,13 +365,13 @@ __device__ __forceinline__ void fft_ct(V (&v)[NF][8], int t, const Sm& sm, const
     }
   }
   if constexpr (NS * R < N) {
-    __syncthreads();
+    sync();
 #pragma unroll
     for (int f = 0; f < NF; ++f)
 #pragma unroll
       for (int m = 0; m < 8; ++m) v[f][m] = sm.get(f, t + m * (N / 8));
-    __syncthreads();
-    fft_ct<V, INV, N, NF, NS * R>(v, t, sm, tw);
+    sync();
+    fft_ct<V, INV, N, NF, NS * R>(v, t, sm, tw, sync);
   }
 }
 
@@ -355,6 +392,11 @@ template <typename V> __device__ __forceinline__ void cp_async_cx(V* smem, const
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N of this thread's committed copy groups are still in flight
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 // Raises a kernel's dynamic shared-memory cap to the device's opt-in maximum.  The value is
@@ -380,7 +422,11 @@ template <typename K> inline void smem_cap(K kern) {
 #define FVIM_NSOLVER_BUFS 26
 
 struct fvim_ctx {
+  // h1: row stride of the half spectrum (complex); power-of-two grids: N1/2 columns (the
+  // k1 = N1/2 coefficient kept apart in nq); gen: floor(N1/2) + 1 columns rounded up to 16
   int n1, n2, nz, h1;
+  int gen;  // a side is not a power of two: direct DFTs (dft.cu), every coefficient in spec
+  int hs;   // stored k1 columns (k1 < hs); == h1 for power-of-two grids
   int prec;  // FVIM_FP32 / FVIM_FP64
   double L1, L2;
   double E, nu, sigma_y, E_h, lam, mu;
@@ -410,6 +456,7 @@ struct fvim_ctx {
   void* srt;       // solver runtime (solvers.cu): own stream, events, captured CUDA graphs
   int depth_chunk; // depth nodes per chunk thread of the depth kernel; 0: depth_chunk_default
   int plan_tuned;  // depth_chunk came from a timing run (fvim_autotune) in this process
+  int fft2_fused;  // one-pass 2-D FFTs through L2: -1 not yet known, 0 not used, 1 used
 };
 
 // tile plan of the depth kernel (depth.cu): default chunk length, and whether a chunk length
@@ -455,6 +502,23 @@ void solver_drop_graphs(fvim_ctx* c);
 bool fft2_cluster_available(const fvim_ctx* c);
 int launch_fft2_fwd_cluster(const fvim_ctx* c, const float* src);
 int launch_fft2_inv_cluster(const fvim_ctx* c, float* out, int nq_mode, float nq_scale);
+
+// one-pass 2-D FFTs with the row spectra exchanged through L2 (fft2d_l2.cu), FP32; zr as for
+// launch_rows_fwd6 (planes of layers outside the range are skipped)
+bool fft2_fused_available(const fvim_ctx* c);
+int launch_fft2_fwd_fused(const fvim_ctx* c, const float* src, const int* zr = nullptr);
+int launch_fft2_inv_fused(const fvim_ctx* c, float* out, int nq_mode, float nq_scale);
+
+// direct DFTs of grids with a side that is not a power of two (dft.cu, fvim_ctx::gen):
+// rows real -> half spectrum [rows][h1], columns in place, half spectrum -> real rows x scale
+template <typename T> int launch_dft_rows_fwd(const fvim_ctx* c, const T* src, void* dst, size_t rows);
+template <typename T> int launch_dft_cols(const fvim_ctx* c, bool inverse, void* planes, int nplanes);
+template <typename T> int launch_dft_rows_inv(const fvim_ctx* c, const void* src, T* dst, size_t rows, T scale);
+// grid sides the library takes: a power of two (4..1024 for N1, 2..1024 for N2, the FFT path)
+// or an odd number 3..255 (with the other side odd or a power of two up to 256: direct DFTs)
+bool grid_ok(int n1, int n2);
+bool grid_gen(int n1, int n2);
+int spec_stride(int n1, int n2);
 
 // compile-time-length FFT kernels (fft_ct.cu); false when the length has no variant
 template <typename T> bool launch_cols_ct(const fvim_ctx* c, bool inverse, void* planes, int nplanes, const int* zr = nullptr);

@@ -42,28 +42,39 @@ MINDLIN_CASES = [
     (256, 256, inputs.uniform_depth(4, 0.06), 1.0, 1.0, "fp32"),
     (512, 256, inputs.uniform_depth(3, 0.02), 1.0, 0.5, "fp32"),
     (256, 512, np.array([0.0, 0.004, 0.011]), 0.5, 1.0, "fp32"),
+    # larger planes, non-square cells, ragged depth chunks
+    (128, 128, inputs.uniform_depth(33, 0.4), 1.0, 0.6, "fp32"),
+    (128, 256, np.array([0.0, 0.005, 0.012, 0.02, 0.035]), 0.7, 1.0, "fp32"),
+    (512, 512, inputs.uniform_depth(3, 0.01), 1.0, 1.0, "fp32"),
+    (1024, 512, inputs.uniform_depth(2, 0.004), 1.0, 0.5, "fp32"),
+    # sides that are not powers of two (direct DFTs): odd grids, whose every mode is in Z^2_N,
+    # and mixed ones, whose even side keeps its Nyquist row or column out of the operator
+    (9, 7, inputs.uniform_depth(5, 0.3), 1.0, 0.8, "fp64"),
+    (27, 27, np.array([0.0, 0.01, 0.03, 0.06, 0.1, 0.15, 0.21, 0.28]), 1.0, 1.0, "fp64"),
+    (81, 81, inputs.uniform_depth(4, 0.03), 1.0, 1.0, "fp32"),
+    (81, 81, inputs.uniform_depth(6, 0.05), 1.0, 1.0, "fp64"),
+    (15, 32, inputs.uniform_depth(9, 0.2), 0.6, 1.0, "fp32"),
+    (64, 27, inputs.uniform_depth(7, 0.1), 1.0, 0.5, "fp64"),
 ]
 
 CLUSTER_PLANES = {(256, 256), (512, 512), (256, 512), (512, 256)}
-
-
-def _cluster(n1, n2, prec):
-    return prec == "fp32" and (n1, n2) in CLUSTER_PLANES
+FUSED_PLANES = {(128, 128), (256, 128), (128, 256), (256, 256), (512, 256), (256, 512), (512, 512),
+                (1024, 512), (512, 1024), (1024, 1024)}
 
 
 def _kernels(n1, n2, prec, with_u3):
-    """Kernels of one Mindlin apply: cluster path (2-D FFT, depth, inverse 2-D FFT) or
-    rows / columns / depth / columns / rows, plus two for the surface displacement."""
-    base = 3 if _cluster(n1, n2, prec) else 5
-    return base + (2 if with_u3 else 0)
+    """Kernels of one Mindlin apply on the default path: rows / columns / depth / columns /
+    rows, plus two for the surface displacement."""
+    return 5 + (2 if with_u3 else 0)
 
 
 @pytest.mark.parametrize("n1,n2,z,L1,L2,prec", MINDLIN_CASES)
 @pytest.mark.parametrize("kind", ["stress", "strain"])
 def test_mindlin_parity(n1, n2, z, L1, L2, prec, kind, monkeypatch):
     torch = require_gpu()
-    # the whole-plane cluster FFTs are opt-in; the plane sizes they cover run through them
-    monkeypatch.setenv("FVIM_FFT2_CLUSTER", "1" if _cluster(n1, n2, prec) else "0")
+    # the default path: separate row and column kernels (direct DFTs on odd grids)
+    monkeypatch.setenv("FVIM_FFT2_CLUSTER", "0")
+    monkeypatch.delenv("FVIM_FFT2_FUSED", raising=False)
     ep = inputs.plastic_strain_field(n1, n2, z, seed=1812 + n1 + n2 + z.size)
     ref, u3_ref = op.mindlin_apply(ep, z, L1, L2, E, NU, kind, with_surface=True)
     ctx = _ctx(n1, n2, z, L1, L2, prec)
@@ -79,28 +90,38 @@ def test_mindlin_parity(n1, n2, z, L1, L2, prec, kind, monkeypatch):
     assert torch.equal(d_ep, to_dev(torch, ep, dt))
 
 
-@pytest.mark.parametrize("n1,n2", sorted(CLUSTER_PLANES))
-def test_cluster_fft_path_equals_row_column_path(n1, n2, monkeypatch):
-    """The whole-plane cluster FFTs and the separate row / column kernels compute the same
-    operator (FP32 rounding apart), for the Mindlin and the Boussinesq volume output."""
+@pytest.mark.parametrize("n1,n2", sorted(FUSED_PLANES | CLUSTER_PLANES))
+def test_fft_paths_agree(n1, n2, monkeypatch):
+    """The one-pass 2-D FFTs through L2, the whole-plane cluster FFTs (both opt-in) in distributed shared memory and the separate row / column
+    kernels compute the same operator (FP32 rounding apart), for the Mindlin stress, strain
+    and surface displacement and the Boussinesq volume output."""
     torch = require_gpu()
     z = inputs.uniform_depth(5, 0.1)
     ep = to_dev(torch, inputs.plastic_strain_field(n1, n2, z, seed=77 + n1 + n2, dtype=np.float32), torch.float32)
     p = to_dev(torch, np.abs(inputs.random_field((n2, n1), seed=5)) + 0.5, torch.float32)
+    paths = {"rows_cols": ({"FVIM_FFT2_CLUSTER": "0"}, 7)}
+    if (n1, n2) in FUSED_PLANES:
+        paths["fused"] = ({"FVIM_FFT2_FUSED": "1", "FVIM_FFT2_CLUSTER": "0"}, 5)
+    if (n1, n2) in CLUSTER_PLANES:
+        paths["cluster"] = ({"FVIM_FFT2_CLUSTER": "1"}, 5)
     outs = {}
-    for flag in ("1", "0"):
-        monkeypatch.setenv("FVIM_FFT2_CLUSTER", flag)
+    for name, (env, nk) in paths.items():
+        for k in ("FVIM_FFT2_FUSED", "FVIM_FFT2_CLUSTER"):
+            monkeypatch.delenv(k, raising=False)
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
         ctx = _ctx(n1, n2, z, 1.0, 1.0, "fp32")
         u3 = torch.empty(ctx.surf_shape, dtype=torch.float32, device="cuda")
         s = ctx.apply_mindlin(ep, kind="stress", u3=u3).clone()
-        assert ctx.last_kernel_count() == (5 if flag == "1" else 7)
+        assert ctx.last_kernel_count() == nk, name
         e = ctx.apply_mindlin(ep, kind="strain").clone()
         vol = torch.empty(ctx.vol_shape, dtype=torch.float32, device="cuda")
         ctx.apply_boussinesq(p, vol=vol, kind="stress")
         torch.cuda.synchronize()
-        outs[flag] = [x.cpu().numpy().astype(np.float64) for x in (s, e, u3, vol)]
-    for a, b in zip(outs["1"], outs["0"]):
-        assert rel_l2(a, b) < 5e-6
+        outs[name] = [x.cpu().numpy().astype(np.float64) for x in (s, e, u3, vol)]
+    for name, got in outs.items():
+        for a, b in zip(got, outs["rows_cols"]):
+            assert rel_l2(a, b) < 5e-6, name
 
 
 def test_mindlin_deterministic_and_reusable():
@@ -152,7 +173,11 @@ BOUS_CASES = [
     (16, 8, inputs.uniform_depth(5, 0.3), 1.0, 0.7, "fp64"),
     (32, 32, np.array([0.0, 0.02, 0.05, 0.1, 0.2, 0.35, 0.5]), 1.0, 1.0, "fp64"),
     (128, 64, inputs.uniform_depth(17, 0.2), 1.0, 1.0, "fp32"),
-    (256, 256, inputs.uniform_depth(3, 0.05), 1.0, 1.0, "fp32"),         # cluster inverse FFT
+    (256, 256, inputs.uniform_depth(3, 0.05), 1.0, 1.0, "fp32"),         # one-pass inverse FFT
+    (512, 128, inputs.uniform_depth(4, 0.03), 1.0, 0.4, "fp32"),
+    (27, 21, inputs.uniform_depth(6, 0.2), 1.0, 0.8, "fp64"),
+    (81, 81, inputs.uniform_depth(5, 0.05), 1.0, 1.0, "fp32"),
+    (32, 9, inputs.uniform_depth(4, 0.1), 1.0, 1.0, "fp64"),
 ]
 
 
@@ -160,7 +185,8 @@ BOUS_CASES = [
 @pytest.mark.parametrize("kind", ["stress", "strain"])
 def test_boussinesq_parity(n1, n2, z, L1, L2, prec, kind, monkeypatch):
     torch = require_gpu()
-    monkeypatch.setenv("FVIM_FFT2_CLUSTER", "1" if _cluster(n1, n2, prec) else "0")
+    monkeypatch.setenv("FVIM_FFT2_CLUSTER", "0")
+    monkeypatch.delenv("FVIM_FFT2_FUSED", raising=False)
     p = np.abs(inputs.random_field((n2, n1), seed=3 + n1)) + 0.5
     u3_ref, vol_ref = op.boussinesq_apply(p, z, L1, L2, E, NU, kind)
     ctx = _ctx(n1, n2, z, L1, L2, prec)
