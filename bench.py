@@ -311,7 +311,7 @@ def run_gpu(args):
         line["solves"]["epp_sweep"] = epp_metrics()
         line["scaling_sweep"] = scaling_metrics()
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(sample_modes=256, sample_planes=None)
+        line["cpu_baseline"] = cpu_baseline()
     if pg is not None:
         pg.barrier()
         pg.destroy_process_group()
@@ -381,13 +381,15 @@ def solve_metrics(repeats=3, served=32, slots=16):
     return out
 
 
-def rough_metrics(n=1024, nz=32, depth=0.05, seed=1813):
+def rough_metrics(n=1024, nz=32, depth=0.05, seed=1813, n_inc=10, cap=120):
     """Algorithm 1 on a rough surface, FP32: seeded self-affine surface n x n (H = 0.8, flat PSD
     for 4 <= |k| < 8, power law to k_s = 64, rms slope 0.1), nz uniform nodes to the given
-    depth, sigma_y = 0.05 E*, E_h = 0.1 E.  (a) the paper's rough-surface load W = 1e-3 E x rms
-    slope in five increments, relaxation 0.3: a converged solve; (b) the load of a 10 % elastic
-    contact fraction, where Algorithm 1 does not reach the tolerance: a fixed budget of 20
-    coupling iterations on each of two increments, timed per coupling iteration."""
+    depth, sigma_y = 0.05 E*, E_h = 0.1 E, relaxation 0.3.  (a) the paper's rough-surface load
+    W = 1e-3 E x rms slope in five increments; (b) the load of a 10 % elastic contact fraction,
+    ramped in n_inc equal increments (the paper's remedy for the coupling's slow convergence
+    on rough surfaces: small load steps), Algorithm 1 capped at ``cap`` iterations per
+    increment.  Both are timed as whole solves; the status says whether every increment
+    reached the tolerance."""
     import torch
 
     from paper_1811_11558_gb300 import Context, inputs
@@ -401,7 +403,7 @@ def rough_metrics(n=1024, nz=32, depth=0.05, seed=1813):
     p = torch.zeros(ctx.surf_shape, dtype=torch.float32, device="cuda")
     out = {"workload": "rough_%dx%dx%d_fp32" % (n, n, nz), "depth": depth, "seed": seed}
     W = 1e-3 * E * 0.1
-    opts = ctx.default_opts(relax=0.3, max_iter=100, tol=1e-6)
+    opts = ctx.default_opts(relax=0.3, max_iter=cap, tol=1e-6)
     ctx.reset_state()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -416,62 +418,80 @@ def rough_metrics(n=1024, nz=32, depth=0.05, seed=1813):
     ctx.elastic_contact(hd, 5e-3, p, ctx.default_opts())
     W10 = 5e-3 * 0.1 / float((p > 0).double().mean())
     ctx.reset_state()
-    opts = ctx.default_opts(relax=0.3, max_iter=20, tol=1e-6)
+    p.zero_()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    rep = ctx.solve_contact(hd, [W10 / 2, W10], p, opts, allow_not_converged=True)
+    rep = ctx.solve_contact(hd, [W10 * (k + 1) / n_inc for k in range(n_inc)], p, opts, allow_not_converged=True)
     t = time.perf_counter() - t0
-    its = sum(rep["alg1_iters"][:2])
-    out["area_10pct"] = {"W": W10, "increments": 2, "relax": 0.3, "alg1_cap": 20, "status": rep["status"],
-                         "ms_per_alg1_iter": 1e3 * t / its, "alg1_error": rep["alg1_error"],
-                         "contact_area": rep["contact_area"][-1],
-                         "note": "Algorithm 1 stalls near 1e-2 on this load (the paper notes it is not robust on "
-                                 "rough surfaces); timed on a fixed budget"}
+    its = sum(rep["alg1_iters"])
+    out["area_10pct"] = {"W": W10, "increments": n_inc, "relax": 0.3, "tol": opts.tol, "alg1_cap": cap,
+                         "status": rep["status"], "converged_increments": sum(
+                             1 for e in rep["alg1_error"] if e < opts.tol),
+                         "solves_per_s": 1.0 / t, "ms_per_solve": 1e3 * t, "ms_per_alg1_iter": 1e3 * t / its,
+                         "alg1_iters": rep["alg1_iters"], "alg1_error": rep["alg1_error"],
+                         "contact_area": rep["contact_area"][-1]}
     ctx.close()
     return out
 
 
-def epp_metrics(n=128, nz=32, depth=0.25, ratios=(2.0, 3.0, 4.0)):
-    """Elastic-perfectly-plastic Hertz load sweep (E_h = 0; the paper's App. C.2 comparison is
-    elastic-perfectly-plastic, on an 81 x 81 x 32 grid): paraboloid R = 0.5 on n x n, nz nodes to
-    the given depth, sigma_y = 0.05 E*, increments at W / W_y = ratios with W_y the elastic onset
-    load (p0 = 1.6 sigma_y).  FP32 and FP64 one solve each (tuned plans), with the peak pressure,
-    contact area and peak plastic strain of every increment, for both.  (At W / W_y = 8 on this
-    grid Algorithm 1 with relaxation 0.5 does not converge in either precision.)"""
+def epp_loads():
+    """W / W_y of the paper's elastic-perfectly-plastic Hertz sweep (App. C.2): 20 values
+    spread evenly over [0.9, 15.5] together with 1, 2.1, 6.4 and 15.5, sorted (monotonic
+    loading), without the repeated 15.5."""
+    return sorted(set(np.round(np.linspace(0.9, 15.5, 20), 12).tolist()) | {1.0, 2.1, 6.4, 15.5})
+
+
+def epp_metrics(n=81, nz=32, a_y_over_L=0.05, relax=0.5, cap=200):
+    """Elastic-perfectly-plastic Hertz load sweep at the paper's discretisation (App. C.2): cell
+    [0, 20 R / 3]^2 x [0, 10 R / 3] with L = 1 (R = 0.15, depth 0.5), N = (81, 81, 32), nu = 0.3,
+    E_h = 0, W / W_y over epp_loads() one increment each (the state carries over), Algorithm-1
+    tolerance 1e-9 (FP64) as in the paper and 1e-7 (FP32).  The paper leaves sigma_y free
+    (normalised results do not depend on it); here it is set so that the onset contact radius
+    a_y = pi R p_y / (2 E*) (p_y = 1.6 sigma_y) is a_y_over_L of the cell.  Reports per load the
+    peak pressure over sigma_y, the contact radius over a_y (from the contact area), the peak
+    plastic strain and the coupling iterations, for FP64 and FP32."""
     import torch
 
     from paper_1811_11558_gb300 import Context, inputs
 
     es = E / (1 - NU * NU)
-    sy = 0.05 * es
-    a_y = np.pi * 0.5 * 1.6 * sy / (2 * es)
-    w_y = 2 * np.pi * a_y ** 2 * 1.6 * sy / 3
-    z = inputs.uniform_depth(nz, depth)
-    h = inputs.hertz_profile(n, n, 1.0, 1.0, 0.5)
-    out = {"workload": "epp_hertz_%dx%dx%d" % (n, n, nz), "W_over_W_y": list(ratios), "relax": 0.5}
+    R = 0.15
+    a_y = a_y_over_L
+    p_y = 2 * es * a_y / (np.pi * R)
+    sy = p_y / 1.6
+    w_y = np.pi ** 3 * R ** 2 * p_y ** 3 / (6 * es ** 2)
+    loads = epp_loads()
+    z = inputs.uniform_depth(nz, 10 * R / 3)
+    h = inputs.hertz_profile(n, n, 1.0, 1.0, R)
+    out = {"workload": "epp_hertz_%dx%dx%d" % (n, n, nz), "W_over_W_y": loads, "relax": relax, "R": R,
+           "sigma_y_over_E_star": sy / es, "a_y": a_y, "W_y": w_y}
     press = {}
-    for prec in ("fp32", "fp64"):
+    for prec, tol in (("fp64", 1e-9), ("fp32", 1e-7)):
         ctx = Context(n, n, z, 1.0, 1.0, precision=prec, E=E, nu=NU, sigma_y=sy, E_h=0.0)
         ctx.autotune()
         hd = torch.from_numpy(h).to("cuda", ctx.dtype)
-        p = torch.empty(ctx.surf_shape, dtype=ctx.dtype, device="cuda")
-        opts = ctx.default_opts(relax=0.5, max_iter=150)
+        p = torch.zeros(ctx.surf_shape, dtype=ctx.dtype, device="cuda")
+        opts = ctx.default_opts(relax=relax, max_iter=cap, tol=tol)
         rows = []
+        ep = torch.empty(ctx.scal_shape, dtype=ctx.dtype, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for r in ratios:     # one increment per call (the state carries over), to read each state
+        for r in loads:      # one increment per call (the state carries over), to read each state
             rep = ctx.solve_contact(hd, [r * w_y], p, opts, allow_not_converged=True)
-            ep = torch.empty(ctx.scal_shape, dtype=ctx.dtype, device="cuda")
             ctx.get_state(None, ep, None)
+            area = rep["contact_area"][-1]
             rows.append({"W_over_W_y": r, "p_max_over_sigma_y": float(p.max()) / sy,
-                         "area": rep["contact_area"][-1], "e_p_max": float(ep.max()),
-                         "alg1_iters": rep["alg1_iters"][-1], "status": rep["status"]})
+                         "a_over_a_y": float(np.sqrt(area / np.pi)) / a_y, "e_p_max": float(ep.max()),
+                         "alg1_iters": rep["alg1_iters"][-1], "alg1_error": rep["alg1_error"][-1],
+                         "status": rep["status"]})
         torch.cuda.synchronize()
-        out[prec] = {"ms_per_sweep": 1e3 * (time.perf_counter() - t0), "increments": rows}
+        out[prec] = {"ms_per_sweep": 1e3 * (time.perf_counter() - t0), "tol": tol,
+                     "converged": sum(1 for q in rows if q["status"] == 0), "increments": rows}
         press[prec] = p.cpu().numpy().astype(np.float64)
         ctx.close()
     out["fp32_vs_fp64_pressure_rel_l2"] = float(np.linalg.norm(press["fp32"] - press["fp64"]) /
                                                 np.linalg.norm(press["fp64"]))
+    out["fp32_vs_fp64_area_diff"] = abs(float((press["fp32"] > 0).mean()) - float((press["fp64"] > 0).mean()))
     return out
 
 
@@ -481,7 +501,7 @@ def batch_problems(n_prob=64, seed=1814):
     (H uniform in [0.6, 0.9], flat PSD for 4 <= |k| < 8, power law to k_s = max(8, n / 16),
     rms slope 0.1, depth 0.05); total load log-uniform over the decade below the load of a 10 %
     elastic contact fraction (Hertz: pi a^2 = 0.1, W = 4 E* a^3 / (3 R); rough: mean pressure
-    0.1 E* slope / 2), five increments; sigma_y = 0.05 E*, E_h = 0.1 E."""
+    0.1 E* slope / 2), five increments (Hertz) or ten (rough); sigma_y = 0.05 E*, E_h = 0.1 E."""
     from paper_1811_11558_gb300 import inputs
 
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -505,12 +525,13 @@ def batch_problems(n_prob=64, seed=1814):
             w10 = 4.0 * es * a ** 3 / (3.0 * 0.5)
             relax = 0.5
         W = w10 * 10.0 ** u
-        probs.append({"n": n, "nz": nz, "rough": rough, "z": z, "h": h, "loads": [W * (k + 1) / 5 for k in range(5)],
-                      "relax": relax})
+        ninc = 10 if rough else 5   # small load steps on rough surfaces (the paper's remedy)
+        probs.append({"n": n, "nz": nz, "rough": rough, "z": z, "h": h,
+                      "loads": [W * (k + 1) / ninc for k in range(ninc)], "relax": relax})
     return probs
 
 
-def batch_metrics(n_prob=64, slots=16, seed=1814, max_iter=60, n64=4):
+def batch_metrics(n_prob=64, slots=16, seed=1814, max_iter=100, n64=4):
     """Batched uneven solves: n_prob problems (batch_problems) submitted at once to the
     server (slots contexts, one stream and one set of captured graphs each, FP32 operators,
     FP64 reductions), aggregate solves/s and per-problem latency; plain FP64 and FP32 one at a
@@ -543,7 +564,7 @@ def batch_metrics(n_prob=64, slots=16, seed=1814, max_iter=60, n64=4):
     conv = sum(1 for r in res if r.report.get("status", 0) == 0)
     small = [i for i, pb in enumerate(probs) if pb["n"] == min(q["n"] for q in probs)][:n64]
     t = {"fp64": [], "fp32": []}
-    err = []
+    err, darea = [], []
     for i in small:
         pb = probs[i]
         press = {}
@@ -562,16 +583,23 @@ def batch_metrics(n_prob=64, slots=16, seed=1814, max_iter=60, n64=4):
             press[prec] = p.cpu().numpy().astype(np.float64)
             ctx.close()
         err.append(float(np.linalg.norm(press["fp32"] - press["fp64"]) / np.linalg.norm(press["fp64"])))
+        darea.append(abs(float((press["fp32"] > 0).mean()) - float((press["fp64"] > 0).mean())))
     return {"workload": "batch_%d_uneven" % n_prob, "grids": sorted({pb["n"] for pb in probs}),
             "nz": sorted({pb["nz"] for pb in probs}), "rough": sum(pb["rough"] for pb in probs),
-            "slots": slots, "alg1_cap": max_iter, "converged": conv,
+            "slots": slots, "alg1_cap": max_iter, "converged": conv, "unconverged": n_prob - conv,
+            "unconverged_problems": [{"i": i, "n": pb["n"], "nz": pb["nz"], "rough": pb["rough"],
+                                      "iters": r.report.get("alg1_iters"), "errors": r.report.get("alg1_error")}
+                                     for i, (pb, r) in enumerate(zip(probs, res))
+                                     if r.report.get("status", 0) != 0],
             "tile_plans": {"shapes": len(plans), "tuning_s": prep_s,
                            "depth_chunk": sorted({(p["n"], p["nz"], p["depth_chunk"]) for p in plans.values()})},
-            "fp32_served": {"solves_per_s": n_prob / wall, "wall_s": wall, "p50_ms": 1e3 * lat[50],
-                            "p99_ms": 1e3 * lat[99], "arrivals": "all at t = 0"},
+            "fp32_served": {"solves_per_s": conv / wall, "counted": "converged solves only", "wall_s": wall,
+                            "all_solves_per_s": n_prob / wall, "p50_ms": 1e3 * lat[50], "p99_ms": 1e3 * lat[99],
+                            "arrivals": "all at t = 0"},
             "sample_n%d" % probs[small[0]]["n"] if small else "sample": {
                 "problems": small, "fp64_plain_ms": [1e3 * x for x in t["fp64"]],
-                "fp32_plain_ms": [1e3 * x for x in t["fp32"]], "fp32_vs_fp64_pressure_rel_l2": err},
+                "fp32_plain_ms": [1e3 * x for x in t["fp32"]], "fp32_vs_fp64_pressure_rel_l2": err,
+                "fp32_vs_fp64_area_diff": darea},
             "per_problem": [{"n": pb["n"], "nz": pb["nz"], "rough": pb["rough"], "ms": 1e3 * (r.finished - r.admitted),
                              "status": r.report.get("status", 0), "iters": r.report.get("alg1_iters")}
                             for pb, r in zip(probs, res)]}
@@ -659,19 +687,31 @@ def stream_metrics(n_req=12, slots=8, seed=1815, rate_sweep=(0.4, 1.0, 1.5)):
             "served_saturated_over_fp64_plain": (n_req / swall) / (n_req / est64)}
 
 
-def scaling_metrics(sizes=(16, 32, 64, 128), reps=20):
-    """Mindlin-apply time on N x N x N grids (the paper's VIM complexity sweep, App. C.4, whose
-    reference time T0 = 1.41 ms was measured on a CPU node), FP32 and FP64, CUDA events,
-    inputs resident."""
+def scaling_metrics(sizes=(4, 8, 16, 32, 64, 128), reps=20):
+    """Mindlin-apply time and device memory on N x N x N grids (the paper's VIM complexity
+    sweep, App. C.4, whose reference time T0 = 1.41 ms and memory 1.27 GB at 2^21 nodes were
+    measured on a CPU node), FP32 and FP64, CUDA events, inputs resident.
+
+    Memory: ``apply_bytes`` is what one apply touches on the device (input eps_p, output
+    sigma, the context's half-spectrum scratch with its Nyquist side array, twiddles and depth
+    nodes); ``context_bytes`` is the device memory the context itself took when it was
+    created (its scratch plus the plastic state it keeps for the solvers), measured with
+    cudaMemGetInfo around the creation."""
     import torch
 
     from paper_1811_11558_gb300 import Context, inputs
 
-    out = {"workload": "mindlin_apply_cube_sweep", "paper_T0_ms_cpu": 1.41, "ms": {}}
+    out = {"workload": "mindlin_apply_cube_sweep", "paper_T0_ms_cpu": 1.41, "paper_memory_gb_128": 1.27,
+           "ms": {}, "apply_bytes": {}, "context_bytes": {}}
     for prec in ("fp32", "fp64"):
+        es = 4 if prec == "fp32" else 8
         for n in sizes:
             z = inputs.uniform_depth(n, 1.0)
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]
             ctx = Context(n, n, z, 1.0, 1.0, precision=prec, E=E, nu=NU)
+            torch.cuda.synchronize()
+            free1 = torch.cuda.mem_get_info()[0]
             ctx.autotune()
             ep = torch.from_numpy(inputs.plastic_strain_field(n, n, z, seed=n)).to("cuda", ctx.dtype)
             o = torch.empty_like(ep)
@@ -683,7 +723,12 @@ def scaling_metrics(sizes=(16, 32, 64, 128), reps=20):
                 ctx.apply_mindlin(ep, o)
             e.record()
             torch.cuda.synchronize()
-            out["ms"]["%s_%d" % (prec, n)] = s.elapsed_time(e) / reps
+            key = "%s_%d" % (prec, n)
+            out["ms"][key] = s.elapsed_time(e) / reps
+            vol = 6 * n * n * n * es
+            spec = n * 6 * n * (n // 2) * 2 * es + n * 6 * n * es
+            out["apply_bytes"][key] = int(2 * vol + spec + 2 * n * 2 * es + n * es)
+            out["context_bytes"][key] = int(free0 - free1)
             ctx.close()
     return out
 
@@ -696,62 +741,137 @@ TRAFFIC_BYTES = {"rows_fwd6": 755.1e6, "cols_fwd": 744.2e6, "mindlin_depth": 743
                  "rows_inv6": None}
 
 
-def _operator_input(seed=SEED):
-    """The operator workload's plastic strain field (seeded), generated once per process."""
-    from paper_1811_11558_gb300 import inputs
-
-    key = ("ep", seed)
-    if key not in _INPUT_CACHE:
-        z = inputs.uniform_depth(NZ, DEPTH)
-        _INPUT_CACHE[key] = (z, inputs.plastic_strain_field(N1, N2, z, seed=seed))
-    return _INPUT_CACHE[key]
 
 
-_INPUT_CACHE = {}
+def _oracle_job(planes, modes, seed):
+    """One bounded sample of the FP64 oracle's Mindlin apply on the operator workload.
 
-
-def cpu_baseline(sample_modes=256, sample_planes=None, seed=SEED):
-    """Time the FP64 oracle on a bounded sample of the operator workload.
-
-    Sample: the oracle's Hooke's law and forward and inverse DFT of ``sample_planes`` of the
-    384 (layer, component) planes (all of them when None) plus its per-mode depth operator
-    on ``sample_modes`` random modes (drawn with ``seed``); both are scaled to one full apply
-    (384 planes each way, 131 072 resolved modes).  Input generation is not timed.
+    Hooke's law and forward and inverse DFT of ``planes`` (layer, component) planes of a
+    plastic strain field drawn like the workload's (first layers of the depth envelope), and
+    the per-mode depth operator on ``modes`` random resolved modes of the 512 x 512 grid.
+    Returns the two measured times and the number of modes kept; input generation is not
+    timed.
     """
     from oracle import operators as op
     from oracle import tensors as T
+    from paper_1811_11558_gb300 import inputs
 
-    z, ep = _operator_input()
+    z = inputs.uniform_depth(NZ, DEPTH)
+    nl = -(-planes // 6)
+    ep = inputs.plastic_strain_field(N1, N2, z[:nl], seed=seed)
     lam, mu = T.lame(E, NU)
-    planes = NZ * 6
-    npl = planes if sample_planes is None else int(sample_planes)
-    nl = -(-npl // 6)  # layers that hold the sampled planes
-    t0 = time.perf_counter()
-    w = T.hooke6(ep[:nl], lam, mu, axis=1).reshape(nl * 6, N2, N1)[:npl]
-    wh = np.fft.fft2(w, axes=(-2, -1))
-    back = np.fft.ifft2(wh, axes=(-2, -1)).real
-    t_fft = (time.perf_counter() - t0) * planes / npl
-    assert back.shape == w.shape
     rng = np.random.default_rng(seed)
-    k2 = rng.integers(0, N2, sample_modes)
-    k1 = rng.integers(0, N1, sample_modes)
     Q1, Q2, nyq, zero = op.mode_grid(N1, N2, 1.0, 1.0)
+    k2 = rng.integers(0, N2, modes)
+    k1 = rng.integers(0, N1, modes)
     keep = ~(nyq[k2, k1] | zero[k2, k1])
     k1, k2 = k1[keep], k2[keep]
     W = (rng.standard_normal((k1.size, NZ, 3, 3)) + 1j * rng.standard_normal((k1.size, NZ, 3, 3))) * 1e-3
     W = 0.5 * (W + np.swapaxes(W, -1, -2))
     Q = np.stack([Q1[k2, k1], Q2[k2, k1]], axis=1)
+    t0 = time.perf_counter()
+    w = T.hooke6(ep, lam, mu, axis=1).reshape(nl * 6, N2, N1)[:planes]
+    back = np.fft.ifft2(np.fft.fft2(w, axes=(-2, -1)), axes=(-2, -1)).real
+    t_fft = time.perf_counter() - t0
+    assert back.shape == w.shape
+    op._MODE_CACHE.clear()
     t1 = time.perf_counter()
     op.mindlin_modes(W, Q, z, E, NU)
-    t_modes = (time.perf_counter() - t1) * (N1 * (N2 // 2)) / k1.size
-    total = t_fft + t_modes
+    t_modes = time.perf_counter() - t1
+    return t_fft, t_modes, int(k1.size)
+
+
+def _oracle_worker(inq, outq):
+    """Spawned worker: runs oracle sample jobs until it receives None."""
+    outq.put("ready")
+    while True:
+        job = inq.get()
+        if job is None:
+            return
+        outq.put(_oracle_job(*job))
+
+
+# one BLAS / OpenMP thread per worker process, so that "cores" counts processes
+_ONE_THREAD_ENV = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                                    "BLIS_NUM_THREADS", "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS")}
+
+
+class OracleWorkers:
+    """A set of spawned single-threaded processes that run oracle sample jobs at the same time
+    (spawned, never forked: the parent may hold a CUDA context)."""
+
+    def __init__(self, n):
+        import multiprocessing as mp
+
+        ctx = mp.get_context("spawn")
+        saved = {k: os.environ.get(k) for k in _ONE_THREAD_ENV}
+        os.environ.update(_ONE_THREAD_ENV)
+        try:
+            self.q = [(ctx.Queue(), ctx.Queue()) for _ in range(n)]
+            self.p = [ctx.Process(target=_oracle_worker, args=qq, daemon=True) for qq in self.q]
+            for p in self.p:
+                p.start()
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        for _, outq in self.q:
+            assert outq.get(timeout=600) == "ready"
+
+    def run(self, jobs):
+        """One job per worker (len(jobs) <= workers), all started together."""
+        for (inq, _), job in zip(self.q, jobs):
+            inq.put(job)
+        return [outq.get(timeout=1800) for (_, outq), _ in zip(self.q, jobs)]
+
+    def close(self):
+        for inq, _ in self.q:
+            inq.put(None)
+        for p in self.p:
+            p.join(timeout=60)
+
+
+def _full_apply_s(t_fft, t_modes, planes, kept):
+    """Extrapolation of one sample to a whole apply: 384 planes each way, 131 072 modes."""
+    return t_fft * (NZ * 6) / planes + t_modes * (N1 * (N2 // 2)) / kept
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(planes=24, modes=256, seed=SEED, workers=None):
+    """Time the FP64 oracle on the host cores: one single-threaded process alone (the 1-core
+    figure), then one single-threaded process per core, all at once, each on its own sample
+    (the all-core figure); every sample is extrapolated to a whole apply (_full_apply_s)."""
+    n = host_cores()
+    own = workers is None
+    w = workers or OracleWorkers(n)
+    try:
+        t1 = w.run([(planes, modes, seed)])[0]
+        one = _full_apply_s(t1[0], t1[1], planes, t1[2])
+        res = w.run([(planes, modes, seed + 1 + i) for i in range(n)])
+        each = [_full_apply_s(r[0], r[1], planes, r[2]) for r in res]
+    finally:
+        if own:
+            w.close()
+    vox = N1 * N2 * NZ
     return {
-        "value": N1 * N2 * NZ / total,
+        "value": n * vox / float(np.mean(each)),
         "unit": UNIT,
-        "cores": 1,
+        "cores": n,
+        "nproc": n,
         "kind": "oracle",
-        "sample": "FP64 oracle: Hooke + DFT of %d of 384 planes each way + per-mode depth quadrature on %d random "
-                  "modes, scaled to one 512x512x64 apply (%.1f s extrapolated)" % (npl, k1.size, total),
+        "one_core": {"value": vox / one, "unit": UNIT, "cores": 1},
+        "sample": "FP64 oracle (numpy, one BLAS thread per process): per process Hooke + DFT of %d of 384 "
+                  "planes each way + per-mode depth quadrature on %d random modes, extrapolated to one "
+                  "512x512x64 apply (%.0f s on one core alone); all-core = %d such processes at once"
+                  % (planes, modes, one, n),
     }
 
 
@@ -759,17 +879,22 @@ def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
         return
-    # each step samples a bounded part of one apply; the sample shrinks with the step count so
-    # that the whole run stays within a few minutes
+    # each step runs one all-core sample of the oracle (a bounded part of one apply per core);
+    # the sample shrinks with the step count so that the whole run stays within a few minutes
     nsteps = args.warmup + args.steps
-    planes, modes = (4, 16) if nsteps <= 60 else (1, 4)
-    _operator_input()
-    t = []
-    for i in range(nsteps):
-        cb = cpu_baseline(sample_modes=modes, sample_planes=planes, seed=SEED + i)
-        if i >= args.warmup:
-            t.append(cb["value"])
-    value = float(np.median(t))
+    planes, modes = (12, 96) if nsteps <= 40 else (6, 32)
+    n = host_cores()
+    w = OracleWorkers(n)
+    vals, one = [], None
+    try:
+        for i in range(nsteps):
+            res = w.run([(planes, modes, SEED + 1000 * i + j) for j in range(n)])
+            each = [_full_apply_s(r[0], r[1], planes, r[2]) for r in res]
+            if i >= args.warmup:
+                vals.append(n * N1 * N2 * NZ / float(np.mean(each)))
+    finally:
+        w.close()
+    value = float(np.median(vals))
     line = {
         "metric": METRIC,
         "value": value,
@@ -786,9 +911,10 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n1": N1, "n2": N2, "nz": NZ, "depth": DEPTH, "output": "stress",
                    "voxels": N1 * N2 * NZ},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "per step: FP64 oracle Hooke + DFT of %d of 384 planes each way + depth "
-                                   "quadrature on <=%d random modes, scaled to one full apply" % (planes, modes)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": n, "nproc": n, "kind": "oracle",
+                         "sample": "per step: %d single-threaded processes at once, each FP64 oracle Hooke + DFT "
+                                   "of %d of 384 planes each way + depth quadrature on %d random modes, "
+                                   "extrapolated to one full apply" % (n, planes, modes)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

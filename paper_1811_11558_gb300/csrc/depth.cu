@@ -258,12 +258,14 @@ template <typename T> struct ModeGeom {
   bool zero, nyq;
 };
 
-// wavevector of the mode (k1, k2) in the arithmetic of the path: w1 = 2 pi / L1, w2 = 2 pi / L2
+// wavevector of the mode (k1, k2) in the arithmetic of the path: w1 = 2 pi / L1, w2 = 2 pi / L2.
+// k2 is signed (k2 - N2 above N2/2); modes outside Z^2_N (k1 = N1/2 or k2 = N2/2 on even
+// sides) and the padding columns k1 >= hs carry no operator term (flag nyq).
 template <typename T>
-__device__ __forceinline__ ModeGeom<T> mode_geom(int k1, int k2, int n2, T w1, T w2) {
+__device__ __forceinline__ ModeGeom<T> mode_geom(int k1, int k2, int n1, int n2, int hs, T w1, T w2) {
   ModeGeom<T> g;
-  const int k2s = k2 < n2 / 2 ? k2 : k2 - n2;
-  g.nyq = (k2 == n2 / 2);
+  const int k2s = 2 * k2 < n2 ? k2 : k2 - n2;
+  g.nyq = (2 * k2 == n2) || (2 * k1 == n1) || k1 >= hs;
   g.zero = (k1 == 0 && k2 == 0);
   const T q1 = w1 * (T)k1;
   const T q2 = w2 * (T)k2s;
@@ -282,7 +284,7 @@ __device__ __forceinline__ ModeGeom<T> mode_geom(int k1, int k2, int n2, T w1, T
 // ----------------------------------------------------------------------------------
 template <typename T, int KT, bool EIN>
 __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __restrict__ spec, typename Cx<T>::t* __restrict__ surf,
-                                const T* __restrict__ zn, int nz, int n2, int h1, int C, int nch, int prow, T w1,
+                                const T* __restrict__ zn, int nz, int n1, int n2, int hs, int h1, int C, int nch, int prow, T w1,
                                 T w2, T lam, T mu, T nu, int out_kind, int want_u3, int uniform, T hz,
                                 const int* __restrict__ zr) {
   typedef typename Cx<T>::t V;
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
   cp_async_wait_all();
   __syncthreads();
 
-  const ModeGeom<T> g = mode_geom<T>(k1, k2, n2, w1, w2);
+  const ModeGeom<T> g = mode_geom<T>(k1, k2, n1, n2, hs, w1, w2);
   const bool special = g.zero || g.nyq;
   const int n0 = ch * C;
   const int nend = min(n0 + C, nz);
@@ -561,7 +563,7 @@ template <typename V> __device__ __forceinline__ void ld6(V (&w)[6], const V* W,
 template <typename T, int KT, int C, bool EIN>
 __global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* __restrict__ spec,
                                                             typename Cx<T>::t* __restrict__ surf,
-                                                            const T* __restrict__ zn, int nz, int n2, int h1, int nch,
+                                                            const T* __restrict__ zn, int nz, int n1, int n2, int hs, int h1, int nch,
                                                             T w1, T w2, T lam, T mu, T nu, int out_kind, int want_u3,
                                                             int uniform, T hz, const int* __restrict__ zr) {
   typedef typename Cx<T>::t V;
@@ -603,7 +605,7 @@ __global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* _
   cp_async_wait_all();
   __syncthreads();
 
-  const ModeGeom<T> g = mode_geom<T>(k1, k2, n2, w1, w2);
+  const ModeGeom<T> g = mode_geom<T>(k1, k2, n1, n2, hs, w1, w2);
   const bool special = g.zero || g.nyq;
   const int n0 = ch * C;
   const int nend = min(n0 + C, nz);
@@ -832,13 +834,13 @@ __global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* _
 // ----------------------------------------------------------------------------------
 template <typename T>
 __global__ void k_boussinesq(typename Cx<T>::t* __restrict__ spec, typename Cx<T>::t* __restrict__ surf,
-                             const T* __restrict__ zn, int nz, int n2, int h1, T w1, T w2, T lam, T mu,
-                             T nu, int out_kind, int want_vol, int want_u3) {
+                             const T* __restrict__ zn, int nz, int n1, int n2, int hs, int h1, T w1, T w2, T lam,
+                             T mu, T nu, int out_kind, int want_vol, int want_u3) {
   typedef typename Cx<T>::t V;
   const int k1 = blockIdx.x * blockDim.x + threadIdx.x;
   const int k2 = blockIdx.y;
   if (k1 >= h1) return;
-  const ModeGeom<T> g = mode_geom<T>(k1, k2, n2, w1, w2);
+  const ModeGeom<T> g = mode_geom<T>(k1, k2, n1, n2, hs, w1, w2);
   const size_t plane = (size_t)n2 * h1;
   const size_t at = (size_t)k2 * h1 + k1;
   const V p = surf[at];
@@ -962,7 +964,8 @@ int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps
   if (C == CV && eps_in == EI) {                                                                                \
     smem_cap(k_mindlin_depth_r<T, 16, CV, EI>);                                                                 \
     k_mindlin_depth_r<T, 16, CV, EI><<<grid, d.threads, d.smem, c->stream>>>(                                   \
-        (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, n2, h1, nch, w1, w2, (T)c->lam, (T)c->mu, (T)c->nu,   \
+        (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, c->n1, n2, c->hs, h1, nch, w1, w2, (T)c->lam, (T)c->mu, \
+        (T)c->nu,                                                                                              \
         out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz, zr);                                                    \
   }
     DEPTHR(2, false) DEPTHR(3, false) DEPTHR(4, false) DEPTHR(6, false) DEPTHR(8, false)
@@ -975,7 +978,8 @@ int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps
   if (KT == KTV && eps_in == EI) {                                                                             \
     smem_cap(k_mindlin_depth<T, KTV, EI>);                                                                     \
     k_mindlin_depth<T, KTV, EI><<<grid, d.threads, d.smem, c->stream>>>(                                       \
-        (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, n2, h1, C, nch, prow, w1, w2, (T)c->lam, (T)c->mu,   \
+        (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, c->n1, n2, c->hs, h1, C, nch, prow, w1, w2, (T)c->lam,  \
+        (T)c->mu,                                                                                              \
         (T)c->nu, out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz, zr);                                       \
   }
   DEPTH(16, false) DEPTH(8, false) DEPTH(4, false) DEPTH(2, false)
@@ -989,7 +993,8 @@ template <typename T> int launch_boussinesq(const fvim_ctx* c, int out_kind, boo
   typedef typename Cx<T>::t V;
   const int threads = 128;
   dim3 grid((c->h1 + threads - 1) / threads, c->n2);
-  k_boussinesq<T><<<grid, threads, 0, c->stream>>>((V*)c->spec, (V*)c->surf, (const T*)c->z_dev, c->nz, c->n2, c->h1,
+  k_boussinesq<T><<<grid, threads, 0, c->stream>>>((V*)c->spec, (V*)c->surf, (const T*)c->z_dev, c->nz, c->n1, c->n2,
+                                                   c->hs, c->h1,
                                                    (T)(kTwoPi / c->L1), (T)(kTwoPi / c->L2), (T)c->lam, (T)c->mu, (T)c->nu,
                                                    out_kind, want_vol ? 1 : 0, want_u3 ? 1 : 0);
   FVIM_CUDA_CHECK_LAUNCH();

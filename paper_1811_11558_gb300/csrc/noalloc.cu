@@ -130,6 +130,7 @@ extern "C" int fvim_apply_mindlin_noalloc(int n1, int n2, int nz, const double* 
   c.n2 = n2;
   c.nz = nz;
   c.h1 = n1 / 2;
+  c.hs = c.h1;
   c.prec = precision;
   c.L1 = L1;
   c.L2 = L2;

@@ -130,8 +130,7 @@ int fvim_autotune(fvim_ctx* c, int reps, fvim_plan* out) {
 }
 
 int fvim_plan_candidates(int n1, int n2, int nz, int precision, int* chunks, int max_chunks) {
-  if (n1 < 4 || n2 < 2 || (n1 & (n1 - 1)) || (n2 & (n2 - 1)) || n1 > 1024 || n2 > 1024 || nz < 2 || nz > 512)
-    return FVIM_ERR_ARG;
+  if (!grid_ok(n1, n2) || nz < 2 || nz > 512) return FVIM_ERR_ARG;
   if ((precision != FVIM_FP32 && precision != FVIM_FP64) || !chunks || max_chunks < 1) return FVIM_ERR_ARG;
   // the launch rules need the grid and precision only: a host-side description of the grid
   fvim_ctx g;
@@ -139,7 +138,9 @@ int fvim_plan_candidates(int n1, int n2, int nz, int precision, int* chunks, int
   g.n1 = n1;
   g.n2 = n2;
   g.nz = nz;
-  g.h1 = n1 / 2;
+  g.gen = grid_gen(n1, n2) ? 1 : 0;
+  g.h1 = spec_stride(n1, n2);
+  g.hs = g.gen ? n1 / 2 + 1 : g.h1;
   g.prec = precision;
   const std::vector<int> cand = candidates(&g);
   const int n = (int)cand.size() < max_chunks ? (int)cand.size() : max_chunks;

@@ -46,7 +46,10 @@ def test_create_rejects_bad_grid_without_launching():
     h = ctypes.c_void_p()
     z = np.array([0.0, 0.1])
     zp = z.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-    assert L.fvim_create(ctypes.byref(h), 6, 8, 2, zp, 1.0, 1.0, 0, None) == -1      # n1 not a power of 2
+    assert L.fvim_create(ctypes.byref(h), 6, 8, 2, zp, 1.0, 1.0, 0, None) == -1      # even, not a power of 2
+    assert L.fvim_create(ctypes.byref(h), 81, 512, 2, zp, 1.0, 1.0, 0, None) == -1   # odd side with a 512 side
+    assert L.fvim_create(ctypes.byref(h), 257, 9, 2, zp, 1.0, 1.0, 0, None) == -1    # odd side beyond 255
+    assert L.fvim_create(ctypes.byref(h), 1, 9, 2, zp, 1.0, 1.0, 0, None) == -1      # a single point
     assert L.fvim_create(ctypes.byref(h), 8, 8, 1, zp, 1.0, 1.0, 0, None) == -1      # one node
     assert L.fvim_create(ctypes.byref(h), 8, 8, 2, zp, -1.0, 1.0, 0, None) == -1     # bad cell
     assert L.fvim_create(ctypes.byref(h), 8, 8, 2, zp, 1.0, 1.0, 7, None) == -1      # bad precision
