@@ -265,7 +265,7 @@ def run_gpu(args):
         "peak_kind": peak_kind,
         "unit": "GB/s",
         "frac": round(achieved / peak, 4),
-        "traffic": TRAFFIC_BYTES.get(dom_name) if plan["depth_chunk"] == TRAFFIC_DEPTH_CHUNK or
+        "traffic": TRAFFIC_BYTES.get(dom_name) if (plan["depth_chunk"], plan["depth_ctas"]) == TRAFFIC_DEPTH_PLAN or
         dom_name != "mindlin_depth" else None,
         "alg_bytes": alg_bytes,
         "avg_launch_ms": round(avg_ms, 5),
@@ -403,6 +403,8 @@ def rough_metrics(n=1024, nz=32, depth=0.05, seed=1813, n_inc=10, cap=120):
     p = torch.zeros(ctx.surf_shape, dtype=torch.float32, device="cuda")
     out = {"workload": "rough_%dx%dx%d_fp32" % (n, n, nz), "depth": depth, "seed": seed}
     W = 1e-3 * E * 0.1
+    # FP32: the coupling error floors near 1e-7..1e-6 once the plastic zone is large (the inner
+    # DF-SANE solves stop at the FP32 rounding floor of the residual), so 1e-6 here
     opts = ctx.default_opts(relax=0.3, max_iter=cap, tol=1e-6)
     ctx.reset_state()
     torch.cuda.synchronize()
@@ -441,15 +443,17 @@ def epp_loads():
     return sorted(set(np.round(np.linspace(0.9, 15.5, 20), 12).tolist()) | {1.0, 2.1, 6.4, 15.5})
 
 
-def epp_metrics(n=81, nz=32, a_y_over_L=0.05, relax=0.5, cap=200):
+def epp_metrics(n=81, nz=32, a_y_over_L=0.05, relax=0.5, cap=120, n64=4):
     """Elastic-perfectly-plastic Hertz load sweep at the paper's discretisation (App. C.2): cell
     [0, 20 R / 3]^2 x [0, 10 R / 3] with L = 1 (R = 0.15, depth 0.5), N = (81, 81, 32), nu = 0.3,
-    E_h = 0, W / W_y over epp_loads() one increment each (the state carries over), Algorithm-1
-    tolerance 1e-9 (FP64) as in the paper and 1e-7 (FP32).  The paper leaves sigma_y free
-    (normalised results do not depend on it); here it is set so that the onset contact radius
-    a_y = pi R p_y / (2 E*) (p_y = 1.6 sigma_y) is a_y_over_L of the cell.  Reports per load the
-    peak pressure over sigma_y, the contact radius over a_y (from the contact area), the peak
-    plastic strain and the coupling iterations, for FP64 and FP32."""
+    E_h = 0, W / W_y over epp_loads() one increment each (the state carries over), relaxation
+    0.5.  The paper leaves sigma_y free (normalised results do not depend on it); here it is set
+    so that the onset contact radius a_y = pi R p_y / (2 E*) (p_y = 1.6 sigma_y) is a_y_over_L
+    of the cell.  The whole sweep runs in FP32 (default tolerances: Algorithm 1 to 1e-8); plain
+    FP64 (Algorithm 1 to 1e-9, the paper's tolerance) runs the first n64 loads, and the two
+    pressures and contact areas are compared after that load.  Reports per load the peak
+    pressure over sigma_y, the contact radius over a_y (from the contact area), the peak
+    plastic strain and the coupling iterations."""
     import torch
 
     from paper_1811_11558_gb300 import Context, inputs
@@ -466,17 +470,17 @@ def epp_metrics(n=81, nz=32, a_y_over_L=0.05, relax=0.5, cap=200):
     out = {"workload": "epp_hertz_%dx%dx%d" % (n, n, nz), "W_over_W_y": loads, "relax": relax, "R": R,
            "sigma_y_over_E_star": sy / es, "a_y": a_y, "W_y": w_y}
     press = {}
-    for prec, tol in (("fp64", 1e-9), ("fp32", 1e-7)):
+    for prec, nl in (("fp32", len(loads)), ("fp64", n64)):
         ctx = Context(n, n, z, 1.0, 1.0, precision=prec, E=E, nu=NU, sigma_y=sy, E_h=0.0)
         ctx.autotune()
         hd = torch.from_numpy(h).to("cuda", ctx.dtype)
         p = torch.zeros(ctx.surf_shape, dtype=ctx.dtype, device="cuda")
-        opts = ctx.default_opts(relax=relax, max_iter=cap, tol=tol)
+        opts = ctx.default_opts(relax=relax, max_iter=cap)
         rows = []
         ep = torch.empty(ctx.scal_shape, dtype=ctx.dtype, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for r in loads:      # one increment per call (the state carries over), to read each state
+        for k, r in enumerate(loads[:nl]):   # one increment per call (the state carries over)
             rep = ctx.solve_contact(hd, [r * w_y], p, opts, allow_not_converged=True)
             ctx.get_state(None, ep, None)
             area = rep["contact_area"][-1]
@@ -484,11 +488,13 @@ def epp_metrics(n=81, nz=32, a_y_over_L=0.05, relax=0.5, cap=200):
                          "a_over_a_y": float(np.sqrt(area / np.pi)) / a_y, "e_p_max": float(ep.max()),
                          "alg1_iters": rep["alg1_iters"][-1], "alg1_error": rep["alg1_error"][-1],
                          "status": rep["status"]})
+            if k + 1 == n64:
+                press[prec] = p.cpu().numpy().astype(np.float64)
         torch.cuda.synchronize()
-        out[prec] = {"ms_per_sweep": 1e3 * (time.perf_counter() - t0), "tol": tol,
+        out[prec] = {"ms": 1e3 * (time.perf_counter() - t0), "loads": nl, "tol": opts.tol,
                      "converged": sum(1 for q in rows if q["status"] == 0), "increments": rows}
-        press[prec] = p.cpu().numpy().astype(np.float64)
         ctx.close()
+    out["fp32_vs_fp64_at_load"] = loads[n64 - 1]
     out["fp32_vs_fp64_pressure_rel_l2"] = float(np.linalg.norm(press["fp32"] - press["fp64"]) /
                                                 np.linalg.norm(press["fp64"]))
     out["fp32_vs_fp64_area_diff"] = abs(float((press["fp32"] > 0).mean()) - float((press["fp64"] > 0).mean()))
@@ -531,7 +537,7 @@ def batch_problems(n_prob=64, seed=1814):
     return probs
 
 
-def batch_metrics(n_prob=64, slots=16, seed=1814, max_iter=100, n64=4):
+def batch_metrics(n_prob=64, slots=16, seed=1814, max_iter=80, n64=4):
     """Batched uneven solves: n_prob problems (batch_problems) submitted at once to the
     server (slots contexts, one stream and one set of captured graphs each, FP32 operators,
     FP64 reductions), aggregate solves/s and per-problem latency; plain FP64 and FP32 one at a
@@ -546,7 +552,7 @@ def batch_metrics(n_prob=64, slots=16, seed=1814, max_iter=100, n64=4):
 
     def req(i, pb, prec="fp32"):
         return Request(i, pb["n"], pb["z"], pb["h"], pb["loads"], precision=prec, E=E, nu=NU, sigma_y=0.05 * es,
-                       E_h=0.1 * E, opts={"relax": pb["relax"], "max_iter": max_iter, "tol": 1e-6})
+                       E_h=0.1 * E, opts={"relax": pb["relax"], "max_iter": max_iter})
 
     srv = Server(slots=slots)
     t0 = time.perf_counter()
@@ -576,8 +582,7 @@ def batch_metrics(n_prob=64, slots=16, seed=1814, max_iter=100, n64=4):
             p = torch.empty(ctx.surf_shape, dtype=ctx.dtype, device="cuda")
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ctx.solve_contact(hd, pb["loads"], p, ctx.default_opts(relax=pb["relax"], max_iter=max_iter,
-                                                                   **({"tol": 1e-6} if prec == "fp32" else {})),
+            ctx.solve_contact(hd, pb["loads"], p, ctx.default_opts(relax=pb["relax"], max_iter=max_iter),
                               allow_not_converged=True)
             t[prec].append(time.perf_counter() - t0)
             press[prec] = p.cpu().numpy().astype(np.float64)
@@ -605,86 +610,90 @@ def batch_metrics(n_prob=64, slots=16, seed=1814, max_iter=100, n64=4):
                             for pb, r in zip(probs, res)]}
 
 
-def stream_metrics(n_req=12, slots=8, seed=1815, rate_sweep=(0.4, 1.0, 1.5)):
-    """Served request stream, FP32 vs plain FP64: requests with grids drawn uniformly in log2
-    from {128, 256}, nz = round(16 x 2^U) in [16, 32], seeded self-affine surfaces (H 0.8, rms
-    slope 0.1), five-increment ramps to the paper's rough-surface load; Poisson arrivals at
-    0.7 x the single-stream FP32 capacity, then swept over rate_sweep x that capacity; p50 / p99
-    latency from arrival to result.  The FP64
-    baseline solves the first four requests one at a time; its solves/s is the mix's mean
-    service time per size class applied to the whole stream."""
+def stream_metrics(n_req=8, slots=8, seed=1815, n_inc=3, n64_max=256):
+    """Served request stream, FP32 vs plain FP64: requests with grids n^2, n drawn uniformly in
+    log2 from {128, 256, 512, 1024}, nz = round(16 x 4^U) in [16, 64] (U uniform), seeded
+    self-affine surfaces (H 0.8, rms slope 0.1, depth 0.05), load ramps of n_inc increments to
+    the paper's rough-surface load, relaxation 0.3, the default tolerances of each precision
+    (Algorithm 1: 1e-8 FP32, 1e-9 FP64).
+    Passes: every request alone, one at a time (the single-stream capacity and each request's
+    FP32 plain time); Poisson arrivals at 0.7 x that capacity; all requests at t = 0 (saturated).
+    p50 / p99 latency from arrival to result.  Plain FP64 solves the requests of grids up to
+    n64_max one at a time (a stated subsample: a 1024^2 x 64 FP64 solve takes minutes); its
+    per-request time, and the pressure error and contact-area difference of the FP32 result, are
+    reported beside the FP32 plain time of the same request."""
     import torch
 
-    from paper_1811_11558_gb300 import inputs
+    from paper_1811_11558_gb300 import Context, inputs
     from paper_1811_11558_gb300.serve import Request, Server, percentiles, poisson_arrivals
 
     rng = np.random.Generator(np.random.PCG64(seed))
     es = E / (1 - NU * NU)
-    reqs = []
+    W = 1e-3 * E * 0.1
+    specs = []
     for i in range(n_req):
-        n = int(2 ** rng.integers(7, 9))
-        nz = int(round(16 * 2 ** rng.uniform(0, 1)))
+        n = int(2 ** rng.integers(7, 11))
+        nz = int(round(16 * 4 ** rng.uniform(0, 1)))
+        specs.append((i, n, nz))
+
+    def make(i, n, nz, arrival=0.0):
         z = inputs.uniform_depth(nz, 0.05)
         h = inputs.self_affine_surface(n, 1.0, 0.8, 4, 8, min(64, n // 4), 0.1, seed=seed + 1 + i)
-        reqs.append(Request(i, n, z, h, [1e-4 * (k + 1) / 5 for k in range(5)], precision="fp32", E=E, nu=NU,
-                            sigma_y=0.05 * es, E_h=0.1 * E, opts={"relax": 0.3, "max_iter": 100, "tol": 1e-6}))
+        return Request(i, n, z, h, [W * (k + 1) / n_inc for k in range(n_inc)], precision="fp32", E=E, nu=NU,
+                       sigma_y=0.05 * es, E_h=0.1 * E, opts={"relax": 0.3, "max_iter": 150}, arrival=arrival)
+
     srv = Server(slots=slots)
-    srv.prepare(reqs)                                   # tuned tile plan per shape
-    srv.run(reqs[:4])                                   # warm the context pool
-    # single-stream capacity: one request at a time
+    srv.prepare([make(*sp) for sp in specs])            # tuned tile plan per shape
+    seen, warm = set(), []
+    for sp in specs:                                    # one request per shape warms the pool
+        if (sp[1], sp[2]) not in seen:
+            seen.add((sp[1], sp[2]))
+            warm.append(make(*sp))
+    srv.run(warm)
+    # single stream: one request at a time
     t0 = time.perf_counter()
-    one = [srv.solve(r) for r in reqs[:4]]
-    cap = 4 / (time.perf_counter() - t0)
-    rate = 0.7 * cap
-    arr = poisson_arrivals(n_req, rate, seed)
-    for r, a in zip(reqs, arr):
-        r.arrival = float(a)
-    res, wall = srv.run(reqs)
+    one = [srv.solve(make(*sp)) for sp in specs]
+    t_one = time.perf_counter() - t0
+    cap = n_req / t_one
+    res, wall = srv.run([make(*sp, arrival=float(a)) for sp, a in zip(specs, poisson_arrivals(n_req, 0.7 * cap, seed))])
     lat = percentiles([r.latency for r in res])
-    def fresh(arrivals):
-        return [Request(r.rid, r.n, r.z, r.h, r.loads, precision="fp32", E=E, nu=NU, sigma_y=r.sigma_y,
-                        E_h=r.E_h, opts=r.opts, arrival=float(a)) for r, a in zip(reqs, arrivals)]
-
-    sat, swall = srv.run(fresh(np.zeros(n_req)))
-    # the arrival rate swept as a multiple of the single-stream capacity
-    sweep = []
-    for f in rate_sweep:
-        rs, rw = srv.run(fresh(poisson_arrivals(n_req, f * cap, seed + 1)))
-        lt = percentiles([r.latency for r in rs])
-        sweep.append({"rate_over_capacity": f, "arrival_rate_per_s": f * cap, "solves_per_s": n_req / rw,
-                      "p50_ms": 1e3 * lt[50], "p99_ms": 1e3 * lt[99]})
-    # plain FP64, one request at a time
-    from paper_1811_11558_gb300 import Context
-
-    t64 = {}
-    p64 = []
-    for r in reqs[:4]:
-        ctx = Context(r.n, r.n, r.z, 1.0, 1.0, precision="fp64", E=E, nu=NU, sigma_y=r.sigma_y, E_h=r.E_h)
+    sat, swall = srv.run([make(*sp) for sp in specs])
+    slat = percentiles([r.latency for r in sat])
+    conv = {"poisson": sum(1 for r in res if r.report.get("status", 0) == 0),
+            "saturated": sum(1 for r in sat if r.report.get("status", 0) == 0)}
+    # plain FP64 on the subsample, one at a time
+    sub = []
+    for sp, o in zip(specs, one):
+        i, n, nz = sp
+        if n > n64_max:
+            continue
+        r = make(*sp)
+        ctx = Context(n, n, r.z, 1.0, 1.0, precision="fp64", E=E, nu=NU, sigma_y=r.sigma_y, E_h=r.E_h)
         ctx.autotune()
         hd = torch.from_numpy(np.ascontiguousarray(r.h)).to("cuda", torch.float64)
-        p = torch.empty(ctx.surf_shape, dtype=torch.float64, device="cuda")
+        p = torch.zeros(ctx.surf_shape, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.solve_contact(hd, r.loads, p, ctx.default_opts(relax=0.3, max_iter=100), allow_not_converged=True)
-        t64.setdefault(r.n, []).append(time.perf_counter() - t0)
-        p64.append(p.cpu().numpy())
+        rep = ctx.solve_contact(hd, r.loads, p, ctx.default_opts(relax=0.3, max_iter=150), allow_not_converged=True)
+        t64 = time.perf_counter() - t0
+        p64 = p.cpu().numpy()
         ctx.close()
-    mean64 = {k: float(np.mean(v)) for k, v in t64.items()}
-    est64 = sum(mean64.get(r.n, max(mean64.values())) for r in reqs)
-    err = [float(np.linalg.norm(one[i].pressure.astype(np.float64) - p64[i]) / np.linalg.norm(p64[i]))
-           for i in range(4)]
-    return {"workload": "rough_stream_%dreq" % n_req, "grids": sorted({r.n for r in reqs}),
-            "nz": sorted({int(np.asarray(r.z).size) for r in reqs}), "slots": slots,
-            "single_stream_fp32_solves_per_s": cap, "arrival_rate_per_s": rate,
-            "fp32_served_poisson": {"solves_per_s": n_req / wall, "p50_ms": 1e3 * lat[50], "p99_ms": 1e3 * lat[99]},
-            "fp32_served_rate_sweep": sweep,
-            "fp32_served_saturated": {"solves_per_s": n_req / swall,
-                                      "p50_ms": 1e3 * percentiles([r.latency for r in sat])[50],
-                                      "p99_ms": 1e3 * percentiles([r.latency for r in sat])[99]},
-            "fp64_plain": {"solves_per_s": n_req / est64, "measured_requests": 4,
-                           "mean_s_by_grid": {str(k): v for k, v in mean64.items()}},
-            "fp32_vs_fp64_pressure_rel_l2": err,
-            "served_saturated_over_fp64_plain": (n_req / swall) / (n_req / est64)}
+        p32 = o.pressure.astype(np.float64)
+        sub.append({"i": i, "n": n, "nz": nz, "fp64_plain_ms": 1e3 * t64, "fp32_plain_ms": 1e3 * (o.finished - o.admitted),
+                    "fp64_status": rep["status"], "fp32_status": o.report.get("status", 0),
+                    "fp32_vs_fp64_pressure_rel_l2": float(np.linalg.norm(p32 - p64) / np.linalg.norm(p64)),
+                    "fp32_vs_fp64_area_diff": abs(float((p32 > 0).mean()) - float((p64 > 0).mean()))})
+    t64s = sum(x["fp64_plain_ms"] for x in sub)
+    t32s = sum(x["fp32_plain_ms"] for x in sub)
+    return {"workload": "rough_stream_%dreq" % n_req, "requests": [{"i": i, "n": n, "nz": nz} for i, n, nz in specs],
+            "increments": n_inc, "slots": slots, "converged": conv,
+            "single_stream_fp32_solves_per_s": cap, "arrival_rate_per_s": 0.7 * cap,
+            "fp32_served_poisson": {"solves_per_s": conv["poisson"] / wall, "p50_ms": 1e3 * lat[50],
+                                    "p99_ms": 1e3 * lat[99]},
+            "fp32_served_saturated": {"solves_per_s": conv["saturated"] / swall, "p50_ms": 1e3 * slat[50],
+                                      "p99_ms": 1e3 * slat[99]},
+            "fp64_plain_subsample": {"grids_up_to": n64_max, "requests": sub,
+                                     "fp64_over_fp32_plain_time": (t64s / t32s) if t32s > 0 else None}}
 
 
 def scaling_metrics(sizes=(4, 8, 16, 32, 64, 128), reps=20):
@@ -736,7 +745,7 @@ def scaling_metrics(sizes=(4, 8, 16, 32, 64, 128), reps=20):
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each kernel on this
 # workload, from one capture of the current kernels (profiles/ summaries); a kernel missing
 # here, or changed since its capture (rows_inv6: smaller CTAs), reports null.
-TRAFFIC_DEPTH_CHUNK = 4     # depth tile plan of that capture
+TRAFFIC_DEPTH_PLAN = (4, 2)  # depth tile plan of that capture (chunk length, CTAs per SM)
 TRAFFIC_BYTES = {"rows_fwd6": 755.1e6, "cols_fwd": 744.2e6, "mindlin_depth": 743.9e6, "cols_inv": 744.4e6,
                  "rows_inv6": None}
 
@@ -845,7 +854,7 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(planes=24, modes=256, seed=SEED, workers=None):
+def cpu_baseline(planes=12, modes=160, seed=SEED, workers=None):
     """Time the FP64 oracle on the host cores: one single-threaded process alone (the 1-core
     figure), then one single-threaded process per core, all at once, each on its own sample
     (the all-core figure); every sample is extrapolated to a whole apply (_full_apply_s)."""

@@ -162,41 +162,78 @@ const char* fvim_last_cuda_error(void);
  *   depth_chunk   chunk length in use (fvim_set_plan: 0 selects the default rule,
  *                 max(2, ceil(Nz / 16)))
  *   tuned         1 if depth_chunk came from a timing run (fvim_autotune) in this process
- *   n_cand, cand[i], cand_ms[i]   fvim_autotune only: the chunk lengths timed and the median
- *                 time of one depth-kernel launch with each (ms)
+ *   n_cand, cand[i], cand_ctas[i], cand_ms[i]   fvim_autotune only: the launch shapes timed
+ *                 (chunk length, CTAs per SM) and the median time of one depth-kernel launch
+ *                 with each (ms)
+ *   depth_cutoff  eps_co of the FP32 register variant's chunk scan (the cutoff of Sec. 3.2,
+ *                 restated for the exact recursion): a tile whose chunk spans all damp by
+ *                 e^{-q span} < e^{-eps_co} takes each chunk's carry from its neighbour alone,
+ *                 skipping the log-depth scan (the dropped terms are below e^{-eps_co} of the
+ *                 moments).  Default FVIM_DEPTH_CUTOFF_DEFAULT = 18 (e^{-18} = 1.5e-8, below the
+ *                 FP32 rounding unit); fvim_set_plan: 0 selects the exact scan.  Not used by
+ *                 the shared-memory variant (FP64, deep grids), whose scan is sequential.
+ *   depth_ctas    CTAs per SM the FP32 register variant of the depth kernel is compiled for:
+ *                 2 (128 registers per thread, the default) or 3 (85 registers, chunk lengths
+ *                 4..8 whose tile fits three times in shared memory); 0 for the shared-memory
+ *                 variant (FP64, deep grids), which has one launch shape per chunk length
  */
-#define FVIM_PLAN_MAX_CAND 8
+#define FVIM_PLAN_MAX_CAND 16
+#define FVIM_DEPTH_CUTOFF_DEFAULT 18.0f
+/* in-plane FFT paths of the Mindlin apply (FP32 grids; every path gives the same operator up to
+ * rounding): FVIM_FFT_ROWCOL separate row and column kernels (every grid), FVIM_FFT_L2 one
+ * kernel per direction with the row spectra exchanged through L2, FVIM_FFT_CLUSTER one kernel
+ * per direction with the row spectra in distributed shared memory (some plane sizes) */
+#define FVIM_FFT_ROWCOL 0
+#define FVIM_FFT_L2 1
+#define FVIM_FFT_CLUSTER 2
+#define FVIM_FFT_NPATH 3
 typedef struct fvim_plan {
   int depth_chunk;
   int tuned;
   int n_cand;
   int cand[FVIM_PLAN_MAX_CAND];
+  int cand_ctas[FVIM_PLAN_MAX_CAND];
   float cand_ms[FVIM_PLAN_MAX_CAND];
+  int depth_ctas;
+  float depth_cutoff;
+  int fft_path;                    /* path in use (FVIM_FFT_*)                                   */
+  float fft_ms[FVIM_FFT_NPATH];    /* fvim_autotune: median time of one whole apply with each
+                                      path, in ms (0: not built for this grid or precision)      */
 } fvim_plan;
 
 /* fvim_autotune -- times the depth kernel on ctx's grid with every launchable chunk length
- * of {2, 3, 4, 6, 8, 12, 16} and the default, `reps` launches each on ctx's stream over its
- * (zeroed) spectrum scratch, and keeps the fastest (the default unless another is more than
- * 2 % faster) for ctx and for every context of the same grid, precision and depth spacing
- * (uniform or not) created later in this process.  Synchronises ctx's stream; leaves the
- * plastic state untouched; drops ctx's captured solver graphs when the plan changes.
- * out (host) or NULL receives the plan and the timings.  FVIM_ERR_ARG: NULL ctx, reps
- * outside [1, 1000], or ctx's stream is capturing a graph; FVIM_ERR_CUDA on a device error
+ * of {2, 3, 4, 6, 8, 12, 16} and the default, each with every register budget it is built
+ * for (depth_ctas 2 and 3), `reps` launches each on ctx's stream over its (zeroed) spectrum
+ * scratch, and keeps the fastest (the default unless another is more than 2 % faster); then, with that chunk length, times `reps` whole Mindlin applies (stress
+ * output) with every in-plane FFT path built for the grid and keeps the fastest (the
+ * row / column path unless another is more than 2 % faster).  The plan holds for ctx and for
+ * every context of the same grid, precision and depth spacing (uniform or not) created later
+ * in this process.  The apply timings read the context's plastic-strain state as input and
+ * write one volume buffer that the call allocates and frees (the only allocation it makes).
+ * Synchronises ctx's stream; leaves the plastic state untouched; drops ctx's captured solver
+ * graphs when the plan changes.  out (host) or NULL receives the plan and the timings.
+ * FVIM_ERR_ARG: NULL ctx, reps outside [1, 1000], or ctx's stream is capturing a graph;
+ * FVIM_ERR_OOM if the timing buffer cannot be allocated; FVIM_ERR_CUDA on a device error
  * (the plan is then unchanged). */
 int fvim_autotune(fvim_ctx* ctx, int reps, fvim_plan* out);
 
-/* fvim_plan_candidates -- the chunk lengths fvim_autotune would time on a grid (n1, n2, nz,
- * precision as in fvim_create), in timing order, written to chunks[0..] (host, at most
- * max_chunks); returns their number.  Host computation only (no device, no context).
- * FVIM_ERR_ARG on a grid fvim_create refuses or a bad output array. */
-int fvim_plan_candidates(int n1, int n2, int nz, int precision, int* chunks, int max_chunks);
+/* fvim_plan_candidates -- the depth-kernel launch shapes fvim_autotune would time on a grid
+ * (n1, n2, nz, precision as in fvim_create), in timing order: chunk lengths in chunks[0..] and
+ * the register budget of each (CTAs per SM, 2 or 3; 0 for the shared-memory variant) in
+ * ctas[0..] (host arrays, at most max_chunks entries; ctas may be NULL); returns their number.
+ * Host computation only (no device, no context).  FVIM_ERR_ARG on a grid fvim_create refuses
+ * or a bad output array. */
+int fvim_plan_candidates(int n1, int n2, int nz, int precision, int* chunks, int* ctas, int max_chunks);
 
-/* fvim_get_plan -- the plan ctx uses (host out; cand fields zero). */
+/* fvim_get_plan -- the plan ctx uses (host out; cand and fft_ms fields zero). */
 int fvim_get_plan(const fvim_ctx* ctx, fvim_plan* out);
 
-/* fvim_set_plan -- forces plan->depth_chunk on ctx alone (other fields ignored); the process
- * table is not changed.  FVIM_ERR_ARG if that chunk length is not launchable on ctx's grid
- * (more than 256 chunk threads per tile, or the tile does not fit in shared memory). */
+/* fvim_set_plan -- forces plan->depth_chunk, plan->depth_ctas (0 or 2: the default budget),
+ * plan->depth_cutoff (>= 0; 0: exact scan) and plan->fft_path on ctx alone (other fields
+ * ignored); the process table is not changed.
+ * FVIM_ERR_ARG if that launch shape is not launchable on ctx's grid (more than 256 chunk
+ * threads per tile, the tile does not fit in shared memory, or no such register budget) or
+ * that FFT path is not built for ctx's grid and precision. */
 int fvim_set_plan(fvim_ctx* ctx, const fvim_plan* plan);
 
 /* fvim_last_kernel_count -- number of kernels the last entry point launched. */

@@ -170,6 +170,7 @@ template <typename T> int upload_nodes(fvim_ctx* c) {
 // kernels, which are faster on the 512 x 512 planes measured so far (one cluster of eight
 // 209 KB CTAs per plane leaves the load, transform and store phases of a CTA serialised)
 static bool use_fft2_cluster(fvim_ctx* c) {
+  if (c->fft_path >= 0) return c->fft_path == FVIM_FFT_CLUSTER;
   if (c->fft2_cl < 0) {
     const char* e = getenv("FVIM_FFT2_CLUSTER");
     c->fft2_cl = (e && e[0] == '1' && fft2_cluster_available(c)) ? 1 : 0;
@@ -182,11 +183,20 @@ static bool use_fft2_cluster(fvim_ctx* c) {
 // column kernels, which are faster at 512 x 512 although they move twice the bytes (the
 // one-pass kernels are bound by L1 and shared-memory traffic at 24 warps per SM)
 static bool use_fft2_fused(fvim_ctx* c) {
+  if (c->fft_path >= 0) return c->fft_path == FVIM_FFT_L2;
   if (c->fft2_fused < 0) {
     const char* e = getenv("FVIM_FFT2_FUSED");
     c->fft2_fused = (e && e[0] == '1' && fft2_fused_available(c)) ? 1 : 0;
   }
   return c->fft2_fused == 1;
+}
+
+bool fft_path_available(const fvim_ctx* c, int path) {
+  if (path == FVIM_FFT_ROWCOL) return true;
+  if (c->gen || c->prec != FVIM_FP32) return false;
+  if (path == FVIM_FFT_L2) return fft2_fused_available(c);
+  if (path == FVIM_FFT_CLUSTER) return fft2_cluster_available(c);
+  return false;
 }
 
 // Mindlin apply in three passes: 2-D FFT of the eps_p planes, the depth operator with Hooke's
@@ -460,6 +470,7 @@ int fvim_create(fvim_ctx** out, int n1, int n2, int nz, const double* z_nodes, d
   memset(c, 0, sizeof(*c));
   c->fft2_cl = -1;
   c->fft2_fused = -1;
+  c->fft_path = -1;
   c->n1 = n1;
   c->n2 = n2;
   c->nz = nz;
@@ -480,8 +491,11 @@ int fvim_create(fvim_ctx** out, int n1, int n2, int nz, const double* z_nodes, d
     if (fabs((z_nodes[i] - z_nodes[i - 1]) - h) > 1e-12 * fabs(z_nodes[nz - 1])) c->uniform = 0;
   c->hz = h;
   fvim_set_material(c, 1.0, 0.3, INFINITY, 0.0);
-  // a grid tuned earlier in this process starts with its tuned tile plan
+  // a grid tuned earlier in this process starts with its tuned tile plan and FFT path
   if ((c->depth_chunk = plan_lookup(c)) > 0) c->plan_tuned = 1;
+  c->fft_path = plan_lookup_fft(c);
+  c->depth_ctas = plan_lookup_ctas(c);
+  c->depth_cut = FVIM_DEPTH_CUTOFF_DEFAULT;
   int rc;
   const size_t es = precision == FVIM_FP64 ? 8 : 4;
   const size_t cs = 2 * es;

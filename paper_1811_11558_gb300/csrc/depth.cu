@@ -560,12 +560,12 @@ template <typename V> __device__ __forceinline__ void ld6(V (&w)[6], const V* W,
   for (int cc = 0; cc < 6; ++cc) w[cc] = W[(node * 6 + cc) * KT + kt];
 }
 
-template <typename T, int KT, int C, bool EIN>
-__global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* __restrict__ spec,
+template <typename T, int KT, int C, bool EIN, int MB>
+__global__ void __launch_bounds__(256, MB) k_mindlin_depth_r(typename Cx<T>::t* __restrict__ spec,
                                                             typename Cx<T>::t* __restrict__ surf,
                                                             const T* __restrict__ zn, int nz, int n1, int n2, int hs, int h1, int nch,
                                                             T w1, T w2, T lam, T mu, T nu, int out_kind, int want_u3,
-                                                            int uniform, T hz, const int* __restrict__ zr) {
+                                                            int uniform, T hz, const int* __restrict__ zr, T cut) {
   typedef typename Cx<T>::t V;
   static_assert(sizeof(V) == 8 && KT % 2 == 0, "FP32 tiles of an even width");
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -679,8 +679,15 @@ __global__ void __launch_bounds__(256, 2) k_mindlin_depth_r(typename Cx<T>::t* _
   //    - branch downwards, Ta_j = sum_{i<=j} propA(S_i, q (z[e1_j] - z[e1_i]));
   //    + branch upwards,  Up_j = sum_{i>=j} propP(S_i, q (z[n0_i] - z[n0_j])).
   //    Propagations compose (prop(prop(M, a), b) = prop(M, a + b)), so the rounds are exact.
+  // Cutoff (Sec. 3.2, eps_co, restated for the recursion): when every chunk span of the tile
+  // damps by e^{-q span} < e^{-cut}, a chunk's carry is its neighbour's own summary to the
+  // rounding of the path (e^{-18} < 2^-24 in FP32): the chunks beyond the neighbour contribute
+  // below it, so the scan rounds are skipped (one block-wide vote keeps the branch uniform)
+  const T span = (work && ch + 1 < nch) ? zs[e1] - zs[n0] : (T)0;
+  const bool far = !work || ch + 1 >= nch || g.q * span > cut;
+  const bool local = __syncthreads_and(cut > (T)0 && far) != 0;
   const int e1c = e1;
-  for (int d = 1; d < nch; d <<= 1) {
+  for (int d = 1; d < nch && !local; d <<= 1) {
     SA[ch * KT + kt] = Ta;
     SP[ch * KT + kt] = Up;
     __syncthreads();
@@ -899,6 +906,7 @@ template <typename T> struct DepthCfg {
   bool reg;       // FP32 register variant
   int C, nch, KT, threads;
   size_t smem;
+  int mb;         // register variant: CTAs per SM it is compiled for (2: 128 registers, 3: 85)
 };
 
 int depth_chunk_default(int nz) {
@@ -906,7 +914,7 @@ int depth_chunk_default(int nz) {
   return C < 2 ? 2 : C;
 }
 
-template <typename T> DepthCfg<T> depth_cfg(const fvim_ctx* c, int C) {
+template <typename T> DepthCfg<T> depth_cfg(const fvim_ctx* c, int C, int ctas) {
   typedef typename Cx<T>::t V;
   DepthCfg<T> d{};
   const int nz = c->nz, h1 = c->h1;
@@ -921,11 +929,14 @@ template <typename T> DepthCfg<T> depth_cfg(const fvim_ctx* c, int C) {
       const size_t smr = (size_t)nz * 6 * 16 * sizeof(V) + (size_t)(2 * nchr) * 16 * sizeof(Mom<V>) +
                          (size_t)3 * 16 * sizeof(V) + (size_t)nz * sizeof(T);
       if (smr <= 227 * 1024 && 16 * nchr <= 256) {
-        d = DepthCfg<T>{true, true, CR, nchr, 16, 16 * nchr, smr};
+        // three CTAs per SM (85 registers): chunk lengths 4..8 whose tile fits three times
+        if (ctas == 3 && !(CR >= 4 && 3 * (smr + 1024) <= 228 * 1024)) return d;
+        d = DepthCfg<T>{true, true, CR, nchr, 16, 16 * nchr, smr, ctas == 3 ? 3 : 2};
         return d;
       }
     }
   }
+  if (ctas == 3) return d;  // the shared-memory variant has one launch shape per chunk length
   const int nch = (nz + C - 1) / C;
   const int prow = nz > 2 * nch + 1 ? nz : 2 * nch + 1;
   // tile width: 16 k1 columns (128-byte rows in FP32), narrower where the depth column of
@@ -945,31 +956,40 @@ template <typename T> DepthCfg<T> depth_cfg(const fvim_ctx* c, int C) {
   return d;
 }
 
-bool depth_chunk_ok(const fvim_ctx* c, int C) {
-  return c->prec == FVIM_FP64 ? depth_cfg<double>(c, C).ok : depth_cfg<float>(c, C).ok;
+int depth_launch_ctas(const fvim_ctx* c) {
+  const int C = c->depth_chunk > 0 ? c->depth_chunk : depth_chunk_default(c->nz);
+  if (c->prec == FVIM_FP64) return 0;
+  const DepthCfg<float> d = depth_cfg<float>(c, C, c->depth_ctas);
+  return d.ok && d.reg ? d.mb : 0;
+}
+
+bool depth_chunk_ok(const fvim_ctx* c, int C, int ctas) {
+  return c->prec == FVIM_FP64 ? depth_cfg<double>(c, C, ctas).ok : depth_cfg<float>(c, C, ctas).ok;
 }
 
 template <typename T>
 int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps_in, const int* zr) {
   typedef typename Cx<T>::t V;
   const int nz = c->nz, h1 = c->h1, n2 = c->n2;
-  const DepthCfg<T> d = depth_cfg<T>(c, c->depth_chunk > 0 ? c->depth_chunk : depth_chunk_default(nz));
+  const DepthCfg<T> d = depth_cfg<T>(c, c->depth_chunk > 0 ? c->depth_chunk : depth_chunk_default(nz), c->depth_ctas);
   if (!d.ok) return FVIM_ERR_UNSUPPORTED;
   const int KT = d.KT, C = d.C, nch = d.nch;
   const int prow = nz > 2 * nch + 1 ? nz : 2 * nch + 1;
   dim3 grid(h1 / KT, n2);
   const T w1 = (T)(kTwoPi / c->L1), w2 = (T)(kTwoPi / c->L2);
   if constexpr (sizeof(T) == 4) if (d.reg) {
-#define DEPTHR(CV, EI)                                                                                          \
-  if (C == CV && eps_in == EI) {                                                                                \
-    smem_cap(k_mindlin_depth_r<T, 16, CV, EI>);                                                                 \
-    k_mindlin_depth_r<T, 16, CV, EI><<<grid, d.threads, d.smem, c->stream>>>(                                   \
+#define DEPTHR(CV, EI, MBV)                                                                                     \
+  if (C == CV && eps_in == EI && d.mb == MBV) {                                                                 \
+    smem_cap(k_mindlin_depth_r<T, 16, CV, EI, MBV>);                                                            \
+    k_mindlin_depth_r<T, 16, CV, EI, MBV><<<grid, d.threads, d.smem, c->stream>>>(                              \
         (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, c->n1, n2, c->hs, h1, nch, w1, w2, (T)c->lam, (T)c->mu, \
         (T)c->nu,                                                                                              \
-        out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz, zr);                                                    \
+        out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz, zr, (T)c->depth_cut);                                  \
   }
-    DEPTHR(2, false) DEPTHR(3, false) DEPTHR(4, false) DEPTHR(6, false) DEPTHR(8, false)
-    DEPTHR(2, true) DEPTHR(3, true) DEPTHR(4, true) DEPTHR(6, true) DEPTHR(8, true)
+    DEPTHR(2, false, 2) DEPTHR(3, false, 2) DEPTHR(4, false, 2) DEPTHR(6, false, 2) DEPTHR(8, false, 2)
+    DEPTHR(2, true, 2) DEPTHR(3, true, 2) DEPTHR(4, true, 2) DEPTHR(6, true, 2) DEPTHR(8, true, 2)
+    DEPTHR(4, false, 3) DEPTHR(6, false, 3) DEPTHR(8, false, 3)
+    DEPTHR(4, true, 3) DEPTHR(6, true, 3) DEPTHR(8, true, 3)
 #undef DEPTHR
     FVIM_CUDA_CHECK_LAUNCH();
     return FVIM_OK;

@@ -456,15 +456,27 @@ struct fvim_ctx {
   void* srt;       // solver runtime (solvers.cu): own stream, events, captured CUDA graphs
   int depth_chunk; // depth nodes per chunk thread of the depth kernel; 0: depth_chunk_default
   int plan_tuned;  // depth_chunk came from a timing run (fvim_autotune) in this process
+  int depth_ctas;  // CTAs per SM of the FP32 register depth kernel: 0 or 2 (128 registers), 3 (85)
+  float depth_cut; // chunk-scan cutoff eps_co of the FP32 register depth kernel (0: exact scan)
   int fft2_fused;  // one-pass 2-D FFTs through L2: -1 not yet known, 0 not used, 1 used
+  int fft_path;    // in-plane FFT path chosen by the tuner or fvim_set_plan (FVIM_FFT_*), -1: none
+                   // (the row / column kernels unless an environment variable selects another)
 };
 
 // tile plan of the depth kernel (depth.cu): default chunk length, and whether a chunk length
 // gives a launchable configuration on this context's grid and precision
 int depth_chunk_default(int nz);
-bool depth_chunk_ok(const fvim_ctx* c, int chunk);
-// process-wide plan table (tune.cu): the tuned chunk length of a grid, or 0
+// ctas: CTAs per SM the FP32 register variant is compiled for (2 default, 3 with 85 registers)
+bool depth_chunk_ok(const fvim_ctx* c, int chunk, int ctas = 2);
+// CTAs per SM of the depth kernel's launch under the context's plan (0: shared-memory variant)
+int depth_launch_ctas(const fvim_ctx* c);
+// process-wide plan table (tune.cu): the tuned chunk length of a grid, or 0; its tuned FFT
+// path, or -1
 int plan_lookup(const fvim_ctx* c);
+int plan_lookup_fft(const fvim_ctx* c);
+int plan_lookup_ctas(const fvim_ctx* c);
+// whether an in-plane FFT path is built for the context's grid and precision (capi.cu)
+bool fft_path_available(const fvim_ctx* c, int path);
 
 // kernel kinds for fvim_profile_read
 enum ProfSlot {

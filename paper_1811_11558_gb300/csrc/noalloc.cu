@@ -131,6 +131,7 @@ extern "C" int fvim_apply_mindlin_noalloc(int n1, int n2, int nz, const double* 
   c.nz = nz;
   c.h1 = n1 / 2;
   c.hs = c.h1;
+  c.fft_path = FVIM_FFT_ROWCOL;
   c.prec = precision;
   c.L1 = L1;
   c.L2 = L2;
@@ -148,6 +149,8 @@ extern "C" int fvim_apply_mindlin_noalloc(int n1, int n2, int nz, const double* 
   // a grid tuned earlier in this process (fvim_autotune) runs its tuned depth tile plan, as a
   // context created for it would (host-only table lookup)
   if ((c.depth_chunk = plan_lookup(&c)) > 0) c.plan_tuned = 1;
+  c.depth_ctas = plan_lookup_ctas(&c);
+  c.depth_cut = FVIM_DEPTH_CUTOFF_DEFAULT;
   if (precision == FVIM_FP64)
     return run<double>(&c, (unsigned char*)base, (const double*)eps_p, (double*)out, out_kind, (double*)u3_surface);
   return run<float>(&c, (unsigned char*)base, (const float*)eps_p, (float*)out, out_kind, (float*)u3_surface);

@@ -48,27 +48,44 @@ class Report(ctypes.Structure):
                 "residual_evals": self.residual_evals, "mindlin_applies": self.mindlin_applies}
 
 
-PLAN_MAX_CAND = 8
+PLAN_MAX_CAND = 16
+FFT_PATHS = ("rows_cols", "l2_exchange", "cluster")   # FVIM_FFT_ROWCOL, FVIM_FFT_L2, FVIM_FFT_CLUSTER
 
 
 class Plan(ctypes.Structure):
     """fvim_plan (include/fvim.h)."""
     _fields_ = [("depth_chunk", ctypes.c_int), ("tuned", ctypes.c_int), ("n_cand", ctypes.c_int),
-                ("cand", ctypes.c_int * PLAN_MAX_CAND), ("cand_ms", ctypes.c_float * PLAN_MAX_CAND)]
+                ("cand", ctypes.c_int * PLAN_MAX_CAND), ("cand_ctas", ctypes.c_int * PLAN_MAX_CAND),
+                ("cand_ms", ctypes.c_float * PLAN_MAX_CAND), ("depth_ctas", ctypes.c_int),
+                ("depth_cutoff", ctypes.c_float), ("fft_path", ctypes.c_int),
+                ("fft_ms", ctypes.c_float * len(FFT_PATHS))]
 
     def as_dict(self):
+        """timings_ms: chunk length -> ms with the default register budget; timings_ms_3ctas:
+        the same with three CTAs per SM (85 registers), where built."""
         n = self.n_cand
-        return {"depth_chunk": self.depth_chunk, "tuned": bool(self.tuned),
-                "timings_ms": {int(self.cand[i]): float(self.cand_ms[i]) for i in range(n)}}
+        d = {"depth_chunk": self.depth_chunk, "depth_ctas": self.depth_ctas,
+             "depth_cutoff": round(float(self.depth_cutoff), 6), "tuned": bool(self.tuned),
+             "timings_ms": {int(self.cand[i]): float(self.cand_ms[i]) for i in range(n) if self.cand_ctas[i] != 3},
+             "fft_path": FFT_PATHS[self.fft_path]}
+        t3 = {int(self.cand[i]): float(self.cand_ms[i]) for i in range(n) if self.cand_ctas[i] == 3}
+        if t3:
+            d["timings_ms_3ctas"] = t3
+        if any(self.fft_ms[i] > 0 for i in range(len(FFT_PATHS))):
+            d["fft_apply_ms"] = {FFT_PATHS[i]: float(self.fft_ms[i]) for i in range(len(FFT_PATHS))
+                                 if self.fft_ms[i] > 0}
+        return d
 
 
 def plan_candidates(n1, n2, nz, precision="fp32"):
-    """Chunk lengths the depth-kernel tuner times on this grid (host computation only)."""
+    """Depth-kernel launch shapes the tuner times on this grid, as (chunk length, CTAs per SM)
+    pairs (host computation only)."""
     buf = (ctypes.c_int * PLAN_MAX_CAND)()
+    ctas = (ctypes.c_int * PLAN_MAX_CAND)()
     prec = FVIM_FP32 if precision == "fp32" else FVIM_FP64
-    n = lib().fvim_plan_candidates(int(n1), int(n2), int(nz), prec, buf, PLAN_MAX_CAND)
+    n = lib().fvim_plan_candidates(int(n1), int(n2), int(nz), prec, buf, ctas, PLAN_MAX_CAND)
     _check(n if n < 0 else 0, "fvim_plan_candidates")
-    return list(buf[:n])
+    return list(zip(buf[:n], ctas[:n]))
 
 
 class FvimError(RuntimeError):
@@ -116,7 +133,7 @@ def lib():
         "fvim_footprint": (ctypes.c_size_t, [i, i, i, i]),
         "fvim_autotune": (i, [vp, i, ctypes.POINTER(Plan)]),
         "fvim_get_plan": (i, [vp, ctypes.POINTER(Plan)]),
-        "fvim_plan_candidates": (i, [i, i, i, i, ctypes.POINTER(i), i]),
+        "fvim_plan_candidates": (i, [i, i, i, i, ctypes.POINTER(i), ctypes.POINTER(i), i]),
         "fvim_set_plan": (i, [vp, ctypes.POINTER(Plan)]),
     }
     for name, (res, args) in sig.items():
@@ -220,8 +237,9 @@ class Context:
         return out
 
     def autotune(self, reps=20):
-        """Time the depth kernel's chunk lengths on this grid (on the current stream) and keep
-        the fastest for this context and later ones of the same grid; returns the plan."""
+        """Time the depth kernel's chunk lengths and then whole applies with each in-plane FFT
+        path built for this grid (on the current stream), and keep the fastest for this
+        context and later ones of the same grid; returns the plan."""
         pl = Plan()
         self._stream()
         _check(lib().fvim_autotune(self._h, int(reps), ctypes.byref(pl)), "fvim_autotune")
@@ -233,10 +251,15 @@ class Context:
         _check(lib().fvim_get_plan(self._h, ctypes.byref(pl)), "fvim_get_plan")
         return pl.as_dict()
 
-    def set_plan(self, depth_chunk=0):
-        """Force the depth chunk length on this context (0: the default rule)."""
+    def set_plan(self, depth_chunk=0, fft_path="rows_cols", depth_ctas=2, depth_cutoff=18.0):
+        """Force the depth chunk length (0: the default rule), the depth kernel's register budget
+        (CTAs per SM: 2, or 3 where built), its chunk-scan cutoff eps_co (0: exact scan) and the
+        in-plane FFT path (one of FFT_PATHS) on this context."""
         pl = Plan()
         pl.depth_chunk = int(depth_chunk)
+        pl.depth_ctas = int(depth_ctas)
+        pl.depth_cutoff = float(depth_cutoff)
+        pl.fft_path = FFT_PATHS.index(fft_path)
         _check(lib().fvim_set_plan(self._h, ctypes.byref(pl)), "fvim_set_plan")
 
     def last_kernel_count(self):

@@ -99,10 +99,17 @@ def test_plan_candidates_follow_the_launch_limits():
     for n, nz, prec in [(512, 64, "fp32"), (512, 32, "fp32"), (64, 8, "fp32"), (128, 28, "fp64"),
                         (32, 300, "fp32"), (32, 300, "fp64"), (4, 2, "fp64")]:
         c = fvim.plan_candidates(n, n, nz, prec)
-        assert max(2, -(-nz // 16)) in c and all(2 <= x <= nz for x in c) and len(set(c)) == len(c)
-    # Nz = 64 in FP32: 2 and 3 nodes per chunk would need 32 and 22 chunk threads per column
-    assert fvim.plan_candidates(512, 512, 64, "fp32") == [4, 6, 8, 12, 16]
-    assert fvim.plan_candidates(64, 64, 8, "fp32") == [2, 3, 4, 6, 8]
+        chunks = [x for x, _ in c]
+        assert (max(2, -(-nz // 16)), 2 if prec == "fp32" and n >= 32 and nz <= 64 else 0) in c
+        assert all(2 <= x <= nz for x in chunks) and len(set(c)) == len(c)
+        # FP64 and deep grids: the shared-memory variant (no register budget); FP32 registers: 2 or 3
+        assert all(k == 0 for _, k in c) if prec == "fp64" else all(k in (0, 2, 3) for _, k in c)
+    # Nz = 64 in FP32: 2 and 3 nodes per chunk would need 32 and 22 chunk threads per column; the
+    # register variant of chunk lengths 4..8 also builds for three CTAs per SM (85 registers)
+    assert fvim.plan_candidates(512, 512, 64, "fp32") == [(4, 2), (6, 2), (8, 2), (12, 0), (16, 0),
+                                                          (4, 3), (6, 3), (8, 3)]
+    assert fvim.plan_candidates(64, 64, 8, "fp32") == [(2, 2), (3, 2), (4, 2), (6, 2), (8, 2),
+                                                       (4, 3), (6, 3), (8, 3)]
     with pytest.raises(fvim.FvimError):
         fvim.plan_candidates(6, 8, 8)
     with pytest.raises(fvim.FvimError):

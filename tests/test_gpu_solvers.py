@@ -2,8 +2,9 @@
 
 The solvers stop at a tolerance, so converged answers are compared with a bound set by
 the two stopping rules (not by rounding): FP64 runs use tight tolerances on both sides;
-FP32 runs use the FP32 defaults and the bars of the FP32 path (2e-5 on stresses where the
-solver tolerance allows it, 1e-4 on the contact area).
+FP32 runs use the FP32 defaults and the bars of the FP32 path (2e-5 on the pressure and the
+plastic strain where the solver tolerance allows it, 1e-4 on the contact area: on the 32 x 32
+golden grids one node is 9.8e-4 of the area, so the areas are equal).
 """
 import os
 
@@ -51,7 +52,8 @@ def test_elastic_contact_parity(prec, n):
         assert rel_l2(got, ref) < 1e-9
         assert area == area_ref
     else:
-        assert rel_l2(got, ref) < 1e-4
+        print("elastic contact FP32 %d^2: p %.2e area %g vs %g" % (n, rel_l2(got, ref), area, area_ref))
+        assert rel_l2(got, ref) < 2e-5
         assert abs(area - area_ref) <= 1e-4
 
 
@@ -64,19 +66,22 @@ def test_plasticity_parity(prec):
     sy, Eh = 0.05 * ES, 0.1
     dT, _ = C.polonsky_keer(h, 3.0e-3, 1.0, 1.0, E, NU, tol=1e-13)
     st = C.PlasticState(nz, n, n)
-    dE_ref, dep_ref, dEp_ref, info = C.plasticity_solve(dT, st, z, 1.0, 1.0, E, NU, sy, Eh, tol_rel=1e-12)
+    # both sides solve to a residual of 1e-14 relative (FP64): the fixed points agree to 1e-10
+    dE_ref, dep_ref, dEp_ref, info = C.plasticity_solve(dT, st, z, 1.0, 1.0, E, NU, sy, Eh, tol_rel=1e-14)
     assert dEp_ref.max() > 0
     ctx = _ctx(n, z, prec, sigma_y=sy, E_h=Eh)
     dt = ctx.dtype
     dE = torch.empty(ctx.vol_shape, dtype=dt, device="cuda")
     dep = torch.empty(ctx.vol_shape, dtype=dt, device="cuda")
     dEp = torch.empty(ctx.scal_shape, dtype=dt, device="cuda")
-    opts = ctx.default_opts(df_tol_rel=1e-12) if prec == "fp64" else ctx.default_opts()
+    opts = ctx.default_opts(df_tol_rel=1e-14) if prec == "fp64" else ctx.default_opts()
     it, res = ctx.plasticity_solve(to_dev(torch, dT, dt), dE, dep, dEp, opts)
-    tol = 1e-8 if prec == "fp64" else 1e-4
-    assert rel_l2(dE.cpu().numpy(), dE_ref) < tol
-    assert rel_l2(dep.cpu().numpy(), dep_ref) < 10 * tol
-    assert rel_l2(dEp.cpu().numpy(), dEp_ref) < 10 * tol
+    e = [rel_l2(dE.cpu().numpy(), dE_ref), rel_l2(dep.cpu().numpy(), dep_ref), rel_l2(dEp.cpu().numpy(), dEp_ref)]
+    print("plasticity %s vs oracle: dE %.2e deps_p %.2e de_p %.2e" % (prec, *e))
+    tol = 1e-10 if prec == "fp64" else 2e-5
+    assert e[0] < tol
+    assert e[1] < 10 * tol
+    assert e[2] < 10 * tol
 
 
 def _golden_run(prec, **opt_kw):
@@ -99,22 +104,30 @@ def _golden_run(prec, **opt_kw):
 
 def test_solve_contact_fp64_matches_oracle_hertz():
     """The plain FP64 elastic-plastic Hertz case (32 x 32 x 16, five increments to the load
-    of an elastic peak pressure of 3 sigma_y): Algorithm 1 on the GPU against the oracle."""
-    g, rep, p, epp, ep = _golden_run("fp64", cg_tol=1e-13, df_tol_rel=1e-11, max_iter=200)
+    of an elastic peak pressure of 3 sigma_y): Algorithm 1 on the GPU against the oracle, both
+    converged to e < 1e-12, at the FP64 bar of 1e-10."""
+    g, rep, p, epp, ep = _golden_run("fp64", tol=1e-12, cg_tol=1e-14, df_tol_rel=1e-13, max_iter=600)
+    print("hertz FP64 vs oracle: p %.2e e_p %.2e eps_p %.2e" % (
+        rel_l2(p, g["p"]), rel_l2(ep, g["e_p"]), rel_l2(epp, g["eps_p"])))
     assert rep["status"] == 0 and rep["n_increments"] == 5
     assert rep["load_error"] < 1e-12
-    assert rel_l2(p, g["p"]) < 1e-7
-    assert rel_l2(ep, g["e_p"]) < 1e-6
-    assert rel_l2(epp, g["eps_p"]) < 1e-6
+    assert rel_l2(p, g["p"]) < 1e-10
+    assert rel_l2(ep, g["e_p"]) < 1e-10
+    assert rel_l2(epp, g["eps_p"]) < 1e-10
     assert np.array_equal(np.array(rep["contact_area"]), g["areas"])
 
 
 def test_solve_contact_fp32_matches_oracle_hertz():
+    """The FP32 path (FP32 defaults: Algorithm-1 tolerance 1e-8) at the FP32 bars: 2e-5 on the
+    pressure and the cumulated plastic strain, 1e-4 on the contact area (on 32 x 32, equal
+    areas)."""
     g, rep, p, epp, ep = _golden_run("fp32", max_iter=200)
+    print("hertz FP32 vs oracle: p %.2e e_p %.2e areas %s vs %s" % (
+        rel_l2(p, g["p"]), rel_l2(ep, g["e_p"]), rep["contact_area"], list(g["areas"])))
     assert rep["status"] == 0
     assert rel_l2(p, g["p"]) < 2e-5
     assert rel_l2(ep, g["e_p"]) < 2e-5
-    assert np.abs(np.array(rep["contact_area"]) - g["areas"]).max() <= 1e-4 + 1.0 / 1024
+    assert np.abs(np.array(rep["contact_area"]) - g["areas"]).max() <= 1e-4
 
 
 EPP = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "epp_hertz_32x32x8.npz")
@@ -139,10 +152,13 @@ def test_solve_contact_perfectly_plastic_sweep(prec):
     ctx.get_state(None, ep, None)
     torch.cuda.synchronize()
     assert rep["status"] == 0 and rep["n_increments"] == 3
-    tol = 1e-7 if prec == "fp64" else 2e-5
-    assert rel_l2(p.cpu().numpy(), g["p"]) < tol
-    assert rel_l2(ep.cpu().numpy(), g["e_p"]) < (1e-6 if prec == "fp64" else 1e-4)
-    assert np.abs(np.array(rep["contact_area"]) - g["areas"]).max() <= (0 if prec == "fp64" else 1.0 / 1024)
+    pn, epn = p.cpu().numpy(), ep.cpu().numpy()
+    print("epp %s vs oracle: p %.2e e_p %.2e areas %s vs %s" % (
+        prec, rel_l2(pn, g["p"]), rel_l2(epn, g["e_p"]), rep["contact_area"], list(g["areas"])))
+    tol = 1e-10 if prec == "fp64" else 2e-5
+    assert rel_l2(pn, g["p"]) < tol
+    assert rel_l2(epn, g["e_p"]) < (1e-10 if prec == "fp64" else 1e-4)
+    assert np.abs(np.array(rep["contact_area"]) - g["areas"]).max() <= (0 if prec == "fp64" else 1e-4)
 
 
 ROUGH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rough_32x32x8.npz")
@@ -173,10 +189,12 @@ def _rough_run(prec, **opt_kw):
 
 def test_rough_solve_fp64_matches_oracle():
     g, rep, p, epp, ep = _rough_run("fp64", cg_tol=1e-13, df_tol_rel=1e-11, max_iter=200)
+    print("rough FP64 vs oracle: p %.2e e_p %.2e eps_p %.2e" % (
+        rel_l2(p, g["p"]), rel_l2(ep, g["e_p"]), rel_l2(epp, g["eps_p"])))
     assert rep["status"] == 0 and rep["n_increments"] == 2
-    assert rel_l2(p, g["p"]) < 1e-7
-    assert rel_l2(ep, g["e_p"]) < 1e-6
-    assert rel_l2(epp, g["eps_p"]) < 1e-6
+    assert rel_l2(p, g["p"]) < 1e-10
+    assert rel_l2(ep, g["e_p"]) < 1e-10
+    assert rel_l2(epp, g["eps_p"]) < 1e-10
     assert np.array_equal(np.array(rep["contact_area"]), g["areas"])
 
 
@@ -187,7 +205,7 @@ def test_rough_solve_fp32_matches_oracle():
     assert rep["status"] == 0
     assert rel_l2(p, g["p"]) < 2e-5
     assert rel_l2(ep, g["e_p"]) < 2e-5
-    assert np.abs(np.array(rep["contact_area"]) - g["areas"]).max() <= 1e-4 + 1.0 / 1024
+    assert np.abs(np.array(rep["contact_area"]) - g["areas"]).max() <= 1e-4
 
 
 def test_solve_contact_deterministic_and_caps():
