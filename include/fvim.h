@@ -136,7 +136,10 @@ int fvim_reset_state(fvim_ctx* ctx);
  * solvers have run (scratch, plastic state and solver workspace); host computation only. */
 size_t fvim_footprint(int n1, int n2, int nz, int precision);
 
-/* fvim_sync -- wait for the context's stream; returns FVIM_ERR_CUDA on a device error. */
+/* fvim_sync -- wait for the context's stream; returns FVIM_ERR_CUDA on a device error and
+ * FVIM_ERR_TIMEOUT (once; the status is then cleared) when a bounded wait inside a kernel
+ * launched since the last fvim_sync expired (the kernel returned without its output: the
+ * results of those calls are invalid). */
 int fvim_sync(fvim_ctx* ctx);
 
 /* fvim_destroy -- free the context and its scratch (synchronises its stream). */

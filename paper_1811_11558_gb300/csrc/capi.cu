@@ -8,6 +8,8 @@
 #include <utility>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "fvim_internal.cuh"
 
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
@@ -127,10 +129,13 @@ size_t nvox(const fvim_ctx* c) { return (size_t)c->nz * c->n2 * c->n1; }
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 void free_all(fvim_ctx* c) {
-  void* bufs[] = {c->z_dev, c->tw1, c->tw2, c->spec, c->nq, c->surf, c->surf_nq, c->st_eps_p, c->st_ep, c->st_sig, c->st_T};
+  void* bufs[] = {c->z_dev, c->tw1, c->tw2, c->spec, c->nq, c->surf, c->surf_nq, c->st_eps_p, c->st_ep, c->st_sig, c->st_T,
+                  c->dev_status};
   for (void* b : bufs)
     if (b) cudaFree(b);
   free(c->z_host);
+  free(c->tmap);
+  c->tmap = nullptr;
   for (int i = 0; i < FVIM_NSOLVER_BUFS; ++i)
     if (c->sv[i]) { cudaFree(c->sv[i]); c->sv[i] = nullptr; }
   solver_release(c);
@@ -161,6 +166,48 @@ template <typename T> int upload_nodes(fvim_ctx* c) {
   if (FVIM_CU(cudaMalloc(&c->z_dev, c->nz * sizeof(T)))) return FVIM_ERR_OOM;
   if (FVIM_CU(cudaMemcpy(c->z_dev, h.data(), c->nz * sizeof(T), cudaMemcpyHostToDevice))) return FVIM_ERR_CUDA;
   return FVIM_OK;
+}
+
+// the driver's tensor-map encoder, looked up once through the runtime (no driver library link)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 f = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return f;
+}
+
+// Tensor map of the FP32 depth tile: the spectrum [Nz 6][N2][N1/2] complex seen as a 3-D float
+// tensor (2 h1, N2, 6 Nz) with a box of 32 floats (16 complex columns, one 128-byte row) x one
+// k2 x B rows, B the largest divisor of 6 Nz up to 256.  FVIM_DEPTH_TMA=0 keeps cp.async.
+void setup_depth_tma(fvim_ctx* c) {
+  const char* e = getenv("FVIM_DEPTH_TMA");
+  if ((e && e[0] == '0') || c->prec != FVIM_FP32 || c->gen || c->h1 < 16) return;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return;
+  const int rows = c->nz * 6;
+  int box_rows = rows < 256 ? rows : 256;
+  while (rows % box_rows) --box_rows;
+  void* m = aligned_alloc(64, sizeof(CUtensorMap));
+  if (!m) return;
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * c->h1, (cuuint64_t)c->n2, (cuuint64_t)rows};
+  const cuuint64_t strides[2] = {(cuuint64_t)c->h1 * 8, (cuuint64_t)c->n2 * c->h1 * 8};
+  const cuuint32_t box[3] = {32, 1, (cuuint32_t)box_rows};
+  const cuuint32_t elem[3] = {1, 1, 1};
+  if (enc(reinterpret_cast<CUtensorMap*>(m), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->spec, dims, strides, box, elem,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+    free(m);
+    return;
+  }
+  c->tmap = m;
+  c->tma_rows = box_rows;
 }
 
 }  // namespace
@@ -516,6 +563,9 @@ int fvim_create(fvim_ctx** out, int n1, int n2, int nz, const double* z_nodes, d
     if (FVIM_CU(cudaMalloc(a.p, a.bytes))) { cudaGetLastError(); free_all(c); delete c; return FVIM_ERR_OOM; }
     if (FVIM_CU(cudaMemset(*a.p, 0, a.bytes))) { free_all(c); delete c; return FVIM_ERR_CUDA; }
   }
+  if (FVIM_CU(cudaMalloc((void**)&c->dev_status, 16))) { cudaGetLastError(); free_all(c); delete c; return FVIM_ERR_OOM; }
+  if (FVIM_CU(cudaMemset(c->dev_status, 0, 16))) { free_all(c); delete c; return FVIM_ERR_CUDA; }
+  setup_depth_tma(c);
   // the fills above run on the legacy stream; wait for them without touching other streams
   // (another thread may be capturing a graph on its own non-blocking stream)
   if (FVIM_CU(cudaStreamSynchronize(cudaStreamLegacy))) { free_all(c); delete c; return FVIM_ERR_CUDA; }
@@ -616,7 +666,18 @@ size_t fvim_footprint(int n1, int n2, int nz, int precision) {
 
 int fvim_sync(fvim_ctx* c) {
   if (!c) return FVIM_ERR_ARG;
-  return FVIM_CU(cudaStreamSynchronize(c->stream)) ? FVIM_ERR_CUDA : FVIM_OK;
+  if (FVIM_CU(cudaStreamSynchronize(c->stream))) return FVIM_ERR_CUDA;
+  if (c->dev_status) {
+    int st = 0;
+    if (FVIM_CU(cudaMemcpyAsync(&st, c->dev_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) ||
+        FVIM_CU(cudaStreamSynchronize(c->stream)))
+      return FVIM_ERR_CUDA;
+    if (st) {
+      if (FVIM_CU(cudaMemsetAsync(c->dev_status, 0, sizeof(int), c->stream))) return FVIM_ERR_CUDA;
+      return FVIM_ERR_TIMEOUT;
+    }
+  }
+  return FVIM_OK;
 }
 
 int fvim_destroy(fvim_ctx* c) {

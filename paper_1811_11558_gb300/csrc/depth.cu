@@ -28,6 +28,8 @@
 //   closed form exp(-q z)(P + q z Q) in the rotated frame.
 // * q = 0 (mode k = 0): laminate solution (sigma_i3 = 0, eps_ab = 0).  k2 = N2/2
 //   (not in Z^2_N): no operator term, so sigma_hat = -w_hat (stress) or 0 (strain).
+#include <string.h>
+
 #include "fvim_internal.cuh"
 
 namespace {
@@ -565,15 +567,20 @@ __global__ void __launch_bounds__(256, MB) k_mindlin_depth_r(typename Cx<T>::t* 
                                                             typename Cx<T>::t* __restrict__ surf,
                                                             const T* __restrict__ zn, int nz, int n1, int n2, int hs, int h1, int nch,
                                                             T w1, T w2, T lam, T mu, T nu, int out_kind, int want_u3,
-                                                            int uniform, T hz, const int* __restrict__ zr, T cut) {
+                                                            int uniform, T hz, const int* __restrict__ zr, T cut,
+                                                            const __grid_constant__ CUtensorMap tmap, int tma_rows,
+                                                            int* __restrict__ status) {
   typedef typename Cx<T>::t V;
   static_assert(sizeof(V) == 8 && KT % 2 == 0, "FP32 tiles of an even width");
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];  // tensor-copy boxes land at 128-byte offsets
   V* W = reinterpret_cast<V*>(smraw);                               // [nz][6][KT]
   Mom<V>* SA = reinterpret_cast<Mom<V>*>(W + (size_t)nz * 6 * KT);  // [nch][KT]
   Mom<V>* SP = SA + (size_t)nch * KT;                               // [nch][KT]
   V* TR = reinterpret_cast<V*>(SP + (size_t)nch * KT);              // [KT][3] image traction
   T* zs = reinterpret_cast<T*>(TR + 3 * KT);                        // [nz]
+  // mbarrier of the tensor copies, 8-byte aligned after the depth nodes
+  unsigned long long* tbar = reinterpret_cast<unsigned long long*>(
+      reinterpret_cast<unsigned char*>(zs) + (((size_t)nz * sizeof(T) + 7) & ~(size_t)7));
   const int kt = threadIdx.x & (KT - 1);
   const int ch = threadIdx.x / KT;
   const int k1 = blockIdx.x * KT + kt;
@@ -581,9 +588,61 @@ __global__ void __launch_bounds__(256, MB) k_mindlin_depth_r(typename Cx<T>::t* 
   const size_t plane = (size_t)n2 * h1;
   const size_t colofs = (size_t)k2 * h1 + blockIdx.x * KT;
 
-  // 1. load the tile (16-byte copies, two FP32 complex values each) and the depth nodes
-  // (layers outside zr hold no input: their spectrum was not computed and reads as zero)
-  if (!zr) {
+  // 1. load the tile and the depth nodes (layers outside zr hold no input: their spectrum was
+  //    not computed and reads as zero).  With a tensor map (tma_rows > 0): one thread issues
+  //    tensor copies of tma_rows x KT complex boxes (rows z c, one k2, KT columns) that complete
+  //    on an mbarrier; the wait is bounded, and a copy that never completes sets the status word
+  //    and every thread of the CTA returns after a second bounded wait.  Otherwise 16-byte
+  //    cp.async copies by all threads.
+  if (tma_rows > 0) {
+    const unsigned bar = (unsigned)__cvta_generic_to_shared(tbar);
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned bytes = (unsigned)(nz * 6 * KT * sizeof(V));
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+      const int x = (int)(blockIdx.x * KT * 2);  // first k1 column, in floats (16-byte multiple)
+      for (int r0 = 0; r0 < nz * 6; r0 += tma_rows) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(W + (size_t)r0 * KT);
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+            "[%5];" ::"r"(dst),
+            "l"(reinterpret_cast<unsigned long long>(&tmap)), "r"(x), "r"(k2), "r"(r0), "r"(bar)
+            : "memory");
+      }
+    }
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];
+    bool done = false;
+    for (int it = 0; it < (1 << 22) && !done; ++it) {
+      unsigned ok;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(ok) : "r"(bar) : "memory");
+      done = ok != 0;
+    }
+    if (__syncthreads_or(!done)) {
+      if (threadIdx.x == 0 && status) atomicOr(status, 1);
+      for (int it = 0; it < (1 << 22) && !done; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok) : "r"(bar) : "memory");
+        done = ok != 0;
+      }
+      return;
+    }
+    if (zr) {
+      const int zlo = zr[0], zhi = zr[1];
+      for (int idx = threadIdx.x; idx < nz * 6 * KT; idx += blockDim.x) {
+        const int zl = idx / (6 * KT);
+        if (zl < zlo || zl >= zhi) W[idx] = mk<V>(0, 0);
+      }
+    }
+    __syncthreads();
+  } else if (!zr) {
     for (int idx = threadIdx.x; idx < nz * 6 * (KT / 2); idx += blockDim.x) {
       const int zc = idx / (KT / 2), j = 2 * (idx % (KT / 2));
       cp_async_16(W + zc * KT + j, spec + (size_t)zc * plane + colofs + j);
@@ -601,9 +660,11 @@ __global__ void __launch_bounds__(256, MB) k_mindlin_depth_r(typename Cx<T>::t* 
       }
     }
   }
-  for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];
-  cp_async_wait_all();
-  __syncthreads();
+  if (tma_rows <= 0) {
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];
+    cp_async_wait_all();
+    __syncthreads();
+  }
 
   const ModeGeom<T> g = mode_geom<T>(k1, k2, n1, n2, hs, w1, w2);
   const bool special = g.zero || g.nyq;
@@ -927,7 +988,7 @@ template <typename T> DepthCfg<T> depth_cfg(const fvim_ctx* c, int C, int ctas) 
       const int CR = C <= 2 ? 2 : (C <= 3 ? 3 : (C <= 4 ? 4 : (C <= 6 ? 6 : 8)));
       const int nchr = (nz + CR - 1) / CR;
       const size_t smr = (size_t)nz * 6 * 16 * sizeof(V) + (size_t)(2 * nchr) * 16 * sizeof(Mom<V>) +
-                         (size_t)3 * 16 * sizeof(V) + (size_t)nz * sizeof(T);
+                         (size_t)3 * 16 * sizeof(V) + (((size_t)nz * sizeof(T) + 7) & ~(size_t)7) + 16;
       if (smr <= 227 * 1024 && 16 * nchr <= 256) {
         // three CTAs per SM (85 registers): chunk lengths 4..8 whose tile fits three times
         if (ctas == 3 && !(CR >= 4 && 3 * (smr + 1024) <= 228 * 1024)) return d;
@@ -978,13 +1039,22 @@ int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps
   dim3 grid(h1 / KT, n2);
   const T w1 = (T)(kTwoPi / c->L1), w2 = (T)(kTwoPi / c->L2);
   if constexpr (sizeof(T) == 4) if (d.reg) {
+    // tensor-map copies of the tile where the context has its map (rows per box divide 6 Nz)
+    CUtensorMap tm;
+    int tma_rows = 0;
+    if (c->tmap && c->tma_rows > 0) {
+      tm = *reinterpret_cast<const CUtensorMap*>(c->tmap);
+      tma_rows = c->tma_rows;
+    } else {
+      memset(&tm, 0, sizeof(tm));
+    }
 #define DEPTHR(CV, EI, MBV)                                                                                     \
   if (C == CV && eps_in == EI && d.mb == MBV) {                                                                 \
     smem_cap(k_mindlin_depth_r<T, 16, CV, EI, MBV>);                                                            \
     k_mindlin_depth_r<T, 16, CV, EI, MBV><<<grid, d.threads, d.smem, c->stream>>>(                              \
         (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, c->n1, n2, c->hs, h1, nch, w1, w2, (T)c->lam, (T)c->mu, \
         (T)c->nu,                                                                                              \
-        out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz, zr, (T)c->depth_cut);                                  \
+        out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz, zr, (T)c->depth_cut, tm, tma_rows, c->dev_status);     \
   }
     DEPTHR(2, false, 2) DEPTHR(3, false, 2) DEPTHR(4, false, 2) DEPTHR(6, false, 2) DEPTHR(8, false, 2)
     DEPTHR(2, true, 2) DEPTHR(3, true, 2) DEPTHR(4, true, 2) DEPTHR(6, true, 2) DEPTHR(8, true, 2)

@@ -2,6 +2,7 @@
 // Not part of the public ABI (see include/fvim.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -458,6 +459,9 @@ struct fvim_ctx {
   int plan_tuned;  // depth_chunk came from a timing run (fvim_autotune) in this process
   int depth_ctas;  // CTAs per SM of the FP32 register depth kernel: 0 or 2 (128 registers), 3 (85)
   float depth_cut; // chunk-scan cutoff eps_co of the FP32 register depth kernel (0: exact scan)
+  void* tmap;      // CUtensorMap (host, 64-byte aligned) over the spectrum for the depth tile, or NULL
+  int tma_rows;    // rows (z, component) per tensor-copy box of the depth tile; 0: no tensor copies
+  int* dev_status; // device status word: bit 0 set by a bounded device wait that expired
   int fft2_fused;  // one-pass 2-D FFTs through L2: -1 not yet known, 0 not used, 1 used
   int fft_path;    // in-plane FFT path chosen by the tuner or fvim_set_plan (FVIM_FFT_*), -1: none
                    // (the row / column kernels unless an environment variable selects another)

@@ -68,7 +68,8 @@ def test_set_plan_rejects_unlaunchable_chunks():
             ctx.set_plan(C)
         assert e.value.status == -1
     ctx.set_plan(4)
-    assert ctx.plan == {"depth_chunk": 4, "depth_ctas": 2, "tuned": False, "timings_ms": {}, "fft_path": "rows_cols"}
+    assert ctx.plan == {"depth_chunk": 4, "depth_ctas": 2, "depth_cutoff": 18.0, "tuned": False, "timings_ms": {},
+                        "fft_path": "rows_cols"}
     ctx.set_plan(4, depth_ctas=3)
     assert ctx.plan["depth_ctas"] == 3
     with pytest.raises(FvimError) as e:
@@ -102,8 +103,8 @@ def test_autotune_keeps_the_fastest_per_grid():
     assert ctx.plan["depth_chunk"] == pl["depth_chunk"] and ctx.plan["depth_ctas"] == pl["depth_ctas"]
     # a later context of the same grid starts with the tuned plan; another grid does not
     same = Context(128, 64, z, precision="fp32")
-    assert same.plan == {"depth_chunk": pl["depth_chunk"], "depth_ctas": pl["depth_ctas"], "tuned": True,
-                         "timings_ms": {}, "fft_path": "rows_cols"}
+    assert same.plan == {"depth_chunk": pl["depth_chunk"], "depth_ctas": pl["depth_ctas"], "depth_cutoff": 18.0,
+                         "tuned": True, "timings_ms": {}, "fft_path": "rows_cols"}
     assert "fft_apply_ms" not in pl      # only the row / column path is built for a 64-point side
     other = Context(128, 64, z, precision="fp64")
     assert not other.plan["tuned"]
