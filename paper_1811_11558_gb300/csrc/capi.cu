@@ -208,6 +208,11 @@ void setup_depth_tma(fvim_ctx* c) {
   }
   c->tmap = m;
   c->tma_rows = box_rows;
+  // test of the expired-wait path: the tile's copies complete, but the mbarrier expects more
+  // bytes than they carry, so its phase never completes and the bounded wait runs out
+  const char* x = getenv("FVIM_TEST_TMA_EXTRA");
+  c->tma_test_extra = x ? atoi(x) : 0;
+  if (c->tma_test_extra < 0 || c->tma_test_extra > 4096 || c->tma_test_extra % 16) c->tma_test_extra = 0;
 }
 
 }  // namespace

@@ -41,6 +41,26 @@ template <typename T> __device__ __forceinline__ T dexp(T x);
 template <> __device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
 template <> __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
 
+// wait for phase 0 of the mbarrier at shared address bar, at most limit_ns nanoseconds of the
+// global timer and at most 2^24 polls (should the timer not advance); true when the phase
+// completed
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned long long limit_ns) {
+  unsigned long long t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (int it = 0; it < (1 << 24); ++it) {
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(bar)
+                 : "memory");
+    if (ok) return true;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > limit_ns) return false;
+  }
+  return false;
+}
+
 // Linear-element integrals of Eq. (int_g0)/(int_g1): with a = q h,
 //   I_n(a) = int_0^1 s^n exp(-a s) ds,  n = 0, 1, 2,
 // closed form for a above a threshold, Taylor series below it (no cancellation).
@@ -569,7 +589,7 @@ __global__ void __launch_bounds__(256, MB) k_mindlin_depth_r(typename Cx<T>::t* 
                                                             T w1, T w2, T lam, T mu, T nu, int out_kind, int want_u3,
                                                             int uniform, T hz, const int* __restrict__ zr, T cut,
                                                             const __grid_constant__ CUtensorMap tmap, int tma_rows,
-                                                            int* __restrict__ status) {
+                                                            int tx_extra, int* __restrict__ status) {
   typedef typename Cx<T>::t V;
   static_assert(sizeof(V) == 8 && KT % 2 == 0, "FP32 tiles of an even width");
   extern __shared__ __align__(128) unsigned char smraw[];  // tensor-copy boxes land at 128-byte offsets
@@ -602,7 +622,7 @@ __global__ void __launch_bounds__(256, MB) k_mindlin_depth_r(typename Cx<T>::t* 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      const unsigned bytes = (unsigned)(nz * 6 * KT * sizeof(V));
+      const unsigned bytes = (unsigned)(nz * 6 * KT * sizeof(V) + tx_extra);
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
       const int x = (int)(blockIdx.x * KT * 2);  // first k1 column, in floats (16-byte multiple)
       for (int r0 = 0; r0 < nz * 6; r0 += tma_rows) {
@@ -615,23 +635,10 @@ __global__ void __launch_bounds__(256, MB) k_mindlin_depth_r(typename Cx<T>::t* 
       }
     }
     for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];
-    bool done = false;
-    for (int it = 0; it < (1 << 22) && !done; ++it) {
-      unsigned ok;
-      asm volatile(
-          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
-          : "=r"(ok) : "r"(bar) : "memory");
-      done = ok != 0;
-    }
+    bool done = mbar_wait_bounded(bar, 1000000000ull);   // 1 s
     if (__syncthreads_or(!done)) {
       if (threadIdx.x == 0 && status) atomicOr(status, 1);
-      for (int it = 0; it < (1 << 22) && !done; ++it) {
-        unsigned ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(ok) : "r"(bar) : "memory");
-        done = ok != 0;
-      }
+      if (!done) mbar_wait_bounded(bar, 1000000000ull);  // the copies of this CTA, once more
       return;
     }
     if (zr) {
@@ -1054,7 +1061,8 @@ int launch_mindlin_depth(const fvim_ctx* c, int out_kind, bool want_u3, bool eps
     k_mindlin_depth_r<T, 16, CV, EI, MBV><<<grid, d.threads, d.smem, c->stream>>>(                              \
         (V*)c->spec, (V*)c->surf, (const T*)c->z_dev, nz, c->n1, n2, c->hs, h1, nch, w1, w2, (T)c->lam, (T)c->mu, \
         (T)c->nu,                                                                                              \
-        out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz, zr, (T)c->depth_cut, tm, tma_rows, c->dev_status);     \
+        out_kind, want_u3 ? 1 : 0, c->uniform, (T)c->hz, zr, (T)c->depth_cut, tm, tma_rows, c->tma_test_extra,  \
+        c->dev_status);                                                                                          \
   }
     DEPTHR(2, false, 2) DEPTHR(3, false, 2) DEPTHR(4, false, 2) DEPTHR(6, false, 2) DEPTHR(8, false, 2)
     DEPTHR(2, true, 2) DEPTHR(3, true, 2) DEPTHR(4, true, 2) DEPTHR(6, true, 2) DEPTHR(8, true, 2)

@@ -462,6 +462,8 @@ struct fvim_ctx {
   void* tmap;      // CUtensorMap (host, 64-byte aligned) over the spectrum for the depth tile, or NULL
   int tma_rows;    // rows (z, component) per tensor-copy box of the depth tile; 0: no tensor copies
   int* dev_status; // device status word: bit 0 set by a bounded device wait that expired
+  int tma_test_extra;  // bytes added to the depth tile's expected copy count (tests of the
+                       // expired-wait path only; FVIM_TEST_TMA_EXTRA at creation, else 0)
   int fft2_fused;  // one-pass 2-D FFTs through L2: -1 not yet known, 0 not used, 1 used
   int fft_path;    // in-plane FFT path chosen by the tuner or fvim_set_plan (FVIM_FFT_*), -1: none
                    // (the row / column kernels unless an environment variable selects another)

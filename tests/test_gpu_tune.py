@@ -232,3 +232,31 @@ def test_chunk_scan_cutoff_error_study():
     for eps in (0.0, 12.0, 18.0):
         assert err[eps] < TOL["fp32"], eps
     ctx.close()
+
+
+def test_depth_tile_wait_expires_and_the_context_stays_usable(monkeypatch):
+    """The depth kernel's tensor-copy wait is bounded: a context created with a test offset on
+    the expected copy bytes (the copies complete, the barrier never does) makes every CTA give up
+    after its time limit and set the status word; fvim_sync reports FVIM_ERR_TIMEOUT once, and
+    the device and a fresh context compute the operator afterwards.  No copy is left in flight."""
+    torch = require_gpu()
+    from paper_1811_11558_gb300 import Context, FvimError
+
+    n, z = 32, inputs.uniform_depth(8, 0.2)        # one wave of 32 CTAs: about 2 s of waiting
+    ep = inputs.plastic_strain_field(n, n, z, seed=1834)
+    d = to_dev(torch, ep, torch.float32)
+    monkeypatch.setenv("FVIM_TEST_TMA_EXTRA", "16")
+    bad = Context(n, n, z, 1.0, 1.0, precision="fp32", E=E, nu=NU)
+    monkeypatch.delenv("FVIM_TEST_TMA_EXTRA")
+    bad.apply_mindlin(d)
+    with pytest.raises(FvimError) as e:
+        bad.sync()
+    assert e.value.status == -6
+    bad.sync()                                     # the status was reported once and cleared
+    ref = op.mindlin_apply(ep, z, 1.0, 1.0, E, NU, "stress")
+    good = Context(n, n, z, 1.0, 1.0, precision="fp32", E=E, nu=NU)
+    out = good.apply_mindlin(d)
+    good.sync()
+    assert rel_l2(out.cpu().numpy(), ref) < TOL["fp32"]
+    for c in (bad, good):
+        c.close()
