@@ -385,10 +385,11 @@ def rough_metrics(n=1024, nz=32, depth=0.05, seed=1813, n_inc=10, cap=120):
     """Algorithm 1 on a rough surface, FP32: seeded self-affine surface n x n (H = 0.8, flat PSD
     for 4 <= |k| < 8, power law to k_s = 64, rms slope 0.1), nz uniform nodes to the given
     depth, sigma_y = 0.05 E*, E_h = 0.1 E, relaxation 0.3.  (a) the paper's rough-surface load
-    W = 1e-3 E x rms slope in five increments; (b) the load of a 10 % elastic contact fraction,
-    ramped in n_inc equal increments (the paper's remedy for the coupling's slow convergence
-    on rough surfaces: small load steps), Algorithm 1 capped at ``cap`` iterations per
-    increment.  Both are timed as whole solves; the status says whether every increment
+    W = 1e-3 E x rms slope in five increments (Algorithm 1 in the listing's order, tolerance
+    1e-6); (b) the load of a 10 % elastic contact fraction, ramped in n_inc equal increments (the
+    paper's remedy for the coupling's slow convergence on rough surfaces: small load steps),
+    Algorithm 1 with the relaxed value carried between iterations (relax_mode 1), tolerance 1e-7,
+    capped at ``cap`` iterations per increment.  Both are timed as whole solves; the status says whether every increment
     reached the tolerance."""
     import torch
 
@@ -419,16 +420,20 @@ def rough_metrics(n=1024, nz=32, depth=0.05, seed=1813, n_inc=10, cap=120):
     p.zero_()
     ctx.elastic_contact(hd, 5e-3, p, ctx.default_opts())
     W10 = 5e-3 * 0.1 / float((p > 0).double().mean())
+    # with the listing's update order the coupling stalls near 1e-5..1e-3 on this load in FP32
+    # and FP64 alike; the relaxed value carried between iterations converges in ~21 per increment
+    opts10 = ctx.default_opts(relax=0.3, max_iter=cap, tol=1e-7, relax_mode=1)
     ctx.reset_state()
     p.zero_()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    rep = ctx.solve_contact(hd, [W10 * (k + 1) / n_inc for k in range(n_inc)], p, opts, allow_not_converged=True)
+    rep = ctx.solve_contact(hd, [W10 * (k + 1) / n_inc for k in range(n_inc)], p, opts10, allow_not_converged=True)
     t = time.perf_counter() - t0
     its = sum(rep["alg1_iters"])
-    out["area_10pct"] = {"W": W10, "increments": n_inc, "relax": 0.3, "tol": opts.tol, "alg1_cap": cap,
+    out["area_10pct"] = {"W": W10, "increments": n_inc, "relax": 0.3, "relax_mode": "carried", "tol": opts10.tol,
+                         "alg1_cap": cap,
                          "status": rep["status"], "converged_increments": sum(
-                             1 for e in rep["alg1_error"] if e < opts.tol),
+                             1 for e in rep["alg1_error"] if e < opts10.tol),
                          "solves_per_s": 1.0 / t, "ms_per_solve": 1e3 * t, "ms_per_alg1_iter": 1e3 * t / its,
                          "alg1_iters": rep["alg1_iters"], "alg1_error": rep["alg1_error"],
                          "contact_area": rep["contact_area"][-1]}
@@ -443,14 +448,15 @@ def epp_loads():
     return sorted(set(np.round(np.linspace(0.9, 15.5, 20), 12).tolist()) | {1.0, 2.1, 6.4, 15.5})
 
 
-def epp_metrics(n=81, nz=32, a_y_over_L=0.05, relax=0.5, cap=120, n64=4):
+def epp_metrics(n=81, nz=32, a_y_over_L=0.05, relax=0.5, cap=200, n64=4):
     """Elastic-perfectly-plastic Hertz load sweep at the paper's discretisation (App. C.2): cell
     [0, 20 R / 3]^2 x [0, 10 R / 3] with L = 1 (R = 0.15, depth 0.5), N = (81, 81, 32), nu = 0.3,
     E_h = 0, W / W_y over epp_loads() one increment each (the state carries over), relaxation
     0.5.  The paper leaves sigma_y free (normalised results do not depend on it); here it is set
     so that the onset contact radius a_y = pi R p_y / (2 E*) (p_y = 1.6 sigma_y) is a_y_over_L
-    of the cell.  The whole sweep runs in FP32 (default tolerances: Algorithm 1 to 1e-8); plain
-    FP64 (Algorithm 1 to 1e-9, the paper's tolerance) runs the first n64 loads, and the two
+    of the cell.  The whole sweep runs in FP32 (Algorithm 1 to 1e-7: with E_h = 0 the FP32 coupling
+    error stalls between 1e-8 and 1e-6 on the heavier loads); plain FP64 (Algorithm 1 to 1e-9,
+    the paper's tolerance) runs the first n64 loads, and the two
     pressures and contact areas are compared after that load.  Reports per load the peak
     pressure over sigma_y, the contact radius over a_y (from the contact area), the peak
     plastic strain and the coupling iterations."""
@@ -475,7 +481,7 @@ def epp_metrics(n=81, nz=32, a_y_over_L=0.05, relax=0.5, cap=120, n64=4):
         ctx.autotune()
         hd = torch.from_numpy(h).to("cuda", ctx.dtype)
         p = torch.zeros(ctx.surf_shape, dtype=ctx.dtype, device="cuda")
-        opts = ctx.default_opts(relax=relax, max_iter=cap)
+        opts = ctx.default_opts(relax=relax, max_iter=cap, **({"tol": 1e-7} if prec == "fp32" else {}))
         rows = []
         ep = torch.empty(ctx.scal_shape, dtype=ctx.dtype, device="cuda")
         torch.cuda.synchronize()
@@ -507,7 +513,9 @@ def batch_problems(n_prob=64, seed=1814):
     (H uniform in [0.6, 0.9], flat PSD for 4 <= |k| < 8, power law to k_s = max(8, n / 16),
     rms slope 0.1, depth 0.05); total load log-uniform over the decade below the load of a 10 %
     elastic contact fraction (Hertz: pi a^2 = 0.1, W = 4 E* a^3 / (3 R); rough: mean pressure
-    0.1 E* slope / 2), five increments (Hertz) or ten (rough); sigma_y = 0.05 E*, E_h = 0.1 E."""
+    0.1 E* slope / 2), five increments (Hertz) or ten (rough); sigma_y = 0.05 E*, E_h = 0.1 E;
+    Algorithm 1 in the listing's order at relaxation 0.5 (Hertz), with the relaxed value carried
+    at relaxation 0.3 (rough)."""
     from paper_1811_11558_gb300 import inputs
 
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -523,17 +531,17 @@ def batch_problems(n_prob=64, seed=1814):
             h = inputs.self_affine_surface(n, 1.0, hurst, 4, 8, max(8, n // 16), 0.1, seed=seed + 1 + i)
             z = inputs.uniform_depth(nz, 0.05)
             w10 = 0.1 * es * 0.1 / 2.0
-            relax = 0.3
+            relax, mode = 0.3, 1   # the relaxed value carried: the listing's order stalls on rough loads
         else:
             h = inputs.hertz_profile(n, n, 1.0, 1.0, 0.5)
             z = inputs.uniform_depth(nz, 0.5)
             a = np.sqrt(0.1 / np.pi)
             w10 = 4.0 * es * a ** 3 / (3.0 * 0.5)
-            relax = 0.5
+            relax, mode = 0.5, 0
         W = w10 * 10.0 ** u
         ninc = 10 if rough else 5   # small load steps on rough surfaces (the paper's remedy)
         probs.append({"n": n, "nz": nz, "rough": rough, "z": z, "h": h,
-                      "loads": [W * (k + 1) / ninc for k in range(ninc)], "relax": relax})
+                      "loads": [W * (k + 1) / ninc for k in range(ninc)], "relax": relax, "relax_mode": mode})
     return probs
 
 
@@ -552,7 +560,8 @@ def batch_metrics(n_prob=64, slots=16, seed=1814, max_iter=80, n64=4):
 
     def req(i, pb, prec="fp32"):
         return Request(i, pb["n"], pb["z"], pb["h"], pb["loads"], precision=prec, E=E, nu=NU, sigma_y=0.05 * es,
-                       E_h=0.1 * E, opts={"relax": pb["relax"], "max_iter": max_iter})
+                       E_h=0.1 * E, opts={"relax": pb["relax"], "relax_mode": pb["relax_mode"],
+                                                         "max_iter": max_iter})
 
     srv = Server(slots=slots)
     t0 = time.perf_counter()
@@ -582,7 +591,8 @@ def batch_metrics(n_prob=64, slots=16, seed=1814, max_iter=80, n64=4):
             p = torch.empty(ctx.surf_shape, dtype=ctx.dtype, device="cuda")
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ctx.solve_contact(hd, pb["loads"], p, ctx.default_opts(relax=pb["relax"], max_iter=max_iter),
+            ctx.solve_contact(hd, pb["loads"], p, ctx.default_opts(relax=pb["relax"], relax_mode=pb["relax_mode"],
+                                                                    max_iter=max_iter),
                               allow_not_converged=True)
             t[prec].append(time.perf_counter() - t0)
             press[prec] = p.cpu().numpy().astype(np.float64)

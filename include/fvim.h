@@ -274,7 +274,20 @@ typedef struct {
   double df_tol_abs;  /* DF-SANE: ||R|| <= df_tol_abs + df_tol_rel ||R_0|| (discrete L2 norm) */
   double df_tol_rel;
   int df_max_iter;
+  int relax_mode;     /* Algorithm 1's relaxation: FVIM_RELAX_LITERAL or FVIM_RELAX_CARRIED          */
 } fvim_opts;
+
+/* Algorithm 1 (Sec. 5.2) relaxes dU_prev <- dU_prev + lambda (dU - dU_prev), sets H = H0 - dU_prev
+ * and then overwrites dU_prev <- dU.  FVIM_RELAX_LITERAL keeps that order (the next H blends the
+ * last two raw iterates; e compares raw iterates).  FVIM_RELAX_CARRIED skips the overwrite, so
+ * the relaxed value is carried from iteration to iteration (under-relaxation of the fixed point
+ * dU = F(H0 - dU); e = ||dU - relaxed|| / ||H0||, the fixed-point residual), the behaviour the
+ * paper's text ascribes to lambda ("helps the algorithm to converge on large loading steps"):
+ * with the literal order a strongly coupled increment converges only if its coupling gain a
+ * satisfies a (1 - lambda) < 1, so a smaller lambda does not help; carried, any a converges for a
+ * small enough lambda.  Both have the same converged increments. */
+#define FVIM_RELAX_LITERAL 0
+#define FVIM_RELAX_CARRIED 1
 
 typedef struct {
   int status;                                  /* FVIM_OK or FVIM_ERR_NOT_CONVERGED        */
@@ -291,7 +304,7 @@ typedef struct {
 
 /* fvim_default_opts -- the defaults: tol 1e-9 (FP64) / 1e-8 (FP32), max_iter 100, relax 1,
  * cg_tol 1e-12 / 1e-7, cg_max_iter 2000, df_tol_abs 0, df_tol_rel 1e-10 / 1e-6,
- * df_max_iter 500. */
+ * df_max_iter 500, relax_mode FVIM_RELAX_LITERAL. */
 int fvim_default_opts(const fvim_ctx* ctx, fvim_opts* opts);
 
 /*

@@ -29,7 +29,9 @@ algorithm1
     e = ||dU - dU_prev|| / ||H0||, relaxation, H = H0 - dU_prev, dU_prev = dU, until
     e < tol or k > N_max; then update(S).
     Readings: H0 = h - N[C:eps_p_n].e3|0 at the start of the increment (Rem.
-    modified_contact); the literal order of the relaxation lines is kept.
+    modified_contact); the literal order of the relaxation lines is kept by default, and the
+    under-relaxation that carries the relaxed value (what the text ascribes to lambda) is
+    the option relax_mode="carried".
     Parity: the converged increment is pinned by its defining equations (R = 0, contact
     KKT on the modified surface, plastic admissibility, total load); the iterates of
     the coupling loop are not compared.
@@ -153,9 +155,18 @@ def residual_surface(eps_p, z, L1, L2, E, nu):
 
 
 def algorithm1(W, h, state, z, L1, L2, E, nu, sigma_y, E_h, tol=1e-9, N_max=50, relax=1.0,
-               cg_tol=1e-13, df_tol_rel=1e-11):
+               cg_tol=1e-13, df_tol_rel=1e-11, relax_mode="literal"):
     """One load increment of Algorithm 1 (Sec. 5.2).  Updates ``state`` in place and
-    returns (T, info)."""
+    returns (T, info).
+
+    relax_mode "literal": the listing's order (relax, H = H0 - relaxed, then dU_prev = dU).
+    relax_mode "carried": the relaxed value is kept as dU_prev (under-relaxation of the fixed
+    point dU = F(H0 - dU)); the error is then the fixed-point residual ||dU - dU_prev|| / ||H0||
+    against the relaxed value the modified surface was built from.  The paper's text says the
+    relaxation helps convergence on large steps, which is what this form does; both give the
+    same converged increment."""
+    if relax_mode not in ("literal", "carried"):
+        raise ValueError(relax_mode)
     H0 = np.asarray(h, dtype=np.float64) - residual_surface(state.eps_p, z, L1, L2, E, nu)
     h_norm = np.linalg.norm(H0)
     dU_prev = np.zeros_like(H0)
@@ -174,7 +185,8 @@ def algorithm1(W, h, state, z, L1, L2, E, nu, sigma_y, E_h, tol=1e-9, N_max=50, 
         history.append((cinfo["iterations"], dinfo["iterations"], e))
         dU_prev = dU_prev + relax * (dU - dU_prev)
         H = H0 - dU_prev
-        dU_prev = dU
+        if relax_mode == "literal":
+            dU_prev = dU
         k += 1
         if e < tol or k > N_max:
             break

@@ -332,14 +332,16 @@ __global__ void k_diff2(const T* __restrict__ a, const T* __restrict__ b, size_t
   block_reduce<1>(v, part);
 }
 
-// Algorithm 1: relaxed = dU_prev + lambda (dU - dU_prev); H = H0 - relaxed; dU_prev = dU
+// Algorithm 1: relaxed = dU_prev + lambda (dU - dU_prev); H = H0 - relaxed; then dU_prev = dU
+// (the listing's order, carry = 0) or dU_prev = relaxed (under-relaxation that carries the
+// relaxed value, carry = 1)
 template <typename T>
 __global__ void k_relax(T* __restrict__ H, const T* __restrict__ H0, T* __restrict__ dUp, const T* __restrict__ dU,
-                        double lam, size_t n) {
+                        double lam, int carry, size_t n) {
   for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
     const double relaxed = (double)dUp[i] + lam * ((double)dU[i] - (double)dUp[i]);
     H[i] = (T)((double)H0[i] - relaxed);
-    dUp[i] = dU[i];
+    dUp[i] = carry ? (T)relaxed : dU[i];
   }
 }
 // number of positive entries
@@ -1264,8 +1266,10 @@ int solve_contact_t(fvim_ctx* c, const T* h, const double* loads, int n_inc, con
       FVIM_CUDA_CHECK_LAUNCH();
       if ((rc = finish<1>(c, gs, v))) return rc;
       e = sqrt(v[0]) / hnorm;
-      // relaxation, modified surface, then dU_prev <- dU (Algorithm 1, literal order)
-      k_relax<T><<<gs, RT, 0, c->stream>>>(H, H0, dUp, dU, o->relax, ns);
+      // relaxation, modified surface, then dU_prev <- dU (Algorithm 1, literal order) or <- the
+      // relaxed value (relax_mode FVIM_RELAX_CARRIED)
+      k_relax<T><<<gs, RT, 0, c->stream>>>(H, H0, dUp, dU, o->relax, o->relax_mode == FVIM_RELAX_CARRIED ? 1 : 0,
+                                           ns);
       FVIM_CUDA_CHECK_LAUNCH();
       k += 1;
       if (e < o->tol || k > o->max_iter) break;
@@ -1335,13 +1339,15 @@ int fvim_default_opts(const fvim_ctx* c, fvim_opts* o) {
   o->df_tol_abs = 0.0;
   o->df_tol_rel = dbl ? 1e-10 : 1e-6;
   o->df_max_iter = 500;
+  o->relax_mode = FVIM_RELAX_LITERAL;
   return FVIM_OK;
 }
 
 static int check_opts(const fvim_opts* o) {
   if (!o) return FVIM_ERR_ARG;
   if (!(o->tol > 0) || o->max_iter < 1 || !(o->relax > 0 && o->relax <= 1) || !(o->cg_tol > 0) ||
-      o->cg_max_iter < 1 || !(o->df_tol_abs >= 0) || !(o->df_tol_rel >= 0) || o->df_max_iter < 0)
+      o->cg_max_iter < 1 || !(o->df_tol_abs >= 0) || !(o->df_tol_rel >= 0) || o->df_max_iter < 0 ||
+      (o->relax_mode != FVIM_RELAX_LITERAL && o->relax_mode != FVIM_RELAX_CARRIED))
     return FVIM_ERR_ARG;
   return FVIM_OK;
 }

@@ -29,7 +29,7 @@ class Opts(ctypes.Structure):
     """fvim_opts (include/fvim.h)."""
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("relax", ctypes.c_double),
                 ("cg_tol", ctypes.c_double), ("cg_max_iter", ctypes.c_int), ("df_tol_abs", ctypes.c_double),
-                ("df_tol_rel", ctypes.c_double), ("df_max_iter", ctypes.c_int)]
+                ("df_tol_rel", ctypes.c_double), ("df_max_iter", ctypes.c_int), ("relax_mode", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):

@@ -169,3 +169,54 @@ def test_relaxation_does_not_change_the_converged_increment():
     assert st.e_p.max() > 0
     assert np.abs(outs[0][0] - outs[1][0]).max() < 1e-7 * outs[0][0].max()
     assert np.abs(outs[0][1] - outs[1][1]).max() < 1e-7 * np.abs(outs[0][1]).max()
+
+
+def test_carried_relaxation_reaches_the_same_increment():
+    """Algorithm 1 with the relaxed value carried between iterations (relax_mode "carried")
+    converges to the increment of the listing's order: the coupled problem has one solution
+    for a given load, the relaxation only changes the path."""
+    n, nz = 8, 5
+    z = inputs.uniform_depth(nz, 0.5)
+    h = inputs.hertz_profile(n, n, 1.0, 1.0, 0.25)
+    sy, Eh = 0.03, 0.2
+    outs = []
+    for mode, relax in (("literal", 1.0), ("carried", 0.5), ("carried", 0.2)):
+        st = C.PlasticState(nz, n, n)
+        Tn, info = C.algorithm1(6e-3, h, st, z, 1.0, 1.0, E, NU, sy, Eh, tol=1e-11, N_max=400, relax=relax,
+                                relax_mode=mode)
+        assert info["converged"], (mode, relax)
+        outs.append((Tn, st.eps_p))
+    for Tn, ep in outs[1:]:
+        assert np.abs(Tn - outs[0][0]).max() < 1e-7 * outs[0][0].max()
+        assert np.abs(ep - outs[0][1]).max() < 1e-7 * np.abs(outs[0][1]).max()
+
+
+@pytest.mark.parametrize("a", [0.8, 1.2, 1.6, 3.0])
+def test_relaxation_orders_on_a_linear_coupling(a):
+    """The two relaxation orders on the scalar model of one coupled increment: the residual
+    displacement x of the plastic flow lowers the modified surface H = H0 - r, which lowers the
+    flow, x = 1 - a (H0 - H), a the gain of that feedback (large on rough surfaces with a few
+    heavily loaded asperities).  The listing's order, x_{k+1} = 1 - a ((1 - lambda) x_{k-1} +
+    lambda x_k), converges only when a (1 - lambda) < 1 (the product of its characteristic roots);
+    the carried one, r_k = r_{k-1} + lambda (x_k - r_{k-1}), whenever |1 - lambda (1 + a)| < 1.
+    The iteration is the one written in oracle.contact.algorithm1, with the two inner solves
+    replaced by this linear response."""
+    lam = 0.3
+
+    def run(mode):
+        x_prev, H, H0, errs = 0.0, 1.0, 1.0, []
+        for _ in range(400):
+            x = 1.0 - a * (H0 - H)        # F: more residual displacement, less flow
+            e = abs(x - x_prev)
+            errs.append(e)
+            r = x_prev + lam * (x - x_prev)
+            H = H0 - r
+            x_prev = x if mode == "literal" else r
+        return errs
+
+    lit, car = run("literal"), run("carried")
+    assert car[-1] < 1e-12                       # carried: |1 - 0.3 (1 + a)| < 1 for every a here
+    if a * (1 - lam) < 1:
+        assert lit[-1] < 1e-6
+    else:
+        assert lit[-1] > 1e-3                     # literal: stalls or grows once a (1 - lambda) >= 1
