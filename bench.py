@@ -310,6 +310,7 @@ def run_gpu(args):
         line["solves"]["batch"] = batch_metrics()
         line["solves"]["epp_sweep"] = epp_metrics()
         line["scaling_sweep"] = scaling_metrics()
+        line["group_apply"] = group_metrics()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if pg is not None:
@@ -514,8 +515,9 @@ def batch_problems(n_prob=64, seed=1814):
     rms slope 0.1, depth 0.05); total load log-uniform over the decade below the load of a 10 %
     elastic contact fraction (Hertz: pi a^2 = 0.1, W = 4 E* a^3 / (3 R); rough: mean pressure
     0.1 E* slope / 2), five increments (Hertz) or ten (rough); sigma_y = 0.05 E*, E_h = 0.1 E;
-    Algorithm 1 in the listing's order at relaxation 0.5 (Hertz), with the relaxed value carried
-    at relaxation 0.3 (rough)."""
+    Algorithm 1 with the relaxed value carried between iterations (relax_mode 1: the listing's
+    order stalls on rough loads and needs two to three times the iterations on Hertz loads) at
+    relaxation 0.5 (Hertz) and 0.3 (rough)."""
     from paper_1811_11558_gb300 import inputs
 
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -531,13 +533,13 @@ def batch_problems(n_prob=64, seed=1814):
             h = inputs.self_affine_surface(n, 1.0, hurst, 4, 8, max(8, n // 16), 0.1, seed=seed + 1 + i)
             z = inputs.uniform_depth(nz, 0.05)
             w10 = 0.1 * es * 0.1 / 2.0
-            relax, mode = 0.3, 1   # the relaxed value carried: the listing's order stalls on rough loads
+            relax, mode = 0.3, 1
         else:
             h = inputs.hertz_profile(n, n, 1.0, 1.0, 0.5)
             z = inputs.uniform_depth(nz, 0.5)
             a = np.sqrt(0.1 / np.pi)
             w10 = 4.0 * es * a ** 3 / (3.0 * 0.5)
-            relax, mode = 0.5, 0
+            relax, mode = 0.5, 1
         W = w10 * 10.0 ** u
         ninc = 10 if rough else 5   # small load steps on rough surfaces (the paper's remedy)
         probs.append({"n": n, "nz": nz, "rough": rough, "z": z, "h": h,
@@ -704,6 +706,74 @@ def stream_metrics(n_req=8, slots=8, seed=1815, n_inc=3, n64_max=256):
                                       "p99_ms": 1e3 * slat[99]},
             "fp64_plain_subsample": {"grids_up_to": n64_max, "requests": sub,
                                      "fp64_over_fp32_plain_time": (t64s / t32s) if t32s > 0 else None}}
+
+
+def group_metrics(n_prob=64, seed=1814, reps=10):
+    """The operator work of the uneven batch in one launch per pass: the Mindlin apply (stress
+    output) of the n_prob problems of batch_problems (grids 64^2..512^2, Nz 8..32, their own
+    depth nodes and cells, FP32, seeded plastic-strain fields) through
+    fvim_apply_mindlin_group, five launches for all problems, replayed from a CUDA graph;
+    beside it the same applies issued problem by problem (five launches each) replayed from
+    one CUDA graph, every context on the same depth plan (chunk length 4, row / column FFTs).
+    The problems' fields (several GB) are far larger than L2, so no flush is needed between
+    replays.  CUDA events on the replay stream; 48 B per voxel (eps_p read, stress written) is
+    the algorithmic traffic of an apply."""
+    import torch
+
+    from paper_1811_11558_gb300 import Context, fvim, inputs
+
+    peak, peak_kind = _peaks()
+    probs = batch_problems(n_prob, seed)
+    ctxs, eps, outs = [], [], []
+    for i, pb in enumerate(probs):
+        c = Context(pb["n"], pb["n"], pb["z"], 1.0, 1.0, precision="fp32", E=E, nu=NU)
+        c.set_plan(depth_chunk=4, fft_path="rows_cols", depth_ctas=2)
+        ctxs.append(c)
+        eps.append(torch.from_numpy(inputs.plastic_strain_field(pb["n"], pb["n"], pb["z"], seed=seed + 100 + i,
+                                                                dtype=np.float32)).to("cuda"))
+        outs.append(torch.empty_like(eps[-1]))
+    vox = sum(c.n1 * c.n2 * c.nz for c in ctxs)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):                 # first calls outside any capture
+        fvim.apply_mindlin_group(ctxs, eps, outs)
+        for c, e, o in zip(ctxs, eps, outs):
+            c.apply_mindlin(e, o)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g_grp, g_seq = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_grp, capture_error_mode="thread_local"):
+        fvim.apply_mindlin_group(ctxs, eps, outs)
+    with torch.cuda.graph(g_seq, capture_error_mode="thread_local"):
+        for c, e, o in zip(ctxs, eps, outs):
+            c.apply_mindlin(e, o)
+
+    def timed(g):
+        for _ in range(3):
+            g.replay()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    t_seq = timed(g_seq)
+    ref = [o.clone() for o in outs]
+    t_grp = timed(g_grp)
+    diff = max(float((o - r).norm() / r.norm()) for o, r in zip(outs, ref))
+    for c in ctxs:
+        c.close()
+    shapes = sorted({(c.n1, c.nz) for c in ctxs})
+    return {"workload": "group_%d_uneven_mindlin_fp32" % n_prob, "problems": n_prob, "shapes": len(shapes),
+            "voxels": vox, "l2": "inputs larger than L2 (%.1f GB per apply)" % (vox * 48e-9),
+            "group": {"ms": t_grp, "voxels_per_s": vox / (t_grp * 1e-3), "launches": 5,
+                      "hbm_frac": vox * ALG_BYTES_PER_VOXEL / (t_grp * 1e-3) / (peak * 1e9), "peak": peak_kind},
+            "per_problem_graph": {"ms": t_seq, "voxels_per_s": vox / (t_seq * 1e-3), "launches": 5 * n_prob},
+            "group_speedup": t_seq / t_grp,
+            "group_vs_per_problem_rel_l2_max": diff}
 
 
 def scaling_metrics(sizes=(4, 8, 16, 32, 64, 128), reps=20):

@@ -94,6 +94,34 @@ int fvim_set_stream(fvim_ctx* ctx, void* stream);
 int fvim_apply_mindlin(fvim_ctx* ctx, const void* eps_p, void* out, int out_kind, void* u3_surface);
 
 /*
+ * fvim_apply_mindlin_group -- fvim_apply_mindlin on n independent problems of uneven grid
+ * size in one launch per pass: forward rows, forward columns, depth operator, inverse
+ * columns, inverse rows, five launches for the whole group (the operator of Thm 1 per
+ * problem, Sec. 3.1-3.2; batching many surfaces has no counterpart in the paper, which
+ * solves one problem at a time).  Every CTA of a launch looks its problem up in a table that
+ * travels as a kernel parameter, so the call allocates nothing, copies nothing to the device
+ * and can be captured in a CUDA graph.
+ *   ctx        HOST array of n distinct FP32 contexts whose grids have power-of-two sides
+ *              64 <= N1, N2 <= 512 and 4 <= Nz <= 64; problem i uses ctx[i]'s grid,
+ *              material and scratch buffers.
+ *   eps_p, out HOST arrays of n device pointers, each as for fvim_apply_mindlin (out may
+ *              not alias eps_p).  No surface displacement output.
+ *   out_kind   FVIM_STRESS or FVIM_STRAIN, for every problem.
+ *   stream     cudaStream_t the launches go to (NULL = legacy default stream).  The
+ *              contexts' scratch buffers are shared with their own calls: the caller orders
+ *              the group after any work of those contexts on their own streams.
+ * Problem i gives the result of fvim_apply_mindlin(ctx[i], eps_p[i], out[i], out_kind,
+ * NULL) under the depth plan {chunk length 4, the context's cutoff}, except that the cutoff
+ * of Sec. 3.2 is decided for the tiles a CTA holds together (with cutoff 0 the results are
+ * bitwise the same).  1 <= n <= FVIM_GROUP_MAX.  Returns FVIM_ERR_ARG for bad arguments
+ * (n out of range, a NULL or repeated context or pointer) and FVIM_ERR_UNSUPPORTED for a
+ * context outside the shapes above; nothing is launched then.
+ */
+#define FVIM_GROUP_MAX 64
+int fvim_apply_mindlin_group(fvim_ctx* const* ctx, int n, const void* const* eps_p, void* const* out, int out_kind,
+                             void* stream);
+
+/*
  * fvim_apply_boussinesq -- the Boussinesq operator M[p] for a normal surface pressure
  * (Eq. M:conv, Eq. B:fourier).
  *   p           device [N2][N1] pressure (input).

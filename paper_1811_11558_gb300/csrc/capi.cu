@@ -606,6 +606,64 @@ int fvim_apply_mindlin(fvim_ctx* c, const void* eps_p, void* out, int out_kind, 
   return apply_mindlin_t<float>(c, (const float*)eps_p, (float*)out, out_kind, (float*)u3);
 }
 
+static_assert(FVIM_GROUP_MAX == kGrpMax, "group size of the C ABI and of the kernels");
+
+int fvim_apply_mindlin_group(fvim_ctx* const* ctx, int n, const void* const* eps_p, void* const* out, int out_kind,
+                             void* stream) {
+  if (!ctx || !eps_p || !out || n < 1 || n > FVIM_GROUP_MAX) return FVIM_ERR_ARG;
+  if (out_kind != FVIM_STRESS && out_kind != FVIM_STRAIN) return FVIM_ERR_ARG;
+  GrpTable t;
+  memset(&t, 0, sizeof(t));
+  t.n = n;
+  for (int i = 0; i < n; ++i) {
+    const fvim_ctx* c = ctx[i];
+    if (!c || !eps_p[i] || !out[i] || eps_p[i] == out[i]) return FVIM_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctx[j] == c || out[j] == out[i]) return FVIM_ERR_ARG;
+    const bool pow2 = (c->n1 & (c->n1 - 1)) == 0 && (c->n2 & (c->n2 - 1)) == 0;
+    if (c->prec != FVIM_FP32 || c->gen || !pow2 || c->n1 < 64 || c->n1 > 512 || c->n2 < 64 || c->n2 > 512 ||
+        c->nz < 4 || c->nz > 64)
+      return FVIM_ERR_UNSUPPORTED;
+    GrpProb& P = t.p[i];
+    P.eps = (const float*)eps_p[i];
+    P.out = (float*)out[i];
+    P.spec = (float2*)c->spec;
+    P.nq = (float*)c->nq;
+    P.tw1 = (const float2*)c->tw1;
+    P.tw2 = (const float2*)c->tw2;
+    P.zn = (const float*)c->z_dev;
+    P.n1 = c->n1;
+    P.n2 = c->n2;
+    P.nz = c->nz;
+    P.h1 = c->h1;
+    P.hs = c->hs;
+    P.nch = (c->nz + 3) / 4;
+    P.nchp = 1;
+    while (P.nchp < P.nch) P.nchp <<= 1;
+    P.uniform = c->uniform;
+    P.out_kind = out_kind;
+    const double two_pi = 6.283185307179586476925;
+    P.w1 = (float)(two_pi / c->L1);
+    P.w2 = (float)(two_pi / c->L2);
+    P.lam = (float)c->lam;
+    P.mu = (float)c->mu;
+    P.nu = (float)c->nu;
+    P.hz = (float)c->hz;
+    P.cut = c->depth_cut;
+    // the k1 = N1/2 column never goes through the column transforms, so it carries the
+    // factor N2 that the 1/(N1 N2) normalisation of the inverse rows removes
+    P.nq_scale = out_kind == FVIM_STRESS ? -(float)c->n2 : 0.f;
+    P.scale = (float)(1.0 / ((double)c->n1 * (double)c->n2));
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc;
+  if ((rc = launch_grp_rows_fwd(t, s))) return rc;
+  if ((rc = launch_grp_cols(t, false, s))) return rc;
+  if ((rc = launch_grp_depth(t, s))) return rc;
+  if ((rc = launch_grp_cols(t, true, s))) return rc;
+  return launch_grp_rows_inv(t, s);
+}
+
 int fvim_apply_boussinesq(fvim_ctx* c, const void* p, void* u3, void* vol, int out_kind) {
   if (!c || !p || (!u3 && !vol)) return FVIM_ERR_ARG;
   if (out_kind != FVIM_STRESS && out_kind != FVIM_STRAIN) return FVIM_ERR_ARG;

@@ -30,6 +30,8 @@
 //   (not in Z^2_N): no operator term, so sigma_hat = -w_hat (stress) or 0 (strain).
 #include <string.h>
 
+#include <algorithm>
+
 #include "fvim_internal.cuh"
 
 namespace {
@@ -582,103 +584,28 @@ template <typename V> __device__ __forceinline__ void ld6(V (&w)[6], const V* W,
   for (int cc = 0; cc < 6; ++cc) w[cc] = W[(node * 6 + cc) * KT + kt];
 }
 
-template <typename T, int KT, int C, bool EIN, int MB>
-__global__ void __launch_bounds__(256, MB) k_mindlin_depth_r(typename Cx<T>::t* __restrict__ spec,
-                                                            typename Cx<T>::t* __restrict__ surf,
-                                                            const T* __restrict__ zn, int nz, int n1, int n2, int hs, int h1, int nch,
-                                                            T w1, T w2, T lam, T mu, T nu, int out_kind, int want_u3,
-                                                            int uniform, T hz, const int* __restrict__ zr, T cut,
-                                                            const __grid_constant__ CUtensorMap tmap, int tma_rows,
-                                                            int tx_extra, int* __restrict__ status) {
+// Steps 2-5 of the register depth kernel on a tile already in shared memory: W[nz][6][KT]
+// (the tile), SA / SP [>= nch][KT] (chunk moments), TR[KT][3], zs[nz].  tid = ch * KT + kt is
+// the thread's place in the tile, kblk the tile's block of KT k1 columns.  A ghost tile (a
+// CTA slot without a tile) takes part in the barriers only.
+template <typename T, int KT, int C, bool EIN>
+__device__ __forceinline__ void depth_r_body(typename Cx<T>::t* W, Mom<typename Cx<T>::t>* SA,
+                                             Mom<typename Cx<T>::t>* SP, typename Cx<T>::t* TR, const T* zs, int tid,
+                                             int kblk, int k2, bool ghost, typename Cx<T>::t* __restrict__ spec,
+                                             typename Cx<T>::t* __restrict__ surf, int nz, int n1, int n2, int hs,
+                                             int h1, int nch, T w1, T w2, T lam, T mu, T nu, int out_kind,
+                                             int want_u3, int uniform, T hz, T cut) {
   typedef typename Cx<T>::t V;
-  static_assert(sizeof(V) == 8 && KT % 2 == 0, "FP32 tiles of an even width");
-  extern __shared__ __align__(128) unsigned char smraw[];  // tensor-copy boxes land at 128-byte offsets
-  V* W = reinterpret_cast<V*>(smraw);                               // [nz][6][KT]
-  Mom<V>* SA = reinterpret_cast<Mom<V>*>(W + (size_t)nz * 6 * KT);  // [nch][KT]
-  Mom<V>* SP = SA + (size_t)nch * KT;                               // [nch][KT]
-  V* TR = reinterpret_cast<V*>(SP + (size_t)nch * KT);              // [KT][3] image traction
-  T* zs = reinterpret_cast<T*>(TR + 3 * KT);                        // [nz]
-  // mbarrier of the tensor copies, 8-byte aligned after the depth nodes
-  unsigned long long* tbar = reinterpret_cast<unsigned long long*>(
-      reinterpret_cast<unsigned char*>(zs) + (((size_t)nz * sizeof(T) + 7) & ~(size_t)7));
-  const int kt = threadIdx.x & (KT - 1);
-  const int ch = threadIdx.x / KT;
-  const int k1 = blockIdx.x * KT + kt;
-  const int k2 = blockIdx.y;
+  const int kt = tid & (KT - 1);
+  const int ch = tid / KT;
+  const int k1 = kblk * KT + kt;
   const size_t plane = (size_t)n2 * h1;
-  const size_t colofs = (size_t)k2 * h1 + blockIdx.x * KT;
-
-  // 1. load the tile and the depth nodes (layers outside zr hold no input: their spectrum was
-  //    not computed and reads as zero).  With a tensor map (tma_rows > 0): one thread issues
-  //    tensor copies of tma_rows x KT complex boxes (rows z c, one k2, KT columns) that complete
-  //    on an mbarrier; the wait is bounded, and a copy that never completes sets the status word
-  //    and every thread of the CTA returns after a second bounded wait.  Otherwise 16-byte
-  //    cp.async copies by all threads.
-  if (tma_rows > 0) {
-    const unsigned bar = (unsigned)__cvta_generic_to_shared(tbar);
-    if (threadIdx.x == 0) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const unsigned bytes = (unsigned)(nz * 6 * KT * sizeof(V) + tx_extra);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-      const int x = (int)(blockIdx.x * KT * 2);  // first k1 column, in floats (16-byte multiple)
-      for (int r0 = 0; r0 < nz * 6; r0 += tma_rows) {
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(W + (size_t)r0 * KT);
-        asm volatile(
-            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-            "[%5];" ::"r"(dst),
-            "l"(reinterpret_cast<unsigned long long>(&tmap)), "r"(x), "r"(k2), "r"(r0), "r"(bar)
-            : "memory");
-      }
-    }
-    for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];
-    bool done = mbar_wait_bounded(bar, 1000000000ull);   // 1 s
-    if (__syncthreads_or(!done)) {
-      if (threadIdx.x == 0 && status) atomicOr(status, 1);
-      if (!done) mbar_wait_bounded(bar, 1000000000ull);  // the copies of this CTA, once more
-      return;
-    }
-    if (zr) {
-      const int zlo = zr[0], zhi = zr[1];
-      for (int idx = threadIdx.x; idx < nz * 6 * KT; idx += blockDim.x) {
-        const int zl = idx / (6 * KT);
-        if (zl < zlo || zl >= zhi) W[idx] = mk<V>(0, 0);
-      }
-    }
-    __syncthreads();
-  } else if (!zr) {
-    for (int idx = threadIdx.x; idx < nz * 6 * (KT / 2); idx += blockDim.x) {
-      const int zc = idx / (KT / 2), j = 2 * (idx % (KT / 2));
-      cp_async_16(W + zc * KT + j, spec + (size_t)zc * plane + colofs + j);
-    }
-  } else {
-    const int zlo = zr[0], zhi = zr[1];
-    for (int idx = threadIdx.x; idx < nz * 6 * (KT / 2); idx += blockDim.x) {
-      const int zc = idx / (KT / 2), j = 2 * (idx % (KT / 2));
-      const int zl = zc / 6;
-      if (zl >= zlo && zl < zhi) {
-        cp_async_16(W + zc * KT + j, spec + (size_t)zc * plane + colofs + j);
-      } else {
-        W[zc * KT + j] = mk<V>(0, 0);
-        W[zc * KT + j + 1] = mk<V>(0, 0);
-      }
-    }
-  }
-  if (tma_rows <= 0) {
-    for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];
-    cp_async_wait_all();
-    __syncthreads();
-  }
-
   const ModeGeom<T> g = mode_geom<T>(k1, k2, n1, n2, hs, w1, w2);
   const bool special = g.zero || g.nyq;
   const int n0 = ch * C;
   const int nend = min(n0 + C, nz);
   const int e1 = min(n0 + C, nz - 1);  // elements [n0, e1)
-  const bool active = n0 < nz;
+  const bool active = !ghost && n0 < nz;
   const bool work = active && !special;
 
   // 2. (eps_p input: w = C:eps_p per mode) rotate own nodes into the (q, p, 3) frame
@@ -903,6 +830,144 @@ __global__ void __launch_bounds__(256, MB) k_mindlin_depth_r(typename Cx<T>::t* 
   }
 }
 
+template <typename T, int KT, int C, bool EIN, int MB>
+__global__ void __launch_bounds__(256, MB) k_mindlin_depth_r(typename Cx<T>::t* __restrict__ spec,
+                                                            typename Cx<T>::t* __restrict__ surf,
+                                                            const T* __restrict__ zn, int nz, int n1, int n2, int hs, int h1, int nch,
+                                                            T w1, T w2, T lam, T mu, T nu, int out_kind, int want_u3,
+                                                            int uniform, T hz, const int* __restrict__ zr, T cut,
+                                                            const __grid_constant__ CUtensorMap tmap, int tma_rows,
+                                                            int tx_extra, int* __restrict__ status) {
+  typedef typename Cx<T>::t V;
+  static_assert(sizeof(V) == 8 && KT % 2 == 0, "FP32 tiles of an even width");
+  extern __shared__ __align__(128) unsigned char smraw[];  // tensor-copy boxes land at 128-byte offsets
+  V* W = reinterpret_cast<V*>(smraw);                               // [nz][6][KT]
+  Mom<V>* SA = reinterpret_cast<Mom<V>*>(W + (size_t)nz * 6 * KT);  // [nch][KT]
+  Mom<V>* SP = SA + (size_t)nch * KT;                               // [nch][KT]
+  V* TR = reinterpret_cast<V*>(SP + (size_t)nch * KT);              // [KT][3] image traction
+  T* zs = reinterpret_cast<T*>(TR + 3 * KT);                        // [nz]
+  // mbarrier of the tensor copies, 8-byte aligned after the depth nodes
+  unsigned long long* tbar = reinterpret_cast<unsigned long long*>(
+      reinterpret_cast<unsigned char*>(zs) + (((size_t)nz * sizeof(T) + 7) & ~(size_t)7));
+  const int k2 = blockIdx.y;
+  const size_t plane = (size_t)n2 * h1;
+  const size_t colofs = (size_t)k2 * h1 + blockIdx.x * KT;
+
+  // 1. load the tile and the depth nodes (layers outside zr hold no input: their spectrum was
+  //    not computed and reads as zero).  With a tensor map (tma_rows > 0): one thread issues
+  //    tensor copies of tma_rows x KT complex boxes (rows z c, one k2, KT columns) that complete
+  //    on an mbarrier; the wait is bounded, and a copy that never completes sets the status word
+  //    and every thread of the CTA returns after a second bounded wait.  Otherwise 16-byte
+  //    cp.async copies by all threads.
+  if (tma_rows > 0) {
+    const unsigned bar = (unsigned)__cvta_generic_to_shared(tbar);
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned bytes = (unsigned)(nz * 6 * KT * sizeof(V) + tx_extra);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+      const int x = (int)(blockIdx.x * KT * 2);  // first k1 column, in floats (16-byte multiple)
+      for (int r0 = 0; r0 < nz * 6; r0 += tma_rows) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(W + (size_t)r0 * KT);
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+            "[%5];" ::"r"(dst),
+            "l"(reinterpret_cast<unsigned long long>(&tmap)), "r"(x), "r"(k2), "r"(r0), "r"(bar)
+            : "memory");
+      }
+    }
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];
+    bool done = mbar_wait_bounded(bar, 1000000000ull);   // 1 s
+    if (__syncthreads_or(!done)) {
+      if (threadIdx.x == 0 && status) atomicOr(status, 1);
+      if (!done) mbar_wait_bounded(bar, 1000000000ull);  // the copies of this CTA, once more
+      return;
+    }
+    if (zr) {
+      const int zlo = zr[0], zhi = zr[1];
+      for (int idx = threadIdx.x; idx < nz * 6 * KT; idx += blockDim.x) {
+        const int zl = idx / (6 * KT);
+        if (zl < zlo || zl >= zhi) W[idx] = mk<V>(0, 0);
+      }
+    }
+    __syncthreads();
+  } else if (!zr) {
+    for (int idx = threadIdx.x; idx < nz * 6 * (KT / 2); idx += blockDim.x) {
+      const int zc = idx / (KT / 2), j = 2 * (idx % (KT / 2));
+      cp_async_16(W + zc * KT + j, spec + (size_t)zc * plane + colofs + j);
+    }
+  } else {
+    const int zlo = zr[0], zhi = zr[1];
+    for (int idx = threadIdx.x; idx < nz * 6 * (KT / 2); idx += blockDim.x) {
+      const int zc = idx / (KT / 2), j = 2 * (idx % (KT / 2));
+      const int zl = zc / 6;
+      if (zl >= zlo && zl < zhi) {
+        cp_async_16(W + zc * KT + j, spec + (size_t)zc * plane + colofs + j);
+      } else {
+        W[zc * KT + j] = mk<V>(0, 0);
+        W[zc * KT + j + 1] = mk<V>(0, 0);
+      }
+    }
+  }
+  if (tma_rows <= 0) {
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];
+    cp_async_wait_all();
+    __syncthreads();
+  }
+
+  depth_r_body<T, KT, C, EIN>(W, SA, SP, TR, zs, threadIdx.x, blockIdx.x, k2, false, spec, surf, nz, n1, n2, hs, h1,
+                              nch, w1, w2, lam, mu, nu, out_kind, want_u3, uniform, hz, cut);
+}
+
+// ----------------------------------------------------------------------------------
+// Grouped depth kernel: the tiles of every problem of a GrpTable in one launch.  Chunks of 4
+// nodes, 16-column tiles; a CTA of 256 threads holds 16 / nchp tiles of one problem (nchp:
+// the chunk count rounded up to a power of two; the chunks beyond nch have no nodes), each
+// with its own shared-memory slot, loaded with 16-byte cp.async copies.  The cutoff vote is
+// taken over the CTA's tiles together.
+// ----------------------------------------------------------------------------------
+__host__ __device__ constexpr size_t grp_depth_slot(int nz, int nchp) {
+  return (size_t)nz * 6 * 16 * sizeof(float2) + (size_t)2 * nchp * 16 * sizeof(Mom<float2>) +
+         (size_t)3 * 16 * sizeof(float2) + (((size_t)nz * sizeof(float) + 15) & ~(size_t)15);
+}
+
+__global__ void __launch_bounds__(256, 2) k_grp_depth(const __grid_constant__ GrpTable tab) {
+  typedef float2 V;
+  constexpr int KT = 16, C = 4;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int pi = grp_find(tab, blockIdx.x);
+  const GrpProb& P = tab.p[pi];
+  const int nz = P.nz, nchp = P.nchp, tt = KT * nchp, tpc = 256 / tt;
+  const int j = threadIdx.x / tt, tid = threadIdx.x - j * tt;
+  const int ncb = P.h1 / KT, tiles = ncb * P.n2;
+  const int tile = ((int)blockIdx.x - tab.start[pi]) * tpc + j;
+  const bool ghost = tile >= tiles;
+  const int kblk = ghost ? 0 : tile % ncb, k2 = ghost ? 0 : tile / ncb;
+  unsigned char* base = smraw + (size_t)j * grp_depth_slot(nz, nchp);
+  V* W = reinterpret_cast<V*>(base);                                // [nz][6][KT]
+  Mom<V>* SA = reinterpret_cast<Mom<V>*>(W + (size_t)nz * 6 * KT);  // [nchp][KT]
+  Mom<V>* SP = SA + (size_t)nchp * KT;                              // [nchp][KT]
+  V* TR = reinterpret_cast<V*>(SP + (size_t)nchp * KT);             // [KT][3]
+  float* zs = reinterpret_cast<float*>(TR + 3 * KT);                // [nz]
+  if (!ghost) {
+    const size_t plane = (size_t)P.n2 * P.h1;
+    const size_t colofs = (size_t)k2 * P.h1 + (size_t)kblk * KT;
+    for (int idx = tid; idx < nz * 6 * (KT / 2); idx += tt) {
+      const int zc = idx / (KT / 2), jj = 2 * (idx % (KT / 2));
+      cp_async_16(W + zc * KT + jj, P.spec + (size_t)zc * plane + colofs + jj);
+    }
+    for (int i = tid; i < nz; i += tt) zs[i] = P.zn[i];
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  depth_r_body<float, KT, C, false>(W, SA, SP, TR, zs, tid, kblk, k2, ghost, P.spec, nullptr, nz, P.n1, P.n2, P.hs,
+                                    P.h1, P.nch, P.w1, P.w2, P.lam, P.mu, P.nu, P.out_kind, 0, P.uniform, P.hz,
+                                    P.cut);
+}
+
 // ----------------------------------------------------------------------------------
 // Boussinesq operator of a normal pressure (Eq. B:fourier): one thread per mode, loop
 // over depth.  surf holds p_hat on entry and u3_hat = 2 p_hat / (E* q) on exit.
@@ -1103,3 +1168,21 @@ template int launch_mindlin_depth<float>(const fvim_ctx*, int, bool, bool, const
 template int launch_mindlin_depth<double>(const fvim_ctx*, int, bool, bool, const int*);
 template int launch_boussinesq<float>(const fvim_ctx*, int, bool, bool);
 template int launch_boussinesq<double>(const fvim_ctx*, int, bool, bool);
+
+int launch_grp_depth(GrpTable& t, cudaStream_t s) {
+  int b = 0;
+  size_t smem = 0;
+  for (int i = 0; i < t.n; ++i) {
+    const GrpProb& P = t.p[i];
+    const int tpc = 16 / P.nchp, tiles = (P.h1 / 16) * P.n2;
+    t.start[i] = b;
+    b += (tiles + tpc - 1) / tpc;
+    smem = std::max(smem, (size_t)tpc * grp_depth_slot(P.nz, P.nchp));
+  }
+  t.start[t.n] = b;
+  if (b == 0) return FVIM_OK;
+  smem_cap(k_grp_depth);
+  k_grp_depth<<<b, 256, smem, s>>>(t);
+  FVIM_CUDA_CHECK_LAUNCH();
+  return FVIM_OK;
+}

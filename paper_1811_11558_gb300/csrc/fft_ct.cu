@@ -25,12 +25,23 @@ template <typename V> struct ColSm {
   __device__ __forceinline__ void put(int, int p, V x) const { buf[p * kc + f] = x; }
   __device__ __forceinline__ V get(int, int p) const { return buf[p * kc + f]; }
 };
-// contiguous rows with one pad slot every 8 entries: transform g at buf[g * ld + p + p/8]
-template <typename V> struct RowSm {
+// Row exchange layout: transform g of a row at buf[g * LD + idx(p)].  8-byte entries on rows
+// of 128 or more: no padding, entry p at p ^ ((p >> 3) & 15) (a permutation inside each
+// aligned block of 16), so that a half-warp's accesses of the radix-8 stage writes (stride 8)
+// and of the contiguous reads both fall on 16 distinct bank pairs; otherwise one pad slot
+// every 8 entries (p + p / 8), which leaves the contiguous 8-byte reads two-way conflicted
+// but suits 16-byte entries and rows shorter than a half-warp.
+template <typename V, int N> struct RowLayout {
+  static constexpr bool swz = sizeof(V) == 8 && N >= 128;
+  static constexpr int LD = swz ? N : N + N / 8;
+  static __device__ __forceinline__ int idx(int p) { return swz ? (p ^ ((p >> 3) & 15)) : p + (p >> 3); }
+};
+template <typename V, int N> struct RowSm {
   V* buf;
-  int ld;
-  __device__ __forceinline__ void put(int g, int p, V x) const { buf[g * ld + p + (p >> 3)] = x; }
-  __device__ __forceinline__ V get(int g, int p) const { return buf[g * ld + p + (p >> 3)]; }
+  __device__ __forceinline__ void put(int g, int p, V x) const {
+    buf[g * RowLayout<V, N>::LD + RowLayout<V, N>::idx(p)] = x;
+  }
+  __device__ __forceinline__ V get(int g, int p) const { return buf[g * RowLayout<V, N>::LD + RowLayout<V, N>::idx(p)]; }
 };
 
 template <typename T, bool INV, int N>
@@ -68,27 +79,37 @@ template <int N, int CW> struct ColsV {
   static constexpr int min_blocks = CW == 16 ? 1024 / threads : 1;  // CW = 16: 64 registers
 };
 
+// one CW-column block of one plane: tid in [0, N / 16 * CW), sm the block's [N][CW] exchange
+// area; a group that has no block (live false) takes part in the exchange barriers only
 template <bool INV, int N, int CW>
-__global__ void __launch_bounds__(ColsV<N, CW>::threads, ColsV<N, CW>::min_blocks)
-    k_cols_v(float2* __restrict__ planes, const float2* __restrict__ tw, int h1, const int* __restrict__ zr) {
-  if (zr && ((int)blockIdx.y / 6 < zr[0] || (int)blockIdx.y / 6 >= zr[1])) return;  // layer without input
-  extern __shared__ __align__(16) unsigned char smraw[];
-  float2* sm = reinterpret_cast<float2*>(smraw);  // [N][CW]
+__device__ __forceinline__ void cols_v_body(float2* __restrict__ planes, const float2* __restrict__ tw, int h1,
+                                            size_t plane, int cblk, int tid, float2* sm, bool live) {
   constexpr int T8 = N / 8, NP = CW / 2;
-  const int f2 = threadIdx.x % NP, t = threadIdx.x / NP;
-  float4* col = reinterpret_cast<float4*>(planes + (size_t)blockIdx.y * N * h1 + (size_t)blockIdx.x * CW + 2 * f2);
+  const int f2 = tid % NP, t = tid / NP;
+  float4* col = reinterpret_cast<float4*>(planes + plane * N * h1 + (size_t)cblk * CW + 2 * f2);
   const size_t rs = (size_t)h1 / 2;  // row stride in float4
   float2 v[2][8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
-    const float4 a = col[(size_t)(t + m * T8) * rs];
+    const float4 a = live ? col[(size_t)(t + m * T8) * rs] : make_float4(0.f, 0.f, 0.f, 0.f);
     v[0][m] = make_float2(a.x, a.y);
     v[1][m] = make_float2(a.z, a.w);
   }
   ColPairSm<CW> x{sm, f2};
   fft_ct<float2, INV, N, 2, 1>(v, t, x, tw);
+  if (live) {
 #pragma unroll
-  for (int m = 0; m < 8; ++m) col[(size_t)(t + m * T8) * rs] = make_float4(v[0][m].x, v[0][m].y, v[1][m].x, v[1][m].y);
+    for (int m = 0; m < 8; ++m)
+      col[(size_t)(t + m * T8) * rs] = make_float4(v[0][m].x, v[0][m].y, v[1][m].x, v[1][m].y);
+  }
+}
+
+template <bool INV, int N, int CW>
+__global__ void __launch_bounds__(ColsV<N, CW>::threads, ColsV<N, CW>::min_blocks)
+    k_cols_v(float2* __restrict__ planes, const float2* __restrict__ tw, int h1, const int* __restrict__ zr) {
+  if (zr && ((int)blockIdx.y / 6 < zr[0] || (int)blockIdx.y / 6 >= zr[1])) return;  // layer without input
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cols_v_body<INV, N, CW>(planes, tw, h1, blockIdx.y, blockIdx.x, threadIdx.x, reinterpret_cast<float2*>(smraw), true);
 }
 
 // Surface displacement of a pressure, column pass fused: forward FFT along x2 of kc k1
@@ -141,7 +162,7 @@ __global__ void __launch_bounds__(256) k_rows_fwd6_ct(const T* __restrict__ eps_
                                                       int n2, int rb, int z0, T lam, T mu, const int* __restrict__ zr) {
   typedef typename Cx<T>::t V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  constexpr int T8 = N / 8, LD = N + N / 8, H1 = N / 2;
+  constexpr int T8 = N / 8, LD = RowLayout<V, N>::LD, H1 = N / 2;
   const int r = threadIdx.x / T8, t = threadIdx.x % T8;
   const int z = z0 + blockIdx.y;
   if (zr && (z < zr[0] || z >= zr[1])) return;  // layer without input
@@ -158,7 +179,7 @@ __global__ void __launch_bounds__(256) k_rows_fwd6_ct(const T* __restrict__ eps_
     v[1][m] = mk<V>(w[2], w[3]);
     v[2][m] = mk<V>(w[4], w[5]);
   }
-  RowSm<V> sm{reinterpret_cast<V*>(smraw) + (size_t)r * 3 * LD, LD};
+  RowSm<V, N> sm{reinterpret_cast<V*>(smraw) + (size_t)r * 3 * LD};
   fft_ct<V, false, N, 3, 1>(v, t, sm, tw);
 #pragma unroll
   for (int g = 0; g < 3; ++g)
@@ -180,17 +201,14 @@ __global__ void __launch_bounds__(256) k_rows_fwd6_ct(const T* __restrict__ eps_
   }
 }
 
+// inverse row FFTs of row x2 of layer z (thread t of the row's N / 8; sm the row's exchange
+// area [3][LD])
 template <typename T, int N>
-__global__ void __launch_bounds__(256) k_rows_inv6_ct(const typename Cx<T>::t* __restrict__ spec,
-                                                      const T* __restrict__ nq, T* __restrict__ out,
-                                                      const typename Cx<T>::t* __restrict__ tw, int n2, int rb, int z0,
-                                                      T nq_scale, T scale) {
+__device__ __forceinline__ void rows_inv6_body(const typename Cx<T>::t* __restrict__ spec, const T* __restrict__ nq,
+                                               T* __restrict__ out, const typename Cx<T>::t* __restrict__ tw, int n2,
+                                               int z, int x2, int t, typename Cx<T>::t* smrow, T nq_scale, T scale) {
   typedef typename Cx<T>::t V;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  constexpr int T8 = N / 8, LD = N + N / 8, H1 = N / 2;
-  const int r = threadIdx.x / T8, t = threadIdx.x % T8;
-  const int z = z0 + blockIdx.y;
-  const int x2 = blockIdx.x * rb + r;
+  constexpr int T8 = N / 8, H1 = N / 2;
   V v[3][8];
 #pragma unroll
   for (int g = 0; g < 3; ++g) {
@@ -216,7 +234,7 @@ __global__ void __launch_bounds__(256) k_rows_inv6_ct(const typename Cx<T>::t* _
       v[g][m] = cadd(A, cmuli(B));
     }
   }
-  RowSm<V> sm{reinterpret_cast<V*>(smraw) + (size_t)r * 3 * LD, LD};
+  RowSm<V, N> sm{smrow};
   fft_ct<V, true, N, 3, 1>(v, t, sm, tw);
 #pragma unroll
   for (int g = 0; g < 3; ++g)
@@ -228,21 +246,33 @@ __global__ void __launch_bounds__(256) k_rows_inv6_ct(const typename Cx<T>::t* _
     }
 }
 
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_rows_inv6_ct(const typename Cx<T>::t* __restrict__ spec,
+                                                      const T* __restrict__ nq, T* __restrict__ out,
+                                                      const typename Cx<T>::t* __restrict__ tw, int n2, int rb, int z0,
+                                                      T nq_scale, T scale) {
+  typedef typename Cx<T>::t V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int T8 = N / 8, LD = RowLayout<V, N>::LD;
+  const int r = threadIdx.x / T8, t = threadIdx.x % T8;
+  rows_inv6_body<T, N>(spec, nq, out, tw, n2, z0 + blockIdx.y, blockIdx.x * rb + r, t,
+                       reinterpret_cast<V*>(smraw) + (size_t)r * 3 * LD, nq_scale, scale);
+}
+
 // FP32 forward row pass with 16-byte global accesses: the CTA's six eps_p rows are staged in
 // shared memory with 16-byte cp.async copies and read from there in the FFT's strided order;
 // the staging area then serves as the FFT exchange area, and the half spectrum leaves as
 // float4 pairs of entries.  (Staging the inverse pass the same way made it slower: 0.254
 // against 0.183 ms at 512 x 512 x 64, from the extra shared-memory traffic and registers.)
+// forward row FFTs of rows x2b .. x2b + rb - 1 of layer z by the CTA's rb * N / 8 threads;
+// smraw the CTA's staging and exchange area
 template <int N>
-__global__ void __launch_bounds__(256) k_rows_fwd6_v(const float* __restrict__ eps_p, float2* __restrict__ spec,
-                                                     float* __restrict__ nq, const float2* __restrict__ tw, int n2,
-                                                     int rb, int z0, float lam, float mu, const int* __restrict__ zr) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  constexpr int T8 = N / 8, LD = N + N / 8, H1 = N / 2;
+__device__ __forceinline__ void rows_fwd6_v_body(const float* __restrict__ eps_p, float2* __restrict__ spec,
+                                                 float* __restrict__ nq, const float2* __restrict__ tw, int n2, int rb,
+                                                 int z, int x2b, float lam, float mu, unsigned char* smraw) {
+  constexpr int T8 = N / 8, LD = RowLayout<float2, N>::LD, H1 = N / 2;
   const int r = threadIdx.x / T8, t = threadIdx.x % T8;
-  const int z = z0 + blockIdx.y;
-  if (zr && (z < zr[0] || z >= zr[1])) return;  // layer without input
-  const int x2b = blockIdx.x * rb, x2 = x2b + r;
+  const int x2 = x2b + r;
   float* stg = reinterpret_cast<float*>(smraw);  // [6][rb][N]
   const int per_c = rb * N / 4;
   for (int i = threadIdx.x; i < 6 * per_c; i += blockDim.x) {
@@ -264,7 +294,7 @@ __global__ void __launch_bounds__(256) k_rows_fwd6_v(const float* __restrict__ e
     v[2][m] = make_float2(w[4], w[5]);
   }
   __syncthreads();  // staging is dead: the exchange area takes its place
-  RowSm<float2> sm{reinterpret_cast<float2*>(smraw) + (size_t)r * 3 * LD, LD};
+  RowSm<float2, N> sm{reinterpret_cast<float2*>(smraw) + (size_t)r * 3 * LD};
   fft_ct<float2, false, N, 3, 1>(v, t, sm, tw);
 #pragma unroll
   for (int g = 0; g < 3; ++g)
@@ -287,6 +317,16 @@ __global__ void __launch_bounds__(256) k_rows_fwd6_v(const float* __restrict__ e
     nq[((size_t)z * 6 + 2 * t) * n2 + x2] = A.x;
     nq[((size_t)z * 6 + 2 * t + 1) * n2 + x2] = B.x;
   }
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) k_rows_fwd6_v(const float* __restrict__ eps_p, float2* __restrict__ spec,
+                                                     float* __restrict__ nq, const float2* __restrict__ tw, int n2,
+                                                     int rb, int z0, float lam, float mu, const int* __restrict__ zr) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int z = z0 + blockIdx.y;
+  if (zr && (z < zr[0] || z >= zr[1])) return;  // layer without input
+  rows_fwd6_v_body<N>(eps_p, spec, nq, tw, n2, rb, z, blockIdx.x * rb, lam, mu, smraw);
 }
 
 template <typename K> void smem_attr(K kern, size_t smem) {
@@ -345,7 +385,7 @@ template <typename T, int N> void rows_fwd_n(const fvim_ctx* c, const T* eps_p, 
   typedef typename Cx<T>::t V;
   const int rb = ct_rows(N, c->n2);
   if constexpr (sizeof(T) == 4 && N >= 64) {
-    const size_t sm = std::max((size_t)rb * 3 * (N + N / 8) * sizeof(V), (size_t)6 * rb * N * sizeof(T));
+    const size_t sm = std::max((size_t)rb * 3 * RowLayout<V, N>::LD * sizeof(V), (size_t)6 * rb * N * sizeof(T));
     dim3 grid(c->n2 / rb, nzs);
     smem_attr(k_rows_fwd6_v<N>, sm);
     k_rows_fwd6_v<N><<<grid, rb * (N / 8), sm, c->stream>>>((const float*)eps_p, (float2*)c->spec, (float*)c->nq,
@@ -353,7 +393,7 @@ template <typename T, int N> void rows_fwd_n(const fvim_ctx* c, const T* eps_p, 
                                                             (float)c->mu, zr);
     return;
   }
-  const size_t smem = (size_t)rb * 3 * (N + N / 8) * sizeof(V);
+  const size_t smem = (size_t)rb * 3 * RowLayout<V, N>::LD * sizeof(V);
   dim3 grid(c->n2 / rb, nzs);
   smem_attr(k_rows_fwd6_ct<T, N>, smem);
   k_rows_fwd6_ct<T, N><<<grid, rb * (N / 8), smem, c->stream>>>(eps_p, (V*)c->spec, (T*)c->nq, (const V*)c->tw1,
@@ -364,12 +404,91 @@ template <typename T, int N> void rows_inv_n(const fvim_ctx* c, T* out, T nq_sca
   typedef typename Cx<T>::t V;
   int rb = ct_rows(N, c->n2);
   if (sizeof(T) == 4 && rb >= 4) rb /= 2;  // smaller CTAs: 5 instead of 2 per SM at 101 registers
-  const size_t smem = (size_t)rb * 3 * (N + N / 8) * sizeof(V);
+  const size_t smem = (size_t)rb * 3 * RowLayout<V, N>::LD * sizeof(V);
   dim3 grid(c->n2 / rb, nzs);
   const T scale = (T)(1.0 / ((double)N * (double)c->n2));
   smem_attr(k_rows_inv6_ct<T, N>, smem);
   k_rows_inv6_ct<T, N><<<grid, rb * (N / 8), smem, c->stream>>>((const V*)c->spec, (const T*)c->nq, out,
                                                               (const V*)c->tw1, c->n2, rb, z0, nq_scale, scale);
+}
+
+// ---- grouped launches: every problem of a GrpTable in one launch per pass ---------------
+// A CTA finds its problem by the table's CTA offsets and runs the same body as the
+// single-problem kernels, so each problem's results are those of its own launch sequence.
+// Shapes are chosen so that every N in 64..512 fills the same CTA: forward rows 2048 / N1 rows
+// per CTA (256 threads), inverse rows 1024 / N1 rows (128 threads), columns 512 / N2 blocks of
+// 16 columns (512 threads, N2 threads per block).
+constexpr int kGrpRowsFwdSmem = 2048 * 3 * 9 / 8 * 8;    // >= 6 * 2048 * 4 bytes of staging
+constexpr int kGrpRowsInvSmem = 1024 * 3 * 9 / 8 * 8;
+constexpr int kGrpColsSmem = 512 * 16 * 8;
+
+template <int N> __device__ __forceinline__ void grp_rows_fwd_case(const GrpProb& P, int local, unsigned char* sm) {
+  const int rb = 2048 / N, nrb = P.n2 / rb;
+  const int z = local / nrb, x2b = (local - z * nrb) * rb;
+  rows_fwd6_v_body<N>(P.eps, P.spec, P.nq, P.tw1, P.n2, rb, z, x2b, P.lam, P.mu, sm);
+}
+
+__global__ void __launch_bounds__(256) k_grp_rows_fwd(const __grid_constant__ GrpTable tab) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pi = grp_find(tab, blockIdx.x);
+  const GrpProb& P = tab.p[pi];
+  const int local = (int)blockIdx.x - tab.start[pi];
+  switch (P.n1) {
+    case 64: grp_rows_fwd_case<64>(P, local, smraw); break;
+    case 128: grp_rows_fwd_case<128>(P, local, smraw); break;
+    case 256: grp_rows_fwd_case<256>(P, local, smraw); break;
+    case 512: grp_rows_fwd_case<512>(P, local, smraw); break;
+    default: break;
+  }
+}
+
+template <int N> __device__ __forceinline__ void grp_rows_inv_case(const GrpProb& P, int local, unsigned char* sm) {
+  constexpr int T8 = N / 8, LD = RowLayout<float2, N>::LD;
+  const int rb = 1024 / N, nrb = P.n2 / rb;
+  const int z = local / nrb, r = threadIdx.x / T8, t = threadIdx.x % T8;
+  const int x2 = (local - z * nrb) * rb + r;
+  rows_inv6_body<float, N>(P.spec, P.nq, P.out, P.tw1, P.n2, z, x2, t,
+                           reinterpret_cast<float2*>(sm) + (size_t)r * 3 * LD, P.nq_scale, P.scale);
+}
+
+__global__ void __launch_bounds__(128) k_grp_rows_inv(const __grid_constant__ GrpTable tab) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pi = grp_find(tab, blockIdx.x);
+  const GrpProb& P = tab.p[pi];
+  const int local = (int)blockIdx.x - tab.start[pi];
+  switch (P.n1) {
+    case 64: grp_rows_inv_case<64>(P, local, smraw); break;
+    case 128: grp_rows_inv_case<128>(P, local, smraw); break;
+    case 256: grp_rows_inv_case<256>(P, local, smraw); break;
+    case 512: grp_rows_inv_case<512>(P, local, smraw); break;
+    default: break;
+  }
+}
+
+template <bool INV, int N>
+__device__ __forceinline__ void grp_cols_case(const GrpProb& P, int local, unsigned char* sm) {
+  constexpr int G = 512 / N;  // column blocks per CTA, N threads each
+  const int g = threadIdx.x / N, tid = threadIdx.x - g * N;
+  const int ncb = P.h1 / 16, items = P.nz * 6 * ncb;
+  const int item = local * G + g;
+  const bool live = item < items;
+  const int plane = live ? item / ncb : 0, cblk = live ? item - plane * ncb : 0;
+  cols_v_body<INV, N, 16>(P.spec, P.tw2, P.h1, (size_t)plane, cblk, tid,
+                          reinterpret_cast<float2*>(sm) + (size_t)g * N * 16, live);
+}
+
+template <bool INV> __global__ void __launch_bounds__(512, 2) k_grp_cols(const __grid_constant__ GrpTable tab) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int pi = grp_find(tab, blockIdx.x);
+  const GrpProb& P = tab.p[pi];
+  const int local = (int)blockIdx.x - tab.start[pi];
+  switch (P.n2) {
+    case 64: grp_cols_case<INV, 64>(P, local, smraw); break;
+    case 128: grp_cols_case<INV, 128>(P, local, smraw); break;
+    case 256: grp_cols_case<INV, 256>(P, local, smraw); break;
+    case 512: grp_cols_case<INV, 512>(P, local, smraw); break;
+    default: break;
+  }
 }
 
 }  // namespace
@@ -440,3 +559,51 @@ template bool launch_rows_fwd6_ct<float>(const fvim_ctx*, const float*, int, int
 template bool launch_rows_fwd6_ct<double>(const fvim_ctx*, const double*, int, int, const int*);
 template bool launch_rows_inv6_ct<float>(const fvim_ctx*, float*, float, int, int);
 template bool launch_rows_inv6_ct<double>(const fvim_ctx*, double*, double, int, int);
+
+int launch_grp_rows_fwd(GrpTable& t, cudaStream_t s) {
+  int b = 0;
+  for (int i = 0; i < t.n; ++i) {
+    t.start[i] = b;
+    b += t.p[i].nz * (t.p[i].n2 / (2048 / t.p[i].n1));
+  }
+  t.start[t.n] = b;
+  if (b == 0) return FVIM_OK;
+  smem_attr(k_grp_rows_fwd, kGrpRowsFwdSmem);
+  k_grp_rows_fwd<<<b, 256, kGrpRowsFwdSmem, s>>>(t);
+  FVIM_CUDA_CHECK_LAUNCH();
+  return FVIM_OK;
+}
+
+int launch_grp_rows_inv(GrpTable& t, cudaStream_t s) {
+  int b = 0;
+  for (int i = 0; i < t.n; ++i) {
+    t.start[i] = b;
+    b += t.p[i].nz * (t.p[i].n2 / (1024 / t.p[i].n1));
+  }
+  t.start[t.n] = b;
+  if (b == 0) return FVIM_OK;
+  smem_attr(k_grp_rows_inv, kGrpRowsInvSmem);
+  k_grp_rows_inv<<<b, 128, kGrpRowsInvSmem, s>>>(t);
+  FVIM_CUDA_CHECK_LAUNCH();
+  return FVIM_OK;
+}
+
+int launch_grp_cols(GrpTable& t, bool inverse, cudaStream_t s) {
+  int b = 0;
+  for (int i = 0; i < t.n; ++i) {
+    t.start[i] = b;
+    const int items = t.p[i].nz * 6 * (t.p[i].h1 / 16), per = 512 / t.p[i].n2;
+    b += (items + per - 1) / per;
+  }
+  t.start[t.n] = b;
+  if (b == 0) return FVIM_OK;
+  if (inverse) {
+    smem_attr(k_grp_cols<true>, kGrpColsSmem);
+    k_grp_cols<true><<<b, 512, kGrpColsSmem, s>>>(t);
+  } else {
+    smem_attr(k_grp_cols<false>, kGrpColsSmem);
+    k_grp_cols<false><<<b, 512, kGrpColsSmem, s>>>(t);
+  }
+  FVIM_CUDA_CHECK_LAUNCH();
+  return FVIM_OK;
+}

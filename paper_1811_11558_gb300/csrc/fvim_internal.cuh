@@ -545,6 +545,46 @@ template <typename T> bool launch_cols_conv_ct(const fvim_ctx* c);
 template <typename T> bool launch_rows_fwd6_ct(const fvim_ctx* c, const T* eps_p, int z0, int nzs, const int* zr = nullptr);
 template <typename T> bool launch_rows_inv6_ct(const fvim_ctx* c, T* out, T nq_scale, int z0, int nzs);
 
+// ---- grouped Mindlin apply: FP32 problems of uneven size, one launch per phase ----------
+// One problem of a group: its context's buffers and the constants its kernels need.
+constexpr int kGrpMax = 64;  // problems per group (the table travels as a kernel parameter)
+struct GrpProb {
+  const float* eps;      // eps_p [nz][6][n2][n1]
+  float* out;            // stress or strain [nz][6][n2][n1]
+  float2* spec;          // half spectrum [nz][6][n2][h1]
+  float* nq;             // k1 = N1/2 coefficients [nz][6][n2]
+  const float2* tw1;     // twiddles of N1
+  const float2* tw2;     // twiddles of N2
+  const float* zn;       // depth nodes [nz]
+  int n1, n2, nz, h1, hs;
+  int nch, nchp;         // depth chunks of 4 nodes, and that count rounded up to a power of two
+  int uniform, out_kind;
+  float w1, w2, lam, mu, nu, hz, cut;
+  float nq_scale, scale; // inverse rows: Nyquist factor and 1 / (N1 N2)
+};
+struct GrpTable {
+  int n;                     // problems
+  int start[kGrpMax + 1];    // first CTA of each problem in the launch; start[n] = CTAs
+  GrpProb p[kGrpMax];
+};
+static_assert(sizeof(GrpTable) < 16 * 1024, "the group table is a kernel parameter");
+// the problem of CTA b: the last i with start[i] <= b
+__device__ __forceinline__ int grp_find(const GrpTable& t, int b) {
+  int lo = 0, hi = t.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (t.start[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+// the four kinds of grouped launch (fft_ct.cu, depth.cu); each fills t.start for its own CTA
+// counts.  Problems: FP32, 64 <= N1, N2 <= 512 powers of two, Nz <= 64.
+int launch_grp_rows_fwd(GrpTable& t, cudaStream_t s);
+int launch_grp_cols(GrpTable& t, bool inverse, cudaStream_t s);
+int launch_grp_depth(GrpTable& t, cudaStream_t s);
+int launch_grp_rows_inv(GrpTable& t, cudaStream_t s);
+
 // launch sequences of the entry points (capi.cu), used by the solvers
 // zr: see launch_rows_fwd6; honoured for FVIM_STRAIN output only
 template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, int kind, T* u3, const int* zr = nullptr);

@@ -111,6 +111,7 @@ def lib():
         "fvim_set_material": (i, [vp, d, d, d, d]),
         "fvim_set_stream": (i, [vp, vp]),
         "fvim_apply_mindlin": (i, [vp, vp, vp, i, vp]),
+        "fvim_apply_mindlin_group": (i, [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]),
         "fvim_apply_boussinesq": (i, [vp, vp, vp, vp, i]),
         "fvim_return_map": (i, [vp, vp, vp, vp]),
         "fvim_commit_state": (i, [vp, vp, vp, vp]),
@@ -167,6 +168,30 @@ def _ptr(t, dtype, shape, name):
     if not t.is_contiguous():
         raise ValueError("%s must be contiguous" % name)
     return ctypes.c_void_p(t.data_ptr())
+
+
+GROUP_MAX = 64
+
+
+def apply_mindlin_group(contexts, eps_list, out_list=None, kind="stress"):
+    """fvim_apply_mindlin_group: the Mindlin apply of up to GROUP_MAX FP32 contexts of uneven
+    grid size (power-of-two sides 64..512, 4..64 depth nodes) in one launch per pass, on torch's
+    current stream.  eps_list[i] and out_list[i] have contexts[i].vol_shape; returns out_list."""
+    import torch
+
+    n = len(contexts)
+    if n != len(eps_list) or (out_list is not None and n != len(out_list)):
+        raise ValueError("one input and one output per context")
+    if out_list is None:
+        out_list = [torch.empty(c.vol_shape, dtype=c.dtype, device=e.device) for c, e in zip(contexts, eps_list)]
+    k = FVIM_STRESS if kind == "stress" else FVIM_STRAIN
+    arr = ctypes.c_void_p * max(n, 1)
+    hs = arr(*[c._h.value for c in contexts])
+    ins = arr(*[_ptr(e, c.dtype, c.vol_shape, "eps_p").value for c, e in zip(contexts, eps_list)])
+    outs = arr(*[_ptr(o, c.dtype, c.vol_shape, "out").value for c, o in zip(contexts, out_list)])
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _check(lib().fvim_apply_mindlin_group(hs, n, ins, outs, k, stream), "fvim_apply_mindlin_group")
+    return out_list
 
 
 class Context:

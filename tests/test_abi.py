@@ -56,6 +56,21 @@ def test_create_rejects_bad_grid_without_launching():
     assert L.fvim_apply_mindlin(None, None, None, 0, None) == -1
 
 
+def test_group_apply_checks_arguments_without_gpu():
+    """The grouped apply refuses a bad group size or NULL arrays on the host."""
+    from paper_1811_11558_gb300 import fvim
+
+    L = fvim.lib()
+    arr = (ctypes.c_void_p * 65)()
+    f = L.fvim_apply_mindlin_group
+    assert f(None, 1, arr, arr, 0, None) == -1
+    assert f(arr, 0, arr, arr, 0, None) == -1
+    assert f(arr, 65, arr, arr, 0, None) == -1
+    assert f(arr, 1, arr, arr, 0, None) == -1        # NULL context
+    assert f(arr, 1, arr, arr, 7, None) == -1        # bad output kind
+    assert fvim.GROUP_MAX == 64
+
+
 def test_product_path_does_not_import_oracle():
     """The product package never names the CPU oracle (no fallback)."""
     pkg = os.path.join(ROOT, "paper_1811_11558_gb300")
