@@ -824,10 +824,10 @@ def scaling_metrics(sizes=(4, 8, 16, 32, 64, 128), reps=20):
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each kernel on this
 # workload, from one capture of the current kernels (profiles/ summaries); a kernel missing
-# here, or changed since its capture (rows_inv6: smaller CTAs), reports null.
+# here, or changed since its capture, reports null.
 TRAFFIC_DEPTH_PLAN = (4, 2)  # depth tile plan of that capture (chunk length, CTAs per SM)
-TRAFFIC_BYTES = {"rows_fwd6": 755.1e6, "cols_fwd": 744.2e6, "mindlin_depth": 743.9e6, "cols_inv": 744.4e6,
-                 "rows_inv6": None}
+TRAFFIC_BYTES = {"rows_fwd6": 754.8e6, "cols_fwd": 744.4e6, "mindlin_depth": 744.2e6, "cols_inv": 744.4e6,
+                 "rows_inv6": 756.4e6}
 
 
 

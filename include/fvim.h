@@ -59,7 +59,11 @@ typedef struct fvim_ctx fvim_ctx;
  * fvim_create -- grid, depth nodes, periodic cell and precision (Sec. 3.1, Eq.
  * periodic_cell).
  *   out        receives the new context (host pointer to an opaque handle).
- *   n1, n2     in-plane points; powers of two, 4 <= n1 <= 1024, 2 <= n2 <= 1024.
+ *   n1, n2     in-plane points: powers of two, 4 <= n1 <= 1024, 2 <= n2 <= 1024 (FFTs), or
+ *              a grid with an odd side 3..255 whose other side is odd (3..255) or a power
+ *              of two up to 256 (direct DFTs of Sec. 3.1, e.g. 81 x 81 of App. C.2).  On
+ *              an odd side every mode is in Z^2_N; on an even side the Nyquist mode
+ *              k = N/2 carries no operator term.
  *   nz         depth nodes, 2 <= nz <= 512.
  *   z_nodes    HOST array of nz depths, z_nodes[0] == 0, strictly increasing.
  *   L1, L2     cell lengths (> 0).

@@ -704,14 +704,17 @@ __device__ __forceinline__ void depth_r_body(typename Cx<T>::t* W, Mom<typename 
   __syncthreads();
 
   // surface traction of the full-space field (A = 0 at x3 = 0, + branch complete: the
-  // scan value of chunk 0), cancelled by the image; one thread per column
-  if (ch == 0 && work) {
+  // scan value of chunk 0), cancelled by the image; one thread per column, the last chunk's
+  // (it has no carry from below to fold, so it works while the other chunks fold theirs)
+  const int tch = nch - 1;
+  if (ch == tch && work) {
     V w0[6];
     ld6(w0, W, 0, KT, kt);
+    const Mom<V> U0 = SP[kt];
     Mom<V> Z;
     mom_zero(Z);
     V e0[6];
-    kelvin_strain<T, V>(Z, Up, w0, g.q, nu, mu, e0);
+    kelvin_strain<T, V>(Z, U0, w0, g.q, nu, mu, e0);
     const V trc = cadd(e0[0], e0[2]);
     const V t0 = csub(cscale(e0[4], (T)2 * mu), w0[4]);
     const V t1 = csub(cscale(e0[3], (T)2 * mu), w0[3]);
@@ -722,8 +725,8 @@ __device__ __forceinline__ void depth_r_body(typename Cx<T>::t* W, Mom<typename 
     if (want_u3) {
       // u3(0) = N_inf[w].e3 + B^T(q, 0) t . e3 (rotated frame)
       const T K = (T)1 / ((T)8 * mu * (nu - (T)1));
-      V u = caxpy(cmuli(Up.m[3]), (T)1, Up.m[1]);  // P_33 + i P_q3
-      u = cadd(cscale(u, (T)2 - (T)4 * nu), Up.n);
+      V u = caxpy(cmuli(U0.m[3]), (T)1, U0.m[1]);  // P_33 + i P_q3
+      u = cadd(cscale(u, (T)2 - (T)4 * nu), U0.n);
       u = cscale(u, K);
       V ub = cscale(cmuli(t0), (T)0.5 * ((T)2 * nu - (T)1));
       ub = caxpy(ub, -(nu - (T)1), t2);
@@ -731,7 +734,20 @@ __device__ __forceinline__ void depth_r_body(typename Cx<T>::t* W, Mom<typename 
       surf[(size_t)k2 * h1 + k1] = u;
     }
   }
-  if (want_u3 && ch == 0 && special) surf[(size_t)k2 * h1 + k1] = mk<V>(0, 0);
+  if (want_u3 && ch == tch && special) surf[(size_t)k2 * h1 + k1] = mk<V>(0, 0);
+  // the carry from below folded into the per-node + branch (so that it is not live during
+  // the output loop)
+  if (work && ch + 1 < nch) {
+    const Mom<V> Pin = SP[(ch + 1) * KT + kt];
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+      if (n0 + l < nend) {
+        Mom<V> P = Pin;
+        propP(P, g.q * (zs[e1] - zs[n0 + l]));
+        mom_add(Ploc[l], P);
+      }
+    }
+  }
   __syncthreads();
 
   if (!active) return;
@@ -768,21 +784,8 @@ __device__ __forceinline__ void depth_r_body(typename Cx<T>::t* W, Mom<typename 
   }
 
   // 5. forward over the chunk: - branch from its carry (scan value of the chunk above),
-  //    + branch = own part + carry from below propagated up, image term, epilogue, rotate
+  //    + branch = own part + carry from below (folded above), image term, epilogue, rotate
   //    back, store
-  //    (the carry from below is folded into the per-node + branch first, so that it is not
-  //    live during the output loop)
-  if (ch + 1 < nch) {
-    const Mom<V> Pin = SP[(ch + 1) * KT + kt];
-#pragma unroll
-    for (int l = 0; l < C; ++l) {
-      if (n0 + l < nend) {
-        Mom<V> P = Pin;
-        propP(P, g.q * (zs[e1] - zs[n0 + l]));
-        mom_add(Ploc[l], P);
-      }
-    }
-  }
   Mom<V> A;
   if (ch > 0) A = SA[(ch - 1) * KT + kt];
   else mom_zero(A);

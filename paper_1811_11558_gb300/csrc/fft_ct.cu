@@ -264,6 +264,13 @@ __global__ void __launch_bounds__(256) k_rows_inv6_ct(const typename Cx<T>::t* _
 // the staging area then serves as the FFT exchange area, and the half spectrum leaves as
 // float4 pairs of entries.  (Staging the inverse pass the same way made it slower: 0.254
 // against 0.183 ms at 512 x 512 x 64, from the extra shared-memory traffic and registers.)
+// row stride (floats) of the forward rows' staging area: rows of 64 or 128 points put two or
+// four rows in one warp, which would read the same banks; N / 8 extra floats shift each row
+// by a warp's span of one row
+template <int N> struct StageLd {
+  static constexpr int v = N <= 128 ? N + N / 8 : N;
+};
+
 // forward row FFTs of rows x2b .. x2b + rb - 1 of layer z by the CTA's rb * N / 8 threads;
 // smraw the CTA's staging and exchange area
 template <int N>
@@ -271,13 +278,15 @@ __device__ __forceinline__ void rows_fwd6_v_body(const float* __restrict__ eps_p
                                                  float* __restrict__ nq, const float2* __restrict__ tw, int n2, int rb,
                                                  int z, int x2b, float lam, float mu, unsigned char* smraw) {
   constexpr int T8 = N / 8, LD = RowLayout<float2, N>::LD, H1 = N / 2;
+  constexpr int SLD = StageLd<N>::v;
   const int r = threadIdx.x / T8, t = threadIdx.x % T8;
   const int x2 = x2b + r;
-  float* stg = reinterpret_cast<float*>(smraw);  // [6][rb][N]
+  float* stg = reinterpret_cast<float*>(smraw);  // [6][rb][SLD]
   const int per_c = rb * N / 4;
   for (int i = threadIdx.x; i < 6 * per_c; i += blockDim.x) {
     const int c = i / per_c, j = i - c * per_c;
-    cp_async_16(stg + (size_t)c * rb * N + 4 * j, eps_p + (((size_t)z * 6 + c) * n2 + x2b) * N + 4 * j);
+    const int row = (4 * j) / N, col = 4 * j - row * N;
+    cp_async_16(stg + ((size_t)c * rb + row) * SLD + col, eps_p + (((size_t)z * 6 + c) * n2 + x2b) * N + 4 * j);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -287,7 +296,7 @@ __device__ __forceinline__ void rows_fwd6_v_body(const float* __restrict__ eps_p
     const int x1 = t + m * T8;
     float e[6], w[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) e[c] = stg[((size_t)c * rb + r) * N + x1];
+    for (int c = 0; c < 6; ++c) e[c] = stg[((size_t)c * rb + r) * SLD + x1];
     hooke6_ct(e, w, lam, mu);
     v[0][m] = make_float2(w[0], w[1]);
     v[1][m] = make_float2(w[2], w[3]);
@@ -385,7 +394,7 @@ template <typename T, int N> void rows_fwd_n(const fvim_ctx* c, const T* eps_p, 
   typedef typename Cx<T>::t V;
   const int rb = ct_rows(N, c->n2);
   if constexpr (sizeof(T) == 4 && N >= 64) {
-    const size_t sm = std::max((size_t)rb * 3 * RowLayout<V, N>::LD * sizeof(V), (size_t)6 * rb * N * sizeof(T));
+    const size_t sm = std::max((size_t)rb * 3 * RowLayout<V, N>::LD * sizeof(V), (size_t)6 * rb * StageLd<N>::v * sizeof(T));
     dim3 grid(c->n2 / rb, nzs);
     smem_attr(k_rows_fwd6_v<N>, sm);
     k_rows_fwd6_v<N><<<grid, rb * (N / 8), sm, c->stream>>>((const float*)eps_p, (float2*)c->spec, (float*)c->nq,
@@ -418,7 +427,7 @@ template <typename T, int N> void rows_inv_n(const fvim_ctx* c, T* out, T nq_sca
 // Shapes are chosen so that every N in 64..512 fills the same CTA: forward rows 2048 / N1 rows
 // per CTA (256 threads), inverse rows 1024 / N1 rows (128 threads), columns 512 / N2 blocks of
 // 16 columns (512 threads, N2 threads per block).
-constexpr int kGrpRowsFwdSmem = 2048 * 3 * 9 / 8 * 8;    // >= 6 * 2048 * 4 bytes of staging
+constexpr int kGrpRowsFwdSmem = 2048 * 3 * 9 / 8 * 8;    // = 6 * 2048 * 9 / 8 * 4 bytes of staging
 constexpr int kGrpRowsInvSmem = 1024 * 3 * 9 / 8 * 8;
 constexpr int kGrpColsSmem = 512 * 16 * 8;
 
