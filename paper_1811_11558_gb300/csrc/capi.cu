@@ -30,48 +30,22 @@ namespace {
 template <typename T>
 __global__ void k_return_map(const T* __restrict__ d_eps, const T* __restrict__ sig_n, const T* __restrict__ ep,
                              T* __restrict__ d_eps_p, T* __restrict__ d_ep, size_t nxy, size_t nvox, T lam, T mu,
-                             T sy, T Eh, int* __restrict__ zr, const void* const* d_eps_at) {
-  if (d_eps_at) d_eps = static_cast<const T*>(*d_eps_at);  // input chosen on the device
+                             T sy, T Eh, int* __restrict__ zr) {
   const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= nvox) return;
   const size_t z = v / nxy, xy = v - z * nxy;
   const size_t base = z * 6 * nxy + xy;
-  T de[6], st[6];
+  T de[6], sg[6], dp[6];
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
     de[c] = d_eps[base + c * nxy];
-    st[c] = sig_n[base + c * nxy];
+    sg[c] = sig_n[base + c * nxy];
   }
-  const T tr = de[0] + de[1] + de[2];
+  const T dEp = rmap_voxel(de, sg, ep[v], lam, mu, sy, Eh, dp);
 #pragma unroll
-  for (int c = 0; c < 6; ++c) st[c] += 2 * mu * de[c];
-  st[0] += lam * tr;
-  st[1] += lam * tr;
-  st[2] += lam * tr;
-  const T m = (st[0] + st[1] + st[2]) / (T)3;
-  T s[6] = {st[0] - m, st[1] - m, st[2] - m, st[3], st[4], st[5]};
-  const T nrm2 = s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + 2 * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
-  const T fy = sqrt((T)1.5 * nrm2);
-  const T f = fy - (sy + Eh * ep[v]);
-  T dEp = 0, k = 0;
-  if (f > 0) {
-    dEp = f / ((T)3 * mu + Eh);
-    k = (T)1.5 * dEp / fy;
-  }
-#pragma unroll
-  for (int c = 0; c < 6; ++c) d_eps_p[base + c * nxy] = k * s[c];
+  for (int c = 0; c < 6; ++c) d_eps_p[base + c * nxy] = dp[c];
   if (d_ep) d_ep[v] = dEp;
-  // layer range of the flowing voxels (elsewhere d_eps_p is exactly zero): one pair of
-  // atomics per warp, over the lanes that flow
-  if (zr && dEp > 0) {
-    const unsigned am = __activemask();
-    const int zi = (int)z;
-    const int lo = __reduce_min_sync(am, zi), hi = __reduce_max_sync(am, zi);
-    if ((int)(threadIdx.x & 31) == __ffs(am) - 1) {
-      atomicMin(zr, lo);
-      atomicMax(zr + 1, hi + 1);
-    }
-  }
+  if (zr && dEp > 0) flow_range_note(zr, (int)z);
 }
 
 // S_{n+1} = S_n + increment (Sec. 4.2, update(S)).
@@ -435,7 +409,7 @@ template <typename T> int apply_boussinesq_t(fvim_ctx* c, const T* p, T* u3, T* 
 }
 
 template <typename T>
-int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep, int* zr, const void* const* d_eps_at) {
+int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep, int* zr) {
   const size_t nv = nvox(c);
   const int threads = 256;
   const unsigned blocks = (unsigned)((nv + threads - 1) / threads);
@@ -443,7 +417,7 @@ int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep, int* zr, cons
   const int rc = timed(c, PROF_RETURN_MAP, nk, [&] {
     k_return_map<T><<<blocks, threads, 0, c->stream>>>(d_eps, (const T*)c->st_sig, (const T*)c->st_ep, d_eps_p, d_ep,
                                                        (size_t)c->n1 * c->n2, nv, (T)c->lam, (T)c->mu,
-                                                       (T)c->sigma_y, (T)c->E_h, zr, d_eps_at);
+                                                       (T)c->sigma_y, (T)c->E_h, zr);
     FVIM_CUDA_CHECK_LAUNCH();
     return FVIM_OK;
   });
@@ -470,8 +444,8 @@ template int apply_mindlin_t<float>(fvim_ctx*, const float*, float*, int, float*
 template int apply_mindlin_t<double>(fvim_ctx*, const double*, double*, int, double*, const int*);
 template int apply_boussinesq_t<float>(fvim_ctx*, const float*, float*, float*, int);
 template int apply_boussinesq_t<double>(fvim_ctx*, const double*, double*, double*, int);
-template int return_map_t<float>(fvim_ctx*, const float*, float*, float*, int*, const void* const*);
-template int return_map_t<double>(fvim_ctx*, const double*, double*, double*, int*, const void* const*);
+template int return_map_t<float>(fvim_ctx*, const float*, float*, float*, int*);
+template int return_map_t<double>(fvim_ctx*, const double*, double*, double*, int*);
 template int commit_t<float>(fvim_ctx*, const float*, const float*, const float*);
 template int commit_t<double>(fvim_ctx*, const double*, const double*, const double*);
 

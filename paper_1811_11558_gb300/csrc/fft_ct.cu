@@ -285,8 +285,12 @@ __device__ __forceinline__ void rows_fwd6_v_body(const float* __restrict__ eps_p
   const int per_c = rb * N / 4;
   for (int i = threadIdx.x; i < 6 * per_c; i += blockDim.x) {
     const int c = i / per_c, j = i - c * per_c;
-    const int row = (4 * j) / N, col = 4 * j - row * N;
-    cp_async_16(stg + ((size_t)c * rb + row) * SLD + col, eps_p + (((size_t)z * 6 + c) * n2 + x2b) * N + 4 * j);
+    float* dst = stg + (size_t)c * rb * SLD + 4 * j;
+    if constexpr (SLD != N) {
+      const int row = (4 * j) / N;
+      dst += row * (SLD - N);
+    }
+    cp_async_16(dst, eps_p + (((size_t)z * 6 + c) * n2 + x2b) * N + 4 * j);
   }
   cp_async_wait_all();
   __syncthreads();

@@ -545,6 +545,47 @@ template <typename T> bool launch_cols_conv_ct(const fvim_ctx* c);
 template <typename T> bool launch_rows_fwd6_ct(const fvim_ctx* c, const T* eps_p, int z0, int nzs, const int* zr = nullptr);
 template <typename T> bool launch_rows_inv6_ct(const fvim_ctx* c, T* out, T nq_scale, int z0, int nzs);
 
+// ---- J2 radial return with linear isotropic hardening (Sec. 4.1) at one voxel -----------
+// de: strain increment, sig: stress of the last converged increment, ep: cumulated plastic
+// strain there.  Returns the increment of cumulated plastic strain and writes the plastic
+// strain increment (Voigt order 11, 22, 33, 23, 13, 12; shear entries are tensor components).
+// Shared by the return-map kernel and the fused DF-SANE trial kernel (the same arithmetic).
+template <typename T>
+__device__ __forceinline__ T rmap_voxel(const T (&de)[6], const T (&sig)[6], T ep, T lam, T mu, T sy, T Eh,
+                                        T (&dp)[6]) {
+  T st[6];
+  const T tr = de[0] + de[1] + de[2];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) st[c] = sig[c] + 2 * mu * de[c];
+  st[0] += lam * tr;
+  st[1] += lam * tr;
+  st[2] += lam * tr;
+  const T m = (st[0] + st[1] + st[2]) / (T)3;
+  const T s[6] = {st[0] - m, st[1] - m, st[2] - m, st[3], st[4], st[5]};
+  const T nrm2 = s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + 2 * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
+  const T fy = sqrt((T)1.5 * nrm2);
+  const T f = fy - (sy + Eh * ep);
+  T dEp = 0, k = 0;
+  if (f > 0) {
+    dEp = f / ((T)3 * mu + Eh);
+    k = (T)1.5 * dEp / fy;
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) dp[c] = k * s[c];
+  return dEp;
+}
+
+// layer range of the flowing voxels (elsewhere the plastic increment is exactly zero): one
+// pair of atomics per warp, over the lanes that flow
+__device__ __forceinline__ void flow_range_note(int* zr, int z) {
+  const unsigned am = __activemask();
+  const int lo = __reduce_min_sync(am, z), hi = __reduce_max_sync(am, z);
+  if ((int)(threadIdx.x & 31) == __ffs(am) - 1) {
+    atomicMin(zr, lo);
+    atomicMax(zr + 1, hi + 1);
+  }
+}
+
 // ---- grouped Mindlin apply: FP32 problems of uneven size, one launch per phase ----------
 // One problem of a group: its context's buffers and the constants its kernels need.
 constexpr int kGrpMax = 64;  // problems per group (the table travels as a kernel parameter)
@@ -590,11 +631,8 @@ int launch_grp_rows_inv(GrpTable& t, cudaStream_t s);
 template <typename T> int apply_mindlin_t(fvim_ctx* c, const T* eps_p, T* out, int kind, T* u3, const int* zr = nullptr);
 template <typename T> int apply_boussinesq_t(fvim_ctx* c, const T* p, T* u3, T* vol, int kind);
 // zr (device, two ints) or NULL: receives the layer range [zr[0], zr[1]) of the voxels that
-// flow (reset by the caller to {INT_MAX-ish, 0} first).  d_eps_at (device) or NULL: a device
-// word holding the input pointer, read by the kernel in place of d_eps.
-template <typename T>
-int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep, int* zr = nullptr,
-                 const void* const* d_eps_at = nullptr);
+// flow (reset by the caller to {INT_MAX-ish, 0} first).
+template <typename T> int return_map_t(fvim_ctx* c, const T* d_eps, T* d_eps_p, T* d_ep, int* zr = nullptr);
 template <typename T> int commit_t(fvim_ctx* c, const T* d_eps, const T* d_eps_p, const T* d_ep);
 
 // true when e is an error; the error and the source line that saw it are kept as this host

@@ -803,7 +803,6 @@ template <typename T> struct DF {
 struct DFS {
   const void* px[2];  // the two point buffers: x = px[cur], trial = px[1 - cur]
   void* pF[2];        // their residuals
-  const void* xtr;    // px[1 - cur] (read by the return map)
   double f, nF0, fmax, eta, ap, am, fp, fm, ftrial, best_old, tol_abs, tol_rel, gamma, smin, smax, tmin, tmax;
   double sy[2];
   double hist[32];    // ring of the accepted residuals, hist[i & 31] for i < len
@@ -812,25 +811,39 @@ struct DFS {
 static_assert(sizeof(DFS) <= kDfsBytes, "device DF-SANE state");
 constexpr int kDfsM = 10, kDfsStag = 30;
 
-// trial = x + coef F, coef = -ap sigma (phase 0) or +am sigma (phase 1)
+// trial = x + coef F (coef = -ap sigma in phase 0, +am sigma in phase 1) fused with the return
+// map at the trial point (Sec. 4.1, Sec. 4.3): one
+// thread per voxel writes the trial point, the plastic strain increment and the increment of
+// cumulated plastic strain, and notes the layer range of the flowing voxels
 template <typename T>
-__global__ void k_dfd_trial(const DFS* __restrict__ s, const double* __restrict__ dsig, size_t n) {
+__global__ void k_dfd_trial_rmap(const DFS* __restrict__ s, const double* __restrict__ dsig,
+                                 const T* __restrict__ sig_n, const T* __restrict__ ep, T* __restrict__ d_eps_p,
+                                 T* __restrict__ d_ep, size_t nxy, size_t nvox, T lam, T mu, T sy, T Eh,
+                                 int* __restrict__ zr) {
+  const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nvox) return;
   const int cur = s->cur;
   const T* a = static_cast<const T*>(s->px[cur]);
   const T* b = static_cast<const T*>(s->pF[cur]);
   T* dst = const_cast<T*>(static_cast<const T*>(s->px[1 - cur]));
   const double coef = (s->phase == 0 ? -s->ap : s->am) * *dsig;
-  if constexpr (sizeof(T) == 4) {
-    const float cf = (float)coef;
-    for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < (n >> 2); i += (size_t)gridDim.x * RT) {
-      const float4 x = reinterpret_cast<const float4*>(a)[i];
-      const float4 y = reinterpret_cast<const float4*>(b)[i];
-      reinterpret_cast<float4*>(dst)[i] =
-          make_float4(fmaf(cf, y.x, x.x), fmaf(cf, y.y, x.y), fmaf(cf, y.z, x.z), fmaf(cf, y.w, x.w));
-    }
-  } else {
-    for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) dst[i] = a[i] + coef * b[i];
+  const T cf = (T)coef;
+  const size_t z = v / nxy, xy = v - z * nxy;
+  const size_t base = z * 6 * nxy + xy;
+  T de[6], sg[6], dp[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const size_t i = base + c * nxy;
+    if constexpr (sizeof(T) == 4) de[c] = fmaf(cf, b[i], a[i]);
+    else de[c] = fma(coef, (double)b[i], (double)a[i]);
+    dst[i] = de[c];
+    sg[c] = sig_n[i];
   }
+  const T dEp = rmap_voxel(de, sg, ep[v], lam, mu, sy, Eh, dp);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) d_eps_p[base + c * nxy] = dp[c];
+  d_ep[v] = dEp;
+  if (dEp > 0) flow_range_note(zr, (int)z);
 }
 
 // residual of the trial point into its residual buffer; ||F||^2 into s->ftrial (last block)
@@ -945,7 +958,6 @@ __global__ void k_dfd_decide(DFS* s, double* dsig, cudaGraphConditionalHandle co
     }
     *dsig = sigma;
     s->cur ^= 1;
-    s->xtr = s->px[1 - s->cur];
     s->f = ft;
     s->hist[s->len & 31] = ft;
     s->len += 1;
@@ -1021,14 +1033,16 @@ template <typename T> int build_dfloop(fvim_ctx* c, SolverRT* r, size_t n, int g
     return FVIM_ERR_CUDA;
   }
   DFS* dfs = dfs_dev(c);
-  const void* const* xtr_at =
-      reinterpret_cast<const void* const*>(reinterpret_cast<const char*>(dfs) + offsetof(DFS, xtr));
   auto seq = [&]() -> int {
     int e;
-    k_dfd_trial<T><<<grd, RT, 0, c->stream>>>(dfs, dfs_sigma(c), n);
-    FVIM_CUDA_CHECK_LAUNCH();
     if ((e = reset_flow_range(c))) return e;
-    if ((e = return_map_t<T>(c, nullptr, S<T>(c, V_DEP), S<T>(c, V_EP), flow_range(c), xtr_at))) return e;
+    {
+      const size_t nv = n / 6;
+      k_dfd_trial_rmap<T><<<(unsigned)((nv + 255) / 256), 256, 0, c->stream>>>(
+          dfs, dfs_sigma(c), (const T*)c->st_sig, (const T*)c->st_ep, S<T>(c, V_DEP), S<T>(c, V_EP),
+          (size_t)c->n1 * c->n2, nv, (T)c->lam, (T)c->mu, (T)c->sigma_y, (T)c->E_h, flow_range(c));
+      FVIM_CUDA_CHECK_LAUNCH();
+    }
     if ((e = apply_mindlin_t<T>(c, S<T>(c, V_DEP), S<T>(c, V_TMP), FVIM_STRAIN, nullptr, flow_range(c)))) return e;
     k_dfd_res<T><<<grd, RT, 0, c->stream>>>(dfs, S<T>(c, V_B), S<T>(c, V_TMP), (const double*)c->sv[V_WZ], lgxy, n,
                                             (double*)c->sv[V_PART], dfs_count(c));
@@ -1123,7 +1137,6 @@ int plasticity_t(fvim_ctx* c, const T* dT, T* dE, T* deps_p, T* dep, const fvim_
     hs->px[1] = xt;
     hs->pF[0] = F;
     hs->pF[1] = Ft;
-    hs->xtr = xt;
     hs->f = f;
     hs->nF0 = nF0;
     hs->fmax = f;
