@@ -175,13 +175,17 @@ __device__ __forceinline__ void propA(Mom<V>& A, T a) {
 #pragma unroll
   for (int j = 0; j < 5; ++j) A.m[j] = cscale(A.m[j], E);
 }
+// with E = e^{-a} given
 template <typename T, typename V>
-__device__ __forceinline__ void propP(Mom<V>& P, T a) {
-  const T E = dexp<T>(-a);
+__device__ __forceinline__ void propP_E(Mom<V>& P, T a, T E) {
   const V n0 = nscal(P.m[0], P.m[1], P.m[3], +1);
   P.n = cscale(caxpy(P.n, a, n0), E);
 #pragma unroll
   for (int j = 0; j < 5; ++j) P.m[j] = cscale(P.m[j], E);
+}
+template <typename T, typename V>
+__device__ __forceinline__ void propP(Mom<V>& P, T a) {
+  propP_E(P, a, dexp<T>(-a));
 }
 template <typename V> __device__ __forceinline__ void mom_add(Mom<V>& a, const Mom<V>& b) {
 #pragma unroll
@@ -625,10 +629,32 @@ __device__ __forceinline__ void depth_r_body(typename Cx<T>::t* W, Mom<typename 
       for (int cc = 0; cc < 6; ++cc) W[(i * 6 + cc) * KT + kt] = x[cc];
     }
   }
+  // element coefficients of a uniform grid: the chunk threads of a column share q and h, so
+  // one thread per column evaluates them and the others read them after the barrier.  They
+  // pass through the traction area TR ([KT][6] values of T), which is written again only
+  // after later barriers, when every thread holds them in registers.
+  T* ecs = reinterpret_cast<T*>(TR);
+  if (uniform && ch == 0 && !ghost) {
+    const Elem<T> e = elem_coef<T>(g.q, hz);
+    ecs[0 * KT + kt] = e.E;
+    ecs[1 * KT + kt] = e.a;
+    ecs[2 * KT + kt] = e.hI0mI1;
+    ecs[3 * KT + kt] = e.hI1;
+    ecs[4 * KT + kt] = e.ahI1mI2;
+    ecs[5 * KT + kt] = e.ahI2;
+  }
   __syncthreads();
 
   Elem<T> ec;
-  if (uniform) ec = elem_coef<T>(g.q, hz);
+  if (uniform) {
+    ec.E = ecs[0 * KT + kt];
+    ec.a = ecs[1 * KT + kt];
+    ec.h = hz;
+    ec.hI0mI1 = ecs[2 * KT + kt];
+    ec.hI1 = ecs[3 * KT + kt];
+    ec.ahI1mI2 = ecs[4 * KT + kt];
+    ec.ahI2 = ecs[5 * KT + kt];
+  }
 
   // 3. chunk summaries from zero (- branch at the chunk's last node e1, + branch at its
   //    first node n0); the + branch of every own node stays in registers
@@ -739,12 +765,25 @@ __device__ __forceinline__ void depth_r_body(typename Cx<T>::t* W, Mom<typename 
   // the output loop)
   if (work && ch + 1 < nch) {
     const Mom<V> Pin = SP[(ch + 1) * KT + kt];
+    if (uniform) {
+      // a chunk above the last one is whole (e1 = n0 + C): node n0 + l lies C - l elements
+      // above e1, so its propagator is E^(C - l), built by products
+      T Ek = ec.E;
 #pragma unroll
-    for (int l = 0; l < C; ++l) {
-      if (n0 + l < nend) {
+      for (int l = C - 1; l >= 0; --l) {
         Mom<V> P = Pin;
-        propP(P, g.q * (zs[e1] - zs[n0 + l]));
+        propP_E(P, g.q * hz * (T)(C - l), Ek);
         mom_add(Ploc[l], P);
+        Ek *= ec.E;
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < C; ++l) {
+        if (n0 + l < nend) {
+          Mom<V> P = Pin;
+          propP(P, g.q * (zs[e1] - zs[n0 + l]));
+          mom_add(Ploc[l], P);
+        }
       }
     }
   }
