@@ -370,7 +370,8 @@ template <int N, int CW> void cols_v_launch(const fvim_ctx* c, bool inverse, voi
 template <typename T, int N> void cols_n(const fvim_ctx* c, bool inverse, void* planes, int nplanes, const int* zr) {
   typedef typename Cx<T>::t V;
   if constexpr (sizeof(T) == 4 && N >= 64) {
-    if (N <= 512 && c->h1 % 16 == 0) {
+    // 16 columns per CTA (whole 128-byte rows): N threads, 1024 at N = 1024 (one CTA per SM)
+    if (c->h1 % 16 == 0) {
       cols_v_launch<N, 16>(c, inverse, planes, nplanes, zr);
       return;
     }

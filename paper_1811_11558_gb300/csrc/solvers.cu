@@ -25,7 +25,7 @@ namespace {
 
 constexpr int RT = 256;       // threads of a reduction block
 constexpr int RMAXB = 1024;   // blocks of a reduction grid
-constexpr int NVMAX = 2;      // values reduced per pass
+constexpr int NVMAX = 3;      // values reduced per pass
 constexpr size_t kScalarBlock = 256;  // bytes of the solver's device scalar block (V_PKS)
 constexpr size_t kDfsBytes = 1024;     // bytes of the device DF-SANE state (V_DFS)
 
@@ -813,8 +813,9 @@ constexpr int kDfsM = 10, kDfsStag = 30;
 
 // trial = x + coef F (coef = -ap sigma in phase 0, +am sigma in phase 1) fused with the return
 // map at the trial point (Sec. 4.1, Sec. 4.3): one
-// thread per voxel writes the trial point, the plastic strain increment and the increment of
-// cumulated plastic strain, and notes the layer range of the flowing voxels
+// thread per voxel writes the trial point, the plastic strain increment and (d_ep not NULL)
+// the increment of cumulated plastic strain, and notes the layer range of the flowing voxels.
+// The loop leaves d_ep out: the solve recomputes the return map of its final point.
 template <typename T>
 __global__ void k_dfd_trial_rmap(const DFS* __restrict__ s, const double* __restrict__ dsig,
                                  const T* __restrict__ sig_n, const T* __restrict__ ep, T* __restrict__ d_eps_p,
@@ -842,85 +843,66 @@ __global__ void k_dfd_trial_rmap(const DFS* __restrict__ s, const double* __rest
   const T dEp = rmap_voxel(de, sg, ep[v], lam, mu, sy, Eh, dp);
 #pragma unroll
   for (int c = 0; c < 6; ++c) d_eps_p[base + c * nxy] = dp[c];
-  d_ep[v] = dEp;
+  if (d_ep) d_ep[v] = dEp;
   if (dEp > 0) flow_range_note(zr, (int)z);
 }
 
-// residual of the trial point into its residual buffer; ||F||^2 into s->ftrial (last block)
+// residual of the trial point into its residual buffer, with ||F||^2 into s->ftrial and <s, s>,
+// <s, y> (s = trial - x, y = F(trial) - F(x)) into s->sy (last block).  The trial point is
+// recomputed from x and F with the expression the trial kernel wrote it with (the same
+// values), so it is not read back.
 template <typename T>
-__global__ void k_dfd_res(DFS* s, const T* __restrict__ b, const T* __restrict__ tmp, const double* __restrict__ wz,
-                          int lgxy, size_t n, double* part, unsigned* cnt) {
-  const int cur = s->cur;
-  const T* x = static_cast<const T*>(s->px[1 - cur]);
-  T* F = static_cast<T*>(s->pF[1 - cur]);
-  double v[1] = {0};
-  if constexpr (sizeof(T) == 4) {
-    const size_t n4 = n >> 2;
-    const int lg4 = lgxy - 2;
-    for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n4; i += (size_t)gridDim.x * RT) {
-      const float4 a = reinterpret_cast<const float4*>(x)[i];
-      const float4 c = reinterpret_cast<const float4*>(b)[i];
-      const float4 d = reinterpret_cast<const float4*>(tmp)[i];
-      const float4 f = make_float4(a.x - c.x - d.x, a.y - c.y - d.y, a.z - c.z - d.z, a.w - c.w - d.w);
-      reinterpret_cast<float4*>(F)[i] = f;
-      const float q = f.x * f.x + f.y * f.y + f.z * f.z + f.w * f.w;
-      v[0] += plane_weight(wz, (unsigned)(i >> lg4)) * (double)q;
-    }
-  } else {
-    for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
-      const T f = x[i] - b[i] - tmp[i];
-      F[i] = f;
-      v[0] += plane_weight(wz, (unsigned)(i >> lgxy)) * (double)f * (double)f;
-    }
-  }
-  block_reduce<1>(v, part);
-  if (last_block(cnt)) {
-    double t[1];
-    fin_sum<1>(part, gridDim.x, t);
-    if (threadIdx.x == 0) s->ftrial = t[0];
-    rearm(cnt);
-  }
-}
-
-// <s, s> and <s, y> of the trial (s = trial - x, y = F(trial) - F(x)) into s->sy (last block)
-template <typename T>
-__global__ void k_dfd_sy(DFS* s, const double* __restrict__ wz, int lgxy, size_t n, double* part, unsigned* cnt) {
+__global__ void k_dfd_res_sy(DFS* s, const double* __restrict__ dsig, const T* __restrict__ b,
+                             const T* __restrict__ tmp, const double* __restrict__ wz, int lgxy, size_t n,
+                             double* part, unsigned* cnt) {
   const int cur = s->cur;
   const T* x = static_cast<const T*>(s->px[cur]);
-  const T* xn = static_cast<const T*>(s->px[1 - cur]);
   const T* F = static_cast<const T*>(s->pF[cur]);
-  const T* Fn = static_cast<const T*>(s->pF[1 - cur]);
-  double v[2] = {0, 0};
+  T* Fn = static_cast<T*>(s->pF[1 - cur]);
+  const double coef = (s->phase == 0 ? -s->ap : s->am) * *dsig;
+  double v[3] = {0, 0, 0};
   if constexpr (sizeof(T) == 4) {
+    const float cf = (float)coef;
     const size_t n4 = n >> 2;
     const int lg4 = lgxy - 2;
     for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n4; i += (size_t)gridDim.x * RT) {
       const float4 a = reinterpret_cast<const float4*>(x)[i];
-      const float4 an = reinterpret_cast<const float4*>(xn)[i];
-      const float4 f = reinterpret_cast<const float4*>(F)[i];
-      const float4 fn = reinterpret_cast<const float4*>(Fn)[i];
-      const float s0 = an.x - a.x, s1 = an.y - a.y, s2 = an.z - a.z, s3 = an.w - a.w;
-      const float y0 = fn.x - f.x, y1 = fn.y - f.y, y2 = fn.z - f.z, y3 = fn.w - f.w;
+      const float4 g = reinterpret_cast<const float4*>(F)[i];
+      const float4 c = reinterpret_cast<const float4*>(b)[i];
+      const float4 d = reinterpret_cast<const float4*>(tmp)[i];
+      const float4 t = make_float4(fmaf(cf, g.x, a.x), fmaf(cf, g.y, a.y), fmaf(cf, g.z, a.z), fmaf(cf, g.w, a.w));
+      const float4 f = make_float4(t.x - c.x - d.x, t.y - c.y - d.y, t.z - c.z - d.z, t.w - c.w - d.w);
+      reinterpret_cast<float4*>(Fn)[i] = f;
       const double w = plane_weight(wz, (unsigned)(i >> lg4));
-      v[0] += w * (double)(s0 * s0 + s1 * s1 + s2 * s2 + s3 * s3);
-      v[1] += w * (double)(s0 * y0 + s1 * y1 + s2 * y2 + s3 * y3);
+      const float q = f.x * f.x + f.y * f.y + f.z * f.z + f.w * f.w;
+      v[0] += w * (double)q;
+      const float s0 = t.x - a.x, s1 = t.y - a.y, s2 = t.z - a.z, s3 = t.w - a.w;
+      const float y0 = f.x - g.x, y1 = f.y - g.y, y2 = f.z - g.z, y3 = f.w - g.w;
+      v[1] += w * (double)(s0 * s0 + s1 * s1 + s2 * s2 + s3 * s3);
+      v[2] += w * (double)(s0 * y0 + s1 * y1 + s2 * y2 + s3 * y3);
     }
   } else {
     for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
       const double w = plane_weight(wz, (unsigned)(i >> lgxy));
-      const double a = (double)xn[i] - (double)x[i];
-      const double y = (double)Fn[i] - (double)F[i];
-      v[0] += w * a * a;
-      v[1] += w * a * y;
+      const double xi = (double)x[i], gi = (double)F[i];
+      const double t = fma(coef, gi, xi);
+      const T f = (T)(t - (double)b[i] - (double)tmp[i]);
+      Fn[i] = f;
+      v[0] += w * (double)f * (double)f;
+      const double a = t - xi;
+      const double y = (double)f - gi;
+      v[1] += w * a * a;
+      v[2] += w * a * y;
     }
   }
-  block_reduce<2>(v, part);
+  block_reduce<3>(v, part);
   if (last_block(cnt)) {
-    double t[2];
-    fin_sum<2>(part, gridDim.x, t);
+    double r[3];
+    fin_sum<3>(part, gridDim.x, r);
     if (threadIdx.x == 0) {
-      s->sy[0] = t[0];
-      s->sy[1] = t[1];
+      s->ftrial = r[0];
+      s->sy[0] = r[1];
+      s->sy[1] = r[2];
     }
     rearm(cnt);
   }
@@ -1039,15 +1021,14 @@ template <typename T> int build_dfloop(fvim_ctx* c, SolverRT* r, size_t n, int g
     {
       const size_t nv = n / 6;
       k_dfd_trial_rmap<T><<<(unsigned)((nv + 255) / 256), 256, 0, c->stream>>>(
-          dfs, dfs_sigma(c), (const T*)c->st_sig, (const T*)c->st_ep, S<T>(c, V_DEP), S<T>(c, V_EP),
+          dfs, dfs_sigma(c), (const T*)c->st_sig, (const T*)c->st_ep, S<T>(c, V_DEP), (T*)nullptr,
           (size_t)c->n1 * c->n2, nv, (T)c->lam, (T)c->mu, (T)c->sigma_y, (T)c->E_h, flow_range(c));
       FVIM_CUDA_CHECK_LAUNCH();
     }
     if ((e = apply_mindlin_t<T>(c, S<T>(c, V_DEP), S<T>(c, V_TMP), FVIM_STRAIN, nullptr, flow_range(c)))) return e;
-    k_dfd_res<T><<<grd, RT, 0, c->stream>>>(dfs, S<T>(c, V_B), S<T>(c, V_TMP), (const double*)c->sv[V_WZ], lgxy, n,
-                                            (double*)c->sv[V_PART], dfs_count(c));
-    k_dfd_sy<T><<<grd, RT, 0, c->stream>>>(dfs, (const double*)c->sv[V_WZ], lgxy, n, (double*)c->sv[V_PART],
-                                           dfs_count(c));
+    k_dfd_res_sy<T><<<grd, RT, 0, c->stream>>>(dfs, dfs_sigma(c), S<T>(c, V_B), S<T>(c, V_TMP),
+                                               (const double*)c->sv[V_WZ], lgxy, n, (double*)c->sv[V_PART],
+                                               dfs_count(c));
     k_dfd_decide<<<1, 32, 0, c->stream>>>(dfs, dfs_sigma(c), cond);
     FVIM_CUDA_CHECK_LAUNCH();
     return FVIM_OK;
