@@ -86,8 +86,10 @@ struct SolverRT {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   std::vector<std::pair<GraphKey, cudaGraphExec_t>> cg, df;  // CG batches, residual evaluations
+  std::vector<std::pair<GraphKey, cudaGraphExec_t>> cgw;     // device CG loops (WHILE node)
   cudaGraphExec_t dfloop = nullptr;                          // device DF-SANE loop (WHILE node)
   bool dfloop_failed = false;                                // building it failed: host loop
+  bool cgw_failed = false;                                   // building a CG loop failed: host loop
 };
 constexpr size_t kMaxGraphs = 8;
 
@@ -188,6 +190,53 @@ struct OnSolverStream {
   }
 };
 
+
+// Builds a graph of one WHILE conditional node whose body is what body(cond) launches on
+// c->stream (captured); the body sets the loop condition through cond.  The condition starts
+// at 1, so the body runs at least once.
+template <class F> static int build_while_graph(fvim_ctx* c, F&& body, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  if (FVIM_CU(cudaGraphCreate(&g, 0))) return FVIM_ERR_CUDA;
+  cudaGraphConditionalHandle cond;
+  alignas(cudaGraphNodeParams) unsigned char cpbuf[sizeof(cudaGraphNodeParams)];
+  memset(cpbuf, 0, sizeof(cpbuf));
+  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cpbuf);
+  cudaGraphNode_t node;
+  if (FVIM_CU(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault))) {
+    cudaGraphDestroy(g);
+    return FVIM_ERR_CUDA;
+  }
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (FVIM_CU(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp))) {
+    cudaGraphDestroy(g);
+    return FVIM_ERR_CUDA;
+  }
+  cudaGraph_t bg = cp.conditional.phGraph_out[0];
+  if (FVIM_CU(cudaStreamBeginCaptureToGraph(c->stream, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal))) {
+    cudaGraphDestroy(g);
+    return FVIM_ERR_CUDA;
+  }
+  const int rc = body(cond);
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(c->stream, &captured);
+  if (rc != FVIM_OK || FVIM_CU(ce)) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return rc != FVIM_OK ? rc : FVIM_ERR_CUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (FVIM_CU(ie)) {
+    cudaGetLastError();
+    return FVIM_ERR_CUDA;
+  }
+  *out = ex;
+  return FVIM_OK;
+}
 
 // ---- block reduction of NV doubles into partial[blockIdx.x][NV] -------------------
 template <int NV> __device__ __forceinline__ void block_reduce(double (&v)[NV], double* partial) {
@@ -467,7 +516,7 @@ template <typename T> int conv(fvim_ctx* c, const T* p, T* u) { return apply_bou
 // leave the pressure untouched: the host only reads the flag every few iterations.
 struct PKS {
   double nIc, gbar, G_old, beta, delta, rbar, tau, s, err;
-  int done, it, bad, pad;
+  int done, it, bad, passes;  // passes: WHILE-loop passes of the device CG loop
 };
 static_assert(sizeof(PKS) <= 128, "the DF-SANE step is kept at byte 128 of the scalar block");
 
@@ -685,6 +734,20 @@ __global__ void k_pkd_scale(T* __restrict__ p, const T* __restrict__ pold, size_
   }
 }
 
+// loop condition of the device CG loop (one thread): stop when the iteration logic has set
+// the stop flag, and after max_it passes in any case, so that the loop always ends
+__global__ void k_pkd_cond(PKS* S, int max_it, cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  S->passes += 1;
+  cudaGraphSetConditional(cond, (S->done || S->passes >= max_it) ? 0u : 1u);
+}
+
+// the CG iterations run as one WHILE graph unless FVIM_DEVICE_CG=0 (read on every solve)
+static bool device_cg_enabled() {
+  const char* e = getenv("FVIM_DEVICE_CG");
+  return !(e && e[0] == '0');
+}
+
 template <typename T>
 int elastic_contact_t(fvim_ctx* c, const T* h, double W, T* p, const fvim_opts* o, int* iters, double* err_out) {
   const size_t n = (size_t)c->n1 * c->n2;
@@ -714,25 +777,68 @@ int elastic_contact_t(fvim_ctx* c, const T* h, double W, T* p, const fvim_opts* 
   if (FVIM_CU(cudaMemsetAsync(cnt, 0, sizeof(unsigned), c->stream))) return FVIM_ERR_CUDA;
   PKS* sh = reinterpret_cast<PKS*>(c->h_part + (size_t)RMAXB * NVMAX);  // pinned
   *sh = s0;
-  const int batch = 4;  // iterations issued between two reads of the stop flag
   SolverRT* srt = rt(c);
   const GraphKey key{{h, p, nullptr}, {W, o->cg_tol}, o->cg_max_iter};
-  for (int issued = 0; issued < o->cg_max_iter;) {
+  auto one_iteration = [&]() -> int {
+    int r;
+    if ((r = conv<T>(c, p, u))) return r;
+    k_pkd_stats<T><<<grd, RT, 0, c->stream>>>(u, h, p, n, part, st, cnt);
+    k_pkd_g<T><<<grd, RT, 0, c->stream>>>(u, h, p, g, n, part, st, cnt);
+    k_pkd_dir<T><<<grd, RT, 0, c->stream>>>(g, p, t, n, st);
+    if ((r = conv<T>(c, t, r_))) return r;
+    k_pkd_rsum<T><<<grd, RT, 0, c->stream>>>(r_, p, n, part, st, cnt);
+    k_pkd_dots<T><<<grd, RT, 0, c->stream>>>(g, t, r_, p, n, part, st, cnt);
+    k_pkd_update<T><<<grd, RT, 0, c->stream>>>(p, pold, t, g, n, part, st, cnt, W, dA);
+    k_pkd_scale<T><<<grd, RT, 0, c->stream>>>(p, pold, n, part, st, cnt, W, dA, o->cg_tol, o->cg_max_iter);
+    FVIM_CUDA_CHECK_LAUNCH();
+    return FVIM_OK;
+  };
+  // the iterations as one WHILE graph per (surface, pressure, load, tolerance, cap): one
+  // iteration and the loop condition per pass, one read of the state at the end
+  bool ran_device = false;
+  if (srt && !c->prof && graphs_enabled() && device_cg_enabled() && o->cg_max_iter > 0) {
+    cudaGraphExec_t ex = nullptr;
+    for (auto& e : srt->cgw)
+      if (e.first == key) ex = e.second;
+    if (!ex && !srt->cgw_failed) {
+      const int max_it = o->cg_max_iter;
+      const int b = build_while_graph(
+          c,
+          [&](cudaGraphConditionalHandle cond) -> int {
+            int r;
+            if ((r = one_iteration())) return r;
+            k_pkd_cond<<<1, 32, 0, c->stream>>>(st, max_it, cond);
+            FVIM_CUDA_CHECK_LAUNCH();
+            return FVIM_OK;
+          },
+          &ex);
+      if (b == FVIM_OK) {
+        if (srt->cgw.size() >= kMaxGraphs) {
+          cudaGraphExecDestroy(srt->cgw.front().second);
+          srt->cgw.erase(srt->cgw.begin());
+        }
+        srt->cgw.emplace_back(key, ex);
+      } else {
+        srt->cgw_failed = true;  // the host loop below takes over
+        ex = nullptr;
+        cudaGetLastError();
+      }
+    }
+    if (ex) {
+      if (FVIM_CU(cudaGraphLaunch(ex, c->stream)) ||
+          FVIM_CU(cudaMemcpyAsync(sh, st, sizeof(PKS), cudaMemcpyDeviceToHost, c->stream)) ||
+          FVIM_CU(cudaStreamSynchronize(c->stream)))
+        return FVIM_ERR_CUDA;
+      ran_device = true;
+    }
+  }
+  const int batch = 4;  // iterations issued between two reads of the stop flag
+  for (int issued = 0; !ran_device && issued < o->cg_max_iter;) {
     const int nb = std::min(batch, o->cg_max_iter - issued);
     auto iterations = [&]() -> int {
       int r;
-      for (int b = 0; b < nb; ++b) {
-        if ((r = conv<T>(c, p, u))) return r;
-        k_pkd_stats<T><<<grd, RT, 0, c->stream>>>(u, h, p, n, part, st, cnt);
-        k_pkd_g<T><<<grd, RT, 0, c->stream>>>(u, h, p, g, n, part, st, cnt);
-        k_pkd_dir<T><<<grd, RT, 0, c->stream>>>(g, p, t, n, st);
-        if ((r = conv<T>(c, t, r_))) return r;
-        k_pkd_rsum<T><<<grd, RT, 0, c->stream>>>(r_, p, n, part, st, cnt);
-        k_pkd_dots<T><<<grd, RT, 0, c->stream>>>(g, t, r_, p, n, part, st, cnt);
-        k_pkd_update<T><<<grd, RT, 0, c->stream>>>(p, pold, t, g, n, part, st, cnt, W, dA);
-        k_pkd_scale<T><<<grd, RT, 0, c->stream>>>(p, pold, n, part, st, cnt, W, dA, o->cg_tol, o->cg_max_iter);
-        FVIM_CUDA_CHECK_LAUNCH();
-      }
+      for (int b = 0; b < nb; ++b)
+        if ((r = one_iteration())) return r;
       return FVIM_OK;
     };
     // a full batch is one captured graph per (surface, pressure, load, tolerance)
@@ -990,66 +1096,26 @@ inline unsigned* dfs_count(fvim_ctx* c) { return reinterpret_cast<unsigned*>(sta
 // The WHILE graph of the device DF-SANE loop (built once per context; the material constants
 // and the buffers are fixed, the points and the scalars live in the device state).
 template <typename T> int build_dfloop(fvim_ctx* c, SolverRT* r, size_t n, int grd, int lgxy) {
-  cudaGraph_t g = nullptr;
-  if (FVIM_CU(cudaGraphCreate(&g, 0))) return FVIM_ERR_CUDA;
-  cudaGraphConditionalHandle cond;
-  alignas(cudaGraphNodeParams) unsigned char cpbuf[sizeof(cudaGraphNodeParams)];
-  memset(cpbuf, 0, sizeof(cpbuf));
-  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cpbuf);
-  cudaGraphNode_t node;
-  if (FVIM_CU(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault))) {
-    cudaGraphDestroy(g);
-    return FVIM_ERR_CUDA;
-  }
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = cond;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  if (FVIM_CU(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp))) {
-    cudaGraphDestroy(g);
-    return FVIM_ERR_CUDA;
-  }
-  cudaGraph_t body = cp.conditional.phGraph_out[0];
-  if (FVIM_CU(cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal))) {
-    cudaGraphDestroy(g);
-    return FVIM_ERR_CUDA;
-  }
   DFS* dfs = dfs_dev(c);
-  auto seq = [&]() -> int {
-    int e;
-    if ((e = reset_flow_range(c))) return e;
-    {
-      const size_t nv = n / 6;
-      k_dfd_trial_rmap<T><<<(unsigned)((nv + 255) / 256), 256, 0, c->stream>>>(
-          dfs, dfs_sigma(c), (const T*)c->st_sig, (const T*)c->st_ep, S<T>(c, V_DEP), (T*)nullptr,
-          (size_t)c->n1 * c->n2, nv, (T)c->lam, (T)c->mu, (T)c->sigma_y, (T)c->E_h, flow_range(c));
-      FVIM_CUDA_CHECK_LAUNCH();
-    }
-    if ((e = apply_mindlin_t<T>(c, S<T>(c, V_DEP), S<T>(c, V_TMP), FVIM_STRAIN, nullptr, flow_range(c)))) return e;
-    k_dfd_res_sy<T><<<grd, RT, 0, c->stream>>>(dfs, dfs_sigma(c), S<T>(c, V_B), S<T>(c, V_TMP),
-                                               (const double*)c->sv[V_WZ], lgxy, n, (double*)c->sv[V_PART],
-                                               dfs_count(c));
-    k_dfd_decide<<<1, 32, 0, c->stream>>>(dfs, dfs_sigma(c), cond);
-    FVIM_CUDA_CHECK_LAUNCH();
-    return FVIM_OK;
-  };
-  const int rc = seq();
-  cudaGraph_t out = nullptr;
-  const cudaError_t ce = cudaStreamEndCapture(c->stream, &out);
-  if (rc != FVIM_OK || FVIM_CU(ce)) {
-    cudaGetLastError();
-    cudaGraphDestroy(g);
-    return rc != FVIM_OK ? rc : FVIM_ERR_CUDA;
-  }
-  cudaGraphExec_t ex = nullptr;
-  const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
-  cudaGraphDestroy(g);
-  if (FVIM_CU(ie)) {
-    cudaGetLastError();
-    return FVIM_ERR_CUDA;
-  }
-  r->dfloop = ex;
-  return FVIM_OK;
+  return build_while_graph(
+      c,
+      [&](cudaGraphConditionalHandle cond) -> int {
+        int e;
+        if ((e = reset_flow_range(c))) return e;
+        const size_t nv = n / 6;
+        k_dfd_trial_rmap<T><<<(unsigned)((nv + 255) / 256), 256, 0, c->stream>>>(
+            dfs, dfs_sigma(c), (const T*)c->st_sig, (const T*)c->st_ep, S<T>(c, V_DEP), (T*)nullptr,
+            (size_t)c->n1 * c->n2, nv, (T)c->lam, (T)c->mu, (T)c->sigma_y, (T)c->E_h, flow_range(c));
+        FVIM_CUDA_CHECK_LAUNCH();
+        if ((e = apply_mindlin_t<T>(c, S<T>(c, V_DEP), S<T>(c, V_TMP), FVIM_STRAIN, nullptr, flow_range(c)))) return e;
+        k_dfd_res_sy<T><<<grd, RT, 0, c->stream>>>(dfs, dfs_sigma(c), S<T>(c, V_B), S<T>(c, V_TMP),
+                                                   (const double*)c->sv[V_WZ], lgxy, n, (double*)c->sv[V_PART],
+                                                   dfs_count(c));
+        k_dfd_decide<<<1, 32, 0, c->stream>>>(dfs, dfs_sigma(c), cond);
+        FVIM_CUDA_CHECK_LAUNCH();
+        return FVIM_OK;
+      },
+      &r->dfloop);
 }
 
 template <typename T>
@@ -1300,6 +1366,7 @@ void solver_drop_graphs(fvim_ctx* c) {
   if (!r) return;
   drop(r->cg);
   drop(r->df);
+  drop(r->cgw);
   if (r->dfloop) cudaGraphExecDestroy(r->dfloop);
   r->dfloop = nullptr;
 }

@@ -58,6 +58,38 @@ def test_elastic_contact_parity(prec, n):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_device_cg_loop_equals_host_loop(prec, monkeypatch):
+    """The contact CG as one WHILE graph (one read of its state per solve) and as host-driven
+    batches of captured iterations run the same kernels: same pressure bit for bit, same
+    iteration count, also with an iteration cap that stops it early and inside Algorithm 1."""
+    torch = require_gpu()
+    n = 64
+    z = inputs.uniform_depth(4, 0.1)
+    h = inputs.hertz_profile(n, n, 1.0, 1.0, R)
+    W = 4.7916e-3
+    res = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("FVIM_DEVICE_CG", mode)
+        ctx = _ctx(n, z, prec, sigma_y=0.05 * E / (1 - NU * NU), E_h=0.1 * E)
+        dt = ctx.dtype
+        hd = to_dev(torch, h, dt)
+        out = []
+        for cap in (500, 7):
+            p = torch.zeros(ctx.surf_shape, dtype=dt, device="cuda")
+            it, err = ctx.elastic_contact(hd, W, p, ctx.default_opts(cg_max_iter=cap), allow_not_converged=True)
+            out.append((it, err, p.cpu().numpy()))
+        p = torch.zeros(ctx.surf_shape, dtype=dt, device="cuda")
+        rep = ctx.solve_contact(hd, [W / 2, W], p, ctx.default_opts(), allow_not_converged=True)
+        out.append((rep["cg_iters"], rep["alg1_iters"], p.cpu().numpy()))
+        res[mode] = out
+        ctx.close()
+    for a, b in zip(res["1"], res["0"]):
+        assert a[0] == b[0] and a[1] == b[1]
+        assert np.array_equal(a[2], b[2])
+    assert res["1"][1][0] == 7                 # the cap ends the loop
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_plasticity_parity(prec):
     torch = require_gpu()
     n, nz = 16, 8
