@@ -50,18 +50,67 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    """SM clock and clock-event (throttle) reasons during the timed region: read through NVML
+    (read-only queries, one sample per millisecond from a host thread) where the library
+    loads, else nvidia-smi every 100 ms."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # clock-event reason bits of NVML's public API
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
+            "hw_power_brake_slowdown": 0x80}
 
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
         self.f = None
+        self.nvml = None
+        self.thread = None
+        self.samples = []
+
+    def _nvml_open(self):
+        import ctypes
+
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None
+        h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.idx), ctypes.byref(h)) != 0:
+            return None
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        lib.nvmlDeviceGetMaxClockInfo(h, ctypes.c_int(1), ctypes.byref(mx))  # NVML_CLOCK_SM
+        return lib, h, reasons, mx.value
+
+    def _poll(self):
+        import ctypes
+
+        lib, h, reasons, _ = self.nvml
+        sm, r = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self.stop_flag.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, ctypes.c_int(1), ctypes.byref(sm)) == 0 and \
+                    reasons(h, ctypes.byref(r)) == 0:
+                self.samples.append((sm.value, r.value))
+            time.sleep(0.001)
 
     def start(self):
+        import threading
+
+        try:
+            self.nvml = self._nvml_open()
+        except Exception:
+            self.nvml = None
+        if self.nvml is not None:
+            self.stop_flag = threading.Event()
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            t_end = time.perf_counter() + 0.5
+            while not self.samples and self.thread.is_alive() and time.perf_counter() < t_end:
+                time.sleep(0.001)  # the first sample before the region
+            self.samples.clear()
+            return
         try:
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
@@ -71,6 +120,15 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            self.stop_flag.set()
+            self.thread.join(timeout=5)
+            if not self.samples:
+                return None
+            sm = [a for a, _ in self.samples]
+            reasons = sorted(nm for nm, bit in self.BITS.items() if any(b & bit for _, b in self.samples))
+            return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(self.nvml[3]), "reasons": reasons,
+                    "samples": len(sm), "source": "nvml, 1 ms"}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -98,7 +156,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi, 100 ms"}
 
 
 def max_over_ranks(x, dist=None, device="cpu"):
@@ -338,47 +396,56 @@ def hertz_case():
 def solve_metrics(repeats=3, served=32, slots=16):
     """Contact solves/s of Algorithm 1 (relaxation 0.5) on the Hertz case: FP64 and FP32 one
     solve at a time, and FP32 served (requests admitted as slots free up, solves overlapping on
-    the device), with p50/p99 latency and the FP32 error against the FP64 solution."""
+    the device), with p50/p99 latency and the FP32 error against the FP64 solution; first with
+    the listing's relaxation order, then (``relax_carried``) with the relaxed value carried
+    between coupling iterations."""
     import torch
 
     from paper_1811_11558_gb300 import Context
     from paper_1811_11558_gb300.serve import Request, Server, percentiles
 
     c = hertz_case()
-    out = {"workload": "hertz_32x32x16_5inc", "relax": 0.5}
-    press = {}
-    for prec in ("fp64", "fp32"):
-        ctx = Context(c["n"], c["n"], c["z"], 1.0, 1.0, precision=prec, E=E, nu=NU, sigma_y=c["sigma_y"],
-                      E_h=c["E_h"])
-        ctx.autotune()
-        h = torch.from_numpy(c["h"]).to("cuda", ctx.dtype)
-        p = torch.empty(ctx.surf_shape, dtype=ctx.dtype, device="cuda")
-        opts = ctx.default_opts(relax=0.5, max_iter=400)
-        times, rep = [], None
-        for r in range(repeats + 1):
-            ctx.reset_state()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            rep = ctx.solve_contact(h, c["loads"], p, opts)
-            times.append(time.perf_counter() - t0)
-        t = float(np.median(times[1:]))
-        press[prec] = p.cpu().numpy().astype(np.float64)
-        out[prec + "_plain"] = {"solves_per_s": 1.0 / t, "ms_per_solve": 1e3 * t, "tol": opts.tol,
-                                "alg1_iters": rep["alg1_iters"], "contact_area": rep["contact_area"][-1]}
-        ctx.close()
-    srv = Server(slots=slots)
-    reqs = [Request(i, c["n"], c["z"], c["h"], c["loads"], precision="fp32", E=E, nu=NU, sigma_y=c["sigma_y"],
-                    E_h=c["E_h"], opts={"relax": 0.5, "max_iter": 400}) for i in range(served)]
-    srv.prepare(reqs[:1])                       # the grid's tuned tile plan
-    srv.run(reqs[:slots])                       # warm the context pool
-    res, wall = srv.run(reqs)
-    lat = percentiles([r.latency for r in res])
-    out["fp32_served"] = {"solves_per_s": served / wall, "slots": slots, "requests": served,
-                          "p50_ms": 1e3 * lat[50], "p99_ms": 1e3 * lat[99], "arrivals": "all at t = 0"}
-    out["fp32_vs_fp64"] = {
-        "pressure_rel_l2": float(np.linalg.norm(press["fp32"] - press["fp64"]) / np.linalg.norm(press["fp64"])),
-        "area_diff": float(abs((press["fp32"] > 0).mean() - (press["fp64"] > 0).mean()))}
-    out["served_over_fp64_plain"] = out["fp32_served"]["solves_per_s"] / out["fp64_plain"]["solves_per_s"]
+
+    def run(mode):
+        out = {"workload": "hertz_32x32x16_5inc", "relax": 0.5, "relax_mode": ("literal", "carried")[mode]}
+        press = {}
+        for prec in ("fp64", "fp32"):
+            ctx = Context(c["n"], c["n"], c["z"], 1.0, 1.0, precision=prec, E=E, nu=NU, sigma_y=c["sigma_y"],
+                          E_h=c["E_h"])
+            ctx.autotune()
+            h = torch.from_numpy(c["h"]).to("cuda", ctx.dtype)
+            p = torch.empty(ctx.surf_shape, dtype=ctx.dtype, device="cuda")
+            opts = ctx.default_opts(relax=0.5, max_iter=400, relax_mode=mode)
+            times, rep = [], None
+            for r in range(repeats + 1):
+                ctx.reset_state()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rep = ctx.solve_contact(h, c["loads"], p, opts)
+                times.append(time.perf_counter() - t0)
+            t = float(np.median(times[1:]))
+            press[prec] = p.cpu().numpy().astype(np.float64)
+            out[prec + "_plain"] = {"solves_per_s": 1.0 / t, "ms_per_solve": 1e3 * t, "tol": opts.tol,
+                                    "alg1_iters": rep["alg1_iters"], "contact_area": rep["contact_area"][-1]}
+            ctx.close()
+        srv = Server(slots=slots)
+        reqs = [Request(i, c["n"], c["z"], c["h"], c["loads"], precision="fp32", E=E, nu=NU, sigma_y=c["sigma_y"],
+                        E_h=c["E_h"], opts={"relax": 0.5, "max_iter": 400, "relax_mode": mode})
+                for i in range(served)]
+        srv.prepare(reqs[:1])                       # the grid's tuned tile plan
+        srv.run(reqs[:slots])                       # warm the context pool
+        res, wall = srv.run(reqs)
+        lat = percentiles([r.latency for r in res])
+        out["fp32_served"] = {"solves_per_s": served / wall, "slots": slots, "requests": served,
+                              "p50_ms": 1e3 * lat[50], "p99_ms": 1e3 * lat[99], "arrivals": "all at t = 0"}
+        out["fp32_vs_fp64"] = {
+            "pressure_rel_l2": float(np.linalg.norm(press["fp32"] - press["fp64"]) / np.linalg.norm(press["fp64"])),
+            "area_diff": float(abs((press["fp32"] > 0).mean() - (press["fp64"] > 0).mean()))}
+        out["served_over_fp64_plain"] = out["fp32_served"]["solves_per_s"] / out["fp64_plain"]["solves_per_s"]
+        return out
+
+    out = run(0)
+    out["relax_carried"] = run(1)
     return out
 
 
@@ -387,7 +454,7 @@ def rough_metrics(n=1024, nz=32, depth=0.05, seed=1813, n_inc=10, cap=120):
     for 4 <= |k| < 8, power law to k_s = 64, rms slope 0.1), nz uniform nodes to the given
     depth, sigma_y = 0.05 E*, E_h = 0.1 E, relaxation 0.3.  (a) the paper's rough-surface load
     W = 1e-3 E x rms slope in five increments (Algorithm 1 in the listing's order, tolerance
-    1e-6); (b) the load of a 10 % elastic contact fraction, ramped in n_inc equal increments (the
+    1e-6), and the same with the relaxed value carried between coupling iterations; (b) the load of a 10 % elastic contact fraction, ramped in n_inc equal increments (the
     paper's remedy for the coupling's slow convergence on rough surfaces: small load steps),
     Algorithm 1 with the relaxed value carried between iterations (relax_mode 1), tolerance 1e-7,
     capped at ``cap`` iterations per increment.  Both are timed as whole solves; the status says whether every increment
@@ -417,6 +484,18 @@ def rough_metrics(n=1024, nz=32, depth=0.05, seed=1813, n_inc=10, cap=120):
                          "solves_per_s": 1.0 / t, "ms_per_solve": 1e3 * t, "alg1_iters": rep["alg1_iters"],
                          "alg1_error": rep["alg1_error"], "contact_area": rep["contact_area"][-1],
                          "residual_evals": rep["residual_evals"], "cg_iters": rep["cg_iters"]}
+    # the same solve with the relaxed value carried between coupling iterations
+    optc = ctx.default_opts(relax=0.3, max_iter=cap, tol=1e-6, relax_mode=1)
+    ctx.reset_state()
+    p.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rep = ctx.solve_contact(hd, [W * (k + 1) / 5 for k in range(5)], p, optc, allow_not_converged=True)
+    t = time.perf_counter() - t0
+    out["paper_load_carried"] = {"W": W, "increments": 5, "relax": 0.3, "relax_mode": "carried", "tol": optc.tol,
+                                 "status": rep["status"], "solves_per_s": 1.0 / t, "ms_per_solve": 1e3 * t,
+                                 "alg1_iters": rep["alg1_iters"], "alg1_error": rep["alg1_error"],
+                                 "contact_area": rep["contact_area"][-1]}
     # load of a 10 % elastic contact fraction (area ~ linear in the load at small fractions)
     p.zero_()
     ctx.elastic_contact(hd, 5e-3, p, ctx.default_opts())
