@@ -417,7 +417,8 @@ template <typename T, int N> void rows_fwd_n(const fvim_ctx* c, const T* eps_p, 
 template <typename T, int N> void rows_inv_n(const fvim_ctx* c, T* out, T nq_scale, int z0, int nzs) {
   typedef typename Cx<T>::t V;
   int rb = ct_rows(N, c->n2);
-  if (sizeof(T) == 4 && rb >= 4) rb /= 2;  // smaller CTAs: 5 instead of 2 per SM at 101 registers
+  // smaller CTAs in FP32 (128 threads at N = 512 and 1024): 5 instead of 2 per SM at ~100 registers
+  if (sizeof(T) == 4 && (rb >= 4 || N >= 1024)) rb = std::max(1, rb / 2);
   const size_t smem = (size_t)rb * 3 * RowLayout<V, N>::LD * sizeof(V);
   dim3 grid(c->n2 / rb, nzs);
   const T scale = (T)(1.0 / ((double)N * (double)c->n2));
