@@ -291,9 +291,10 @@ const char* fvim_profile_name(int slot);
  * partials summed in block order by the last block to finish), so repeated runs give
  * bitwise identical results.  The iteration logic runs on the device: the contact CG's
  * scalars (step, conjugation, rigid shift, load scaling, stop test) are kept in device
- * memory and the host reads one small status block per batch of iterations; DF-SANE's
- * line search runs inside one captured CUDA graph (a device-side loop) and the host
- * reads its state once per solve.  Every loop has an iteration cap.
+ * memory; the CG iterations and DF-SANE's iterations with its line search each run inside
+ * one captured CUDA graph (a device-side WHILE loop), and the host reads their state once
+ * per solve (batches of captured CG iterations with one status read per batch when
+ * FVIM_DEVICE_CG=0).  Every loop has an iteration cap, enforced on the device.
  * ------------------------------------------------------------------------------------ */
 #define FVIM_MAX_INCREMENTS 64
 

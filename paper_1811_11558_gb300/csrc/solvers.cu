@@ -7,9 +7,10 @@
 // Vectors stay on the device in the context's precision.  Every reduction is a grid of
 // fixed blocks writing FP64 partial sums that the last block to finish adds in block order
 // (the host-loop fallbacks add them on the host in the same order), so results are bitwise
-// reproducible.  The CG's scalar logic runs in single-block finisher kernels and the host
-// reads one status block per batch of captured iterations; DF-SANE's line search runs as a
-// device-side loop (a WHILE node of one captured graph).  Every loop is capped.
+// reproducible.  The CG's scalar logic runs in single-block finisher kernels; the CG
+// iterations and DF-SANE's iterations with its line search each run as a device-side loop (a
+// WHILE node of one captured graph) whose state the host reads once per solve (batches of
+// captured CG iterations with one status read each as the fallback).  Every loop is capped.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
