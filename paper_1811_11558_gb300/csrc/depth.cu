@@ -662,7 +662,34 @@ __device__ __forceinline__ void depth_r_body(typename Cx<T>::t* W, Mom<typename 
   Mom<V> Ta, Up;
   mom_zero(Ta);
   mom_zero(Up);
-  if (work) {
+  if (work && uniform) {
+    // the two recursions are independent chains: advance them together (same steps in the
+    // same order per chain as below, so the same values)
+    V wa[6], wb[6];
+    ld6(wa, W, n0, KT, kt);
+    ld6(wb, W, e1, KT, kt);
+#pragma unroll
+    for (int st = 0; st < C; ++st) {
+      const int la = st, lp = C - 1 - st;
+      if (n0 + la < e1) {
+        V wn[6];
+        ld6(wn, W, n0 + la + 1, KT, kt);
+        stepA(Ta, ec, wa, wn);
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) wa[cc] = wn[cc];
+      }
+      if (n0 + lp < e1) {
+        V wc[6];
+        ld6(wc, W, n0 + lp, KT, kt);
+        stepP(Up, ec, wc, wb);
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) wb[cc] = wc[cc];
+        Ploc[lp] = Up;
+      } else {
+        mom_zero(Ploc[lp]);
+      }
+    }
+  } else if (work) {
     V wa[6];
     ld6(wa, W, n0, KT, kt);
 #pragma unroll
