@@ -614,7 +614,10 @@ __device__ __forceinline__ void depth_r_body(typename Cx<T>::t* W, Mom<typename 
 
   // 2. (eps_p input: w = C:eps_p per mode) rotate own nodes into the (q, p, 3) frame
   if (active) {
-    for (int i = n0; i < nend; ++i) {
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+      const int i = n0 + l;
+      if (i >= nend) break;
       V x[6];
       ld6(x, W, i, KT, kt);
       if (EIN) {
