@@ -51,3 +51,30 @@ def test_rough_surfaces_of_the_batch_have_the_stated_slope():
         g = np.fft.fft2(h)
         slope = np.sqrt(np.sum(((2 * np.pi) ** 2) * (K1 ** 2 + K2 ** 2) * np.abs(g) ** 2)) / (n * n)
         assert abs(slope - 0.1) < 1e-9
+
+
+def test_reference_arm_line_keeps_the_contract():
+    """`bench.py --impl reference` (the oracle on the host cores, no GPU) prints one JSON line
+    with the GPU arm's metric and unit, a measured step time that the run can account for, and
+    the extrapolated one-core apply time beside it."""
+    import json
+    import subprocess
+
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True and d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 3
+    assert 0 < d["ms_per_step"] < 600e3
+    assert d["ms_per_apply_one_core_extrapolated"] > d["ms_per_step"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_batch_runs_every_problem_with_the_carried_relaxation():
+    for pb in bench.batch_problems(64, 1814):
+        assert pb["relax_mode"] == 1
+        assert pb["relax"] == (0.3 if pb["rough"] else 0.5)
