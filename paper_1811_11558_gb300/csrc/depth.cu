@@ -588,6 +588,28 @@ template <typename V> __device__ __forceinline__ void ld6(V (&w)[6], const V* W,
   for (int cc = 0; cc < 6; ++cc) w[cc] = W[(node * 6 + cc) * KT + kt];
 }
 
+// Per-column quantities that do not depend on the tile, computed while its copy is in flight:
+// the mode geometry (every thread) and, on a uniform grid, the element integrals (one thread
+// per column, written to the traction area TR as [6][KT] values of T for the body to read
+// after its first barrier).
+template <typename T, int KT>
+__device__ __forceinline__ ModeGeom<T> depth_prep(typename Cx<T>::t* TR, int tid, int kblk, int k2, bool ghost,
+                                                  int n1, int n2, int hs, T w1, T w2, int uniform, T hz) {
+  const int kt = tid & (KT - 1);
+  const ModeGeom<T> g = mode_geom<T>(kblk * KT + kt, k2, n1, n2, hs, w1, w2);
+  if (uniform && tid < KT && !ghost) {
+    T* ecs = reinterpret_cast<T*>(TR);
+    const Elem<T> e = elem_coef<T>(g.q, hz);
+    ecs[0 * KT + kt] = e.E;
+    ecs[1 * KT + kt] = e.a;
+    ecs[2 * KT + kt] = e.hI0mI1;
+    ecs[3 * KT + kt] = e.hI1;
+    ecs[4 * KT + kt] = e.ahI1mI2;
+    ecs[5 * KT + kt] = e.ahI2;
+  }
+  return g;
+}
+
 // Steps 2-5 of the register depth kernel on a tile already in shared memory: W[nz][6][KT]
 // (the tile), SA / SP [>= nch][KT] (chunk moments), TR[KT][3], zs[nz].  tid = ch * KT + kt is
 // the thread's place in the tile, kblk the tile's block of KT k1 columns.  A ghost tile (a
@@ -598,13 +620,12 @@ __device__ __forceinline__ void depth_r_body(typename Cx<T>::t* W, Mom<typename 
                                              int kblk, int k2, bool ghost, typename Cx<T>::t* __restrict__ spec,
                                              typename Cx<T>::t* __restrict__ surf, int nz, int n1, int n2, int hs,
                                              int h1, int nch, T w1, T w2, T lam, T mu, T nu, int out_kind,
-                                             int want_u3, int uniform, T hz, T cut) {
+                                             int want_u3, int uniform, T hz, T cut, const ModeGeom<T> g) {
   typedef typename Cx<T>::t V;
   const int kt = tid & (KT - 1);
   const int ch = tid / KT;
   const int k1 = kblk * KT + kt;
   const size_t plane = (size_t)n2 * h1;
-  const ModeGeom<T> g = mode_geom<T>(k1, k2, n1, n2, hs, w1, w2);
   const bool special = g.zero || g.nyq;
   const int n0 = ch * C;
   const int nend = min(n0 + C, nz);
@@ -633,19 +654,10 @@ __device__ __forceinline__ void depth_r_body(typename Cx<T>::t* W, Mom<typename 
     }
   }
   // element coefficients of a uniform grid: the chunk threads of a column share q and h, so
-  // one thread per column evaluates them and the others read them after the barrier.  They
-  // pass through the traction area TR ([KT][6] values of T), which is written again only
-  // after later barriers, when every thread holds them in registers.
-  T* ecs = reinterpret_cast<T*>(TR);
-  if (uniform && ch == 0 && !ghost) {
-    const Elem<T> e = elem_coef<T>(g.q, hz);
-    ecs[0 * KT + kt] = e.E;
-    ecs[1 * KT + kt] = e.a;
-    ecs[2 * KT + kt] = e.hI0mI1;
-    ecs[3 * KT + kt] = e.hI1;
-    ecs[4 * KT + kt] = e.ahI1mI2;
-    ecs[5 * KT + kt] = e.ahI2;
-  }
+  // one thread per column evaluated them (depth_prep, before this barrier) and the others read
+  // them here.  They pass through the traction area TR ([6][KT] values of T), which is written
+  // again only after later barriers, when every thread holds them in registers.
+  const T* ecs = reinterpret_cast<const T*>(TR);
   __syncthreads();
 
   Elem<T> ec;
@@ -924,6 +936,7 @@ __global__ void __launch_bounds__(256, MB) k_mindlin_depth_r(typename Cx<T>::t* 
   const int k2 = blockIdx.y;
   const size_t plane = (size_t)n2 * h1;
   const size_t colofs = (size_t)k2 * h1 + blockIdx.x * KT;
+  ModeGeom<T> g;
 
   // 1. load the tile and the depth nodes (layers outside zr hold no input: their spectrum was
   //    not computed and reads as zero).  With a tensor map (tma_rows > 0): one thread issues
@@ -952,6 +965,7 @@ __global__ void __launch_bounds__(256, MB) k_mindlin_depth_r(typename Cx<T>::t* 
       }
     }
     for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];
+    g = depth_prep<T, KT>(TR, threadIdx.x, blockIdx.x, k2, false, n1, n2, hs, w1, w2, uniform, hz);
     bool done = mbar_wait_bounded(bar, 1000000000ull);   // 1 s
     if (__syncthreads_or(!done)) {
       if (threadIdx.x == 0 && status) atomicOr(status, 1);
@@ -986,12 +1000,13 @@ __global__ void __launch_bounds__(256, MB) k_mindlin_depth_r(typename Cx<T>::t* 
   }
   if (tma_rows <= 0) {
     for (int i = threadIdx.x; i < nz; i += blockDim.x) zs[i] = zn[i];
+    g = depth_prep<T, KT>(TR, threadIdx.x, blockIdx.x, k2, false, n1, n2, hs, w1, w2, uniform, hz);
     cp_async_wait_all();
     __syncthreads();
   }
 
   depth_r_body<T, KT, C, EIN>(W, SA, SP, TR, zs, threadIdx.x, blockIdx.x, k2, false, spec, surf, nz, n1, n2, hs, h1,
-                              nch, w1, w2, lam, mu, nu, out_kind, want_u3, uniform, hz, cut);
+                              nch, w1, w2, lam, mu, nu, out_kind, want_u3, uniform, hz, cut, g);
 }
 
 // ----------------------------------------------------------------------------------
@@ -1033,11 +1048,13 @@ __global__ void __launch_bounds__(256, 2) k_grp_depth(const __grid_constant__ Gr
     }
     for (int i = tid; i < nz; i += tt) zs[i] = P.zn[i];
   }
+  const ModeGeom<float> g =
+      depth_prep<float, KT>(TR, tid, kblk, k2, ghost, P.n1, P.n2, P.hs, P.w1, P.w2, P.uniform, P.hz);
   cp_async_wait_all();
   __syncthreads();
   depth_r_body<float, KT, C, false>(W, SA, SP, TR, zs, tid, kblk, k2, ghost, P.spec, nullptr, nz, P.n1, P.n2, P.hs,
                                     P.h1, P.nch, P.w1, P.w2, P.lam, P.mu, P.nu, P.out_kind, 0, P.uniform, P.hz,
-                                    P.cut);
+                                    P.cut, g);
 }
 
 // ----------------------------------------------------------------------------------
