@@ -905,7 +905,7 @@ def scaling_metrics(sizes=(4, 8, 16, 32, 64, 128), reps=20):
 # workload, from one capture of the current kernels (profiles/ summaries); a kernel missing
 # here, or changed since its capture, reports null.
 TRAFFIC_DEPTH_PLAN = (4, 2)  # depth tile plan of that capture (chunk length, CTAs per SM)
-TRAFFIC_BYTES = {"rows_fwd6": 755.3e6, "cols_fwd": 744.3e6, "mindlin_depth": 743.8e6, "cols_inv": 744.3e6,
+TRAFFIC_BYTES = {"rows_fwd6": 755.3e6, "cols_fwd": 744.3e6, "mindlin_depth": 743.9e6, "cols_inv": 744.3e6,
                  "rows_inv6": 756.2e6}
 
 
