@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(256) k_mindlin_depth(typename Cx<T>::t* __rest
                                 T w2, T lam, T mu, T nu, int out_kind, int want_u3, int uniform, T hz,
                                 const int* __restrict__ zr) {
   typedef typename Cx<T>::t V;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];  // one alignment for every kernel of this file
   V* W = reinterpret_cast<V*>(smraw);                 // [nz][6][KT]
   V* Pst = W + (size_t)nz * 6 * KT;                   // [max(nz, 2 nch + 1)][6][KT]
   T* zs = reinterpret_cast<T*>(Pst + (size_t)prow * KT * 6);  // [nz] depth nodes
